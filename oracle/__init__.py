@@ -1,0 +1,225 @@
+"""FP64 CPU oracle for batched MIMO tree-search detection (arXiv 2002.09561).
+
+TEST INFRASTRUCTURE ONLY.  The tests, the smoke check and the CPU-baseline
+leg of the benchmark load it; the product path (the CUDA library and its
+binding) never does, and it shares no code with the CUDA sources.  The
+arithmetic lives in oracle.c (plain C, double precision, each function
+citing the passage of the paper it writes out); this module only builds
+that library and marshals numpy arrays into it.
+
+Parity unpinned: none of the functions here; every one has a pin in
+tests/test_oracle.py (brute force, closed forms, library routines, the
+paper's printed counts and its ML symbol-error curve).
+"""
+
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "oracle.c")
+_HDR = os.path.join(_HERE, "oracle.h")
+_SO = os.path.join(_HERE, "liboracle.so")
+_lock = threading.Lock()
+_lib = None
+
+ALGO = {"sd": 0, "kbest": 1, "hybrid": 2, "ml": 3}
+ORDER = {"se": 0, "natural": 1, "reversed": 2, "random": 3}
+V_OK, V_EMPTY_RETRIED, V_BUDGET_EXCEEDED = 0, 1, 2
+
+
+def build(force: bool = False) -> str:
+    """Compile oracle.c into liboracle.so (gcc, OpenMP, -O2)."""
+    stale = (not os.path.exists(_SO)) or any(
+        os.path.getmtime(p) > os.path.getmtime(_SO) for p in (_SRC, _HDR))
+    if force or stale:
+        tmp = _SO + f".tmp{os.getpid()}"
+        subprocess.check_call(["gcc", "-O2", "-std=c11", "-fopenmp", "-fPIC", "-shared", "-o", tmp,
+                               _SRC, "-lm"])
+        os.replace(tmp, _SO)
+    return _SO
+
+
+def lib():
+    global _lib
+    with _lock:
+        if _lib is None:
+            build()
+            L = ctypes.CDLL(_SO)
+            d, i, ll, vp = ctypes.c_double, ctypes.c_int, ctypes.c_longlong, ctypes.c_void_p
+            L.orc_pam_levels.argtypes = [i, vp]
+            L.orc_pam_levels.restype = i
+            L.orc_real_decompose.argtypes = [i, i, vp, vp, vp, vp]
+            L.orc_qr.argtypes = [i, i, vp, vp, vp, vp, vp]
+            L.orc_qr.restype = i
+            L.orc_metric.argtypes = [i, vp, vp, vp, vp]
+            L.orc_metric.restype = d
+            L.orc_ml_bruteforce.argtypes = [i, i, i, vp, vp, vp, vp, vp]
+            L.orc_sd.argtypes = [i, i, vp, vp, vp, d, ll, i, ctypes.c_uint64, i, vp, vp, vp, vp]
+            L.orc_sd.restype = i
+            L.orc_kbest.argtypes = [i, i, vp, vp, vp, i, d, vp, vp, vp, vp]
+            L.orc_kbest.restype = i
+            L.orc_hybrid.argtypes = [i, i, vp, vp, vp, i, i, d, i, ctypes.c_uint64, vp, vp, vp, vp]
+            L.orc_hybrid.restype = i
+            L.orc_detect_batch.argtypes = [i, i, i, i, i, vp, vp, vp, d, i, i, ll, i, i, vp, vp, vp,
+                                           vp, vp, i]
+            L.orc_detect_batch.restype = i
+            L.orc_qr_batch.argtypes = [i, i, i, vp, vp, vp, vp, i]
+            L.orc_qr_batch.restype = i
+            L.orc_count_errors.argtypes = [i, i, i, vp, vp, vp]
+            L.orc_max_threads.restype = i
+            _lib = L
+    return _lib
+
+
+def _p(a):
+    return None if a is None else a.ctypes.data_as(ctypes.c_void_p)
+
+
+def _f64(a):
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+class Stats(ctypes.Structure):
+    _fields_ = [("nodes", ctypes.c_longlong), ("peds", ctypes.c_longlong),
+                ("restarts", ctypes.c_longlong), ("leaves", ctypes.c_longlong)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+def max_threads() -> int:
+    return lib().orc_max_threads()
+
+
+def pam_levels(qam: int) -> np.ndarray:
+    out = np.zeros(16)
+    P = lib().orc_pam_levels(qam, _p(out))
+    if P < 0:
+        raise ValueError(qam)
+    return out[:P].copy()
+
+
+def real_decompose(H: np.ndarray, y: np.ndarray):
+    """H [N][M][2], y [N][2] -> Hr [2N][2M], yr [2N]."""
+    H, y = _f64(H), _f64(y)
+    N, M = H.shape[0], H.shape[1]
+    Hr = np.zeros((2 * N, 2 * M))
+    yr = np.zeros(2 * N)
+    lib().orc_real_decompose(N, M, _p(H), _p(y), _p(Hr), _p(yr))
+    return Hr, yr
+
+
+def qr(A: np.ndarray, y: np.ndarray | None = None, want_q: bool = False):
+    A = _f64(A)
+    m, n = A.shape
+    R = np.zeros((n, n))
+    yb = np.zeros(n)
+    Q = np.zeros((m, n)) if want_q else None
+    yv = None if y is None else _f64(y)
+    sing = lib().orc_qr(m, n, _p(A), _p(yv), _p(Q), _p(R), _p(yb))
+    return {"Q": Q, "R": R, "ybar": yb, "singular": bool(sing)}
+
+
+def metric(R, ybar, qam, k) -> float:
+    R, ybar = _f64(R), _f64(ybar)
+    lev = pam_levels(qam)
+    k = np.ascontiguousarray(k, dtype=np.int32)
+    return lib().orc_metric(R.shape[0], _p(R), _p(ybar), _p(lev), _p(k))
+
+
+def ml_bruteforce(H, y, qam):
+    H, y = _f64(H), _f64(y)
+    N, M = H.shape[0], H.shape[1]
+    sym = np.zeros(M, dtype=np.uint8)
+    d1 = np.zeros(1)
+    d2 = np.zeros(1)
+    lib().orc_ml_bruteforce(N, M, qam, _p(H), _p(y), _p(sym), _p(d1), _p(d2))
+    return {"sym": sym, "d1": d1[0], "d2": d2[0]}
+
+
+def sd(R, ybar, qam, r2=np.inf, budget=0, order="se", seed=0, two_best=False):
+    R, ybar = _f64(R), _f64(ybar)
+    n = R.shape[0]
+    lev = pam_levels(qam)
+    k = np.zeros(n, dtype=np.int32)
+    d1 = np.zeros(1)
+    d2 = np.zeros(1)
+    st = Stats()
+    rc = lib().orc_sd(n, len(lev), _p(R), _p(ybar), _p(lev), float(r2), int(budget), ORDER[order],
+                      int(seed), int(two_best), _p(k), _p(d1), _p(d2), ctypes.byref(st))
+    if rc < 0:
+        raise ValueError("bad arguments")
+    return {"k": k, "d1": d1[0], "d2": d2[0], "status": rc, **st.as_dict()}
+
+
+def kbest(R, ybar, qam, K, r2=np.inf):
+    R, ybar = _f64(R), _f64(ybar)
+    n = R.shape[0]
+    lev = pam_levels(qam)
+    k = np.zeros(n, dtype=np.int32)
+    d1 = np.zeros(1)
+    gap = np.zeros(1)
+    st = Stats()
+    rc = lib().orc_kbest(n, len(lev), _p(R), _p(ybar), _p(lev), int(K), float(r2), _p(k), _p(d1),
+                         _p(gap), ctypes.byref(st))
+    if rc < 0:
+        raise ValueError("bad arguments")
+    return {"k": k, "d1": d1[0], "gap": gap[0], "status": rc, **st.as_dict()}
+
+
+def hybrid(R, ybar, qam, K, depth, r2=np.inf, order="se", seed=0):
+    R, ybar = _f64(R), _f64(ybar)
+    n = R.shape[0]
+    lev = pam_levels(qam)
+    k = np.zeros(n, dtype=np.int32)
+    d1 = np.zeros(1)
+    gap = np.zeros(1)
+    st = Stats()
+    rc = lib().orc_hybrid(n, len(lev), _p(R), _p(ybar), _p(lev), int(K), int(depth), float(r2),
+                          ORDER[order], int(seed), _p(k), _p(d1), _p(gap), ctypes.byref(st))
+    if rc < 0:
+        raise ValueError("bad arguments")
+    return {"k": k, "d1": d1[0], "gap": gap[0], "status": rc, **st.as_dict()}
+
+
+def detect_batch(algo, H, y, noise_var, qam, radius=np.inf, K=16, depth=4, budget=0, order="se",
+                 want_gap=False, nthreads=0):
+    """Detect a batch; radius: float (inf = none) or 'paper' for r^2 = N M sigma^2."""
+    H, y, nv = _f64(H), _f64(y), _f64(noise_var)
+    B, N, M = H.shape[0], H.shape[1], H.shape[2]
+    r = -1.0 if isinstance(radius, str) else float(radius)
+    sym = np.zeros((B, M), dtype=np.uint8)
+    met = np.zeros(B)
+    status = np.zeros(B, dtype=np.int32)
+    stats = np.zeros((B, 4), dtype=np.int64)
+    gap = np.zeros(B)
+    rc = lib().orc_detect_batch(ALGO[algo], B, N, M, int(qam), _p(H), _p(y), _p(nv), r, int(K),
+                                int(depth), int(budget), ORDER[order], int(want_gap), _p(sym),
+                                _p(met), _p(status), _p(stats), _p(gap), int(nthreads))
+    if rc < 0:
+        raise ValueError("bad arguments")
+    return {"sym": sym, "metric": met, "status": status, "stats": stats, "gap": gap}
+
+
+def qr_batch(H, y, nthreads=0):
+    H, y = _f64(H), _f64(y)
+    B, N, M = H.shape[0], H.shape[1], H.shape[2]
+    n = 2 * M
+    R = np.zeros((B, n, n))
+    yb = np.zeros((B, n))
+    lib().orc_qr_batch(B, N, M, _p(H), _p(y), _p(R), _p(yb), int(nthreads))
+    return R, yb
+
+
+def count_errors(sym_hat, sym_true, qam):
+    a = np.ascontiguousarray(sym_hat, dtype=np.uint8)
+    b = np.ascontiguousarray(sym_true, dtype=np.uint8)
+    out = np.zeros(2, dtype=np.int64)
+    lib().orc_count_errors(a.shape[0], a.shape[1], int(qam), _p(a), _p(b), _p(out))
+    return int(out[0]), int(out[1])

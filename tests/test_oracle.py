@@ -1,0 +1,356 @@
+"""Pins of the FP64 oracle against facts that do not come from the oracle itself.
+
+Each test checks one function of oracle/ against brute force (Eq. 2),
+a library routine (LAPACK's complex QR), a closed form (the Babai point,
+node-count formulas), an invariant the paper states (radius pruning never
+loses the ML point, Sec. III-B; the K-best node count, Sec. VI) or the
+paper's printed values (tests/golden).
+"""
+
+import json
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2002_09561_gb300 import workload as wl
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _complex(a):
+    return a[..., 0] + 1j * a[..., 1]
+
+
+def _interleave(v):
+    out = np.empty(v.shape[:-1] + (2 * v.shape[-1],))
+    out[..., 0::2] = v.real
+    out[..., 1::2] = v.imag
+    return out
+
+
+def _system(seed, N, M, qam, snr):
+    w = wl.generate(seed, 1, N, M, qam, snr)
+    Hr, yr = oracle.real_decompose(w["H"][0], w["y"][0])
+    f = oracle.qr(Hr, yr, want_q=True)
+    return w, Hr, yr, f
+
+
+# --------------------------------------------------------------------- alphabet / model
+
+
+@pytest.mark.parametrize("qam", [4, 16, 64])
+def test_pam_levels_unit_energy_and_spacing(qam):
+    lev = oracle.pam_levels(qam)
+    P = len(lev)
+    assert P * P == qam
+    # E|s|^2 over the complex alphabet = 2 * mean(level^2) = 1 exactly
+    assert abs(2 * np.mean(lev ** 2) - 1.0) < 1e-15
+    np.testing.assert_allclose(np.diff(lev), np.full(P - 1, lev[1] - lev[0]), rtol=1e-15)
+    np.testing.assert_allclose(lev, -lev[::-1], atol=1e-16)
+    # the generator's independent alphabet agrees
+    np.testing.assert_allclose(wl.qam_symbols(np.arange(P) * P, qam).real, lev, rtol=1e-15)
+
+
+def test_real_decomposition_matches_complex_product():
+    rng = np.random.default_rng(1)
+    H = rng.standard_normal((5, 3, 2))
+    s = rng.standard_normal(3) + 1j * rng.standard_normal(3)
+    Hr, _ = oracle.real_decompose(H, np.zeros((5, 2)))
+    np.testing.assert_allclose(Hr @ _interleave(s), _interleave(_complex(H) @ s), atol=1e-14)
+
+
+# ------------------------------------------------------------------------------- QR
+
+
+@pytest.mark.parametrize("N,M", [(4, 4), (16, 16), (12, 8), (40, 40)])
+def test_qr_factorises(N, M):
+    w, Hr, yr, f = _system(2, N, M, 16, 10.0)
+    Q, R = f["Q"], f["R"]
+    assert np.linalg.norm(Q @ R - Hr) / np.linalg.norm(Hr) < 1e-13
+    assert np.linalg.norm(Q.T @ Q - np.eye(2 * M)) < 1e-13
+    assert np.all(np.tril(R, -1) == 0.0)
+    assert np.all(np.diag(R) > 0)
+    np.testing.assert_allclose(f["ybar"], Q.T @ yr, atol=1e-12)
+
+
+@pytest.mark.parametrize("N,M", [(4, 4), (16, 16), (10, 6)])
+def test_real_r_is_block_form_of_complex_qr(N, M):
+    """QR with a positive diagonal is unique, so the real R of the interleaved
+    system must equal the 2x2-block form [[a,-b],[b,a]] of the complex R that
+    LAPACK returns once its row phases are normalised."""
+    w, Hr, yr, f = _system(3, N, M, 4, 8.0)
+    Hc, yc = _complex(w["H"][0]), _complex(w["y"][0])
+    Qc, Rc = np.linalg.qr(Hc)
+    ph = np.diag(Rc) / np.abs(np.diag(Rc))
+    Rc = Rc / ph[:, None]
+    ybc = (Qc.conj().T @ yc) / ph
+    blk = np.zeros((2 * M, 2 * M))
+    blk[0::2, 0::2] = Rc.real
+    blk[0::2, 1::2] = -Rc.imag
+    blk[1::2, 0::2] = Rc.imag
+    blk[1::2, 1::2] = Rc.real
+    np.testing.assert_allclose(f["R"], blk, atol=1e-12)
+    np.testing.assert_allclose(f["ybar"], _interleave(ybc), atol=1e-12)
+
+
+def test_reduced_metric_differs_by_a_constant():
+    """Sec. III-B: ||y - Hs||^2 = ||ybar - Rs||^2 + const for every s."""
+    w, Hr, yr, f = _system(4, 12, 8, 64, 15.0)
+    rng = np.random.default_rng(0)
+    offs = []
+    for _ in range(100):
+        k = rng.integers(0, 8, size=16).astype(np.int32)
+        x = oracle.pam_levels(64)[k]
+        full = np.sum((yr - Hr @ x) ** 2)
+        offs.append(full - oracle.metric(f["R"], f["ybar"], 64, k))
+    assert np.ptp(offs) < 1e-10 * np.sum(yr ** 2)
+
+
+# ------------------------------------------------------------------------- sphere decoder
+
+
+def test_sd_equals_brute_force_4x4_4qam_1000_vectors():
+    """The exact-SD configuration: 4x4 4-QAM, 10 dB, 1,000 vectors, r = inf,
+    checked against enumeration of all 256 symbol vectors (Eq. 2)."""
+    w = wl.generate(0, 1000, 4, 4, 4, 10.0)
+    sd = oracle.detect_batch("sd", w["H"], w["y"], w["noise_var"], 4)
+    ml = oracle.detect_batch("ml", w["H"], w["y"], w["noise_var"], 4)
+    np.testing.assert_array_equal(sd["sym"], ml["sym"])
+    np.testing.assert_allclose(sd["metric"], ml["metric"], rtol=1e-12, atol=1e-14)
+    # independent enumeration in numpy for a few vectors
+    P = 2
+    lev = oracle.pam_levels(4)
+    allq = np.array(np.meshgrid(*[np.arange(4)] * 4, indexing="ij")).reshape(4, -1).T
+    S = (lev[allq // P] + 1j * lev[allq % P])
+    for b in range(20):
+        d = np.sum(np.abs(_complex(w["y"][b])[None, :] - S @ _complex(w["H"][b]).T) ** 2, axis=1)
+        np.testing.assert_array_equal(sd["sym"][b], allq[np.argmin(d)])
+
+
+@pytest.mark.parametrize("N,M,qam,snr", [(2, 2, 16, 5.0), (3, 3, 4, 0.0), (2, 2, 64, 12.0),
+                                          (3, 2, 16, 8.0), (3, 3, 16, 20.0)])
+def test_sd_equals_brute_force_small(N, M, qam, snr):
+    w = wl.generate(7, 200, N, M, qam, snr)
+    sd = oracle.detect_batch("sd", w["H"], w["y"], w["noise_var"], qam, radius="paper",
+                             want_gap=True)
+    ml = oracle.detect_batch("ml", w["H"], w["y"], w["noise_var"], qam)
+    np.testing.assert_array_equal(sd["sym"], ml["sym"])
+    np.testing.assert_allclose(sd["metric"], ml["metric"], rtol=1e-11, atol=1e-13)
+    # with no initial radius the two-best pass recovers the brute-force
+    # second-best metric; with one it can only report a smaller gap
+    np.testing.assert_array_less(sd["gap"], ml["gap"] * (1 + 1e-9) + 1e-15)
+    free = oracle.detect_batch("sd", w["H"], w["y"], w["noise_var"], qam, want_gap=True)
+    np.testing.assert_allclose(free["gap"], ml["gap"], rtol=1e-7, atol=1e-12)
+
+
+def test_sd_radius_invariance():
+    """Any radius above the ML metric returns the ML point (Sec. III-B); a
+    radius at the ML metric leaves the sphere empty (pruning is E >= r^2),
+    which triggers one radius doubling."""
+    w, Hr, yr, f = _system(5, 6, 6, 16, 9.0)
+    ref = oracle.sd(f["R"], f["ybar"], 16)
+    d = ref["d1"]
+    above = oracle.sd(f["R"], f["ybar"], 16, r2=d * (1 + 1e-9))
+    np.testing.assert_array_equal(above["k"], ref["k"])
+    assert above["status"] == oracle.V_OK and above["nodes"] <= ref["nodes"]
+    at = oracle.sd(f["R"], f["ybar"], 16, r2=d)
+    assert at["status"] == oracle.V_EMPTY_RETRIED and at["restarts"] == 1
+    np.testing.assert_array_equal(at["k"], ref["k"])
+
+
+def test_sd_order_independence_and_best_first_benefit():
+    """The exact result does not depend on the child order (Alg. 1 prunes
+    with the current radius only); Best-FS (Sec. IV-A) visits fewer nodes
+    than plain DFS."""
+    nodes = {o: 0 for o in ("se", "natural", "reversed", "random")}
+    for seed in range(30):
+        w, Hr, yr, f = _system(100 + seed, 8, 8, 16, 8.0)
+        ref = None
+        for o in nodes:
+            r = oracle.sd(f["R"], f["ybar"], 16, r2=np.inf, order=o, seed=seed)
+            nodes[o] += r["nodes"]
+            if ref is None:
+                ref = r
+            np.testing.assert_array_equal(r["k"], ref["k"])
+            assert r["d1"] == pytest.approx(ref["d1"], rel=1e-12)
+    assert nodes["se"] < nodes["natural"] and nodes["se"] < nodes["reversed"]
+
+
+def test_sd_budget_stops_early():
+    w, Hr, yr, f = _system(6, 16, 16, 16, 4.0)
+    r = oracle.sd(f["R"], f["ybar"], 16, budget=50)
+    assert r["status"] == oracle.V_BUDGET_EXCEEDED
+    assert r["nodes"] <= 50
+
+
+def test_sd_metric_is_the_leaf_partial_distance():
+    """Eq. inc accumulated to a leaf equals ||ybar - R x||^2 recomputed."""
+    for seed in range(10):
+        w, Hr, yr, f = _system(200 + seed, 10, 10, 64, 14.0)
+        r = oracle.sd(f["R"], f["ybar"], 64)
+        assert r["d1"] == pytest.approx(oracle.metric(f["R"], f["ybar"], 64, r["k"]), rel=1e-12)
+
+
+# -------------------------------------------------------------------------------- K-best
+
+
+@pytest.mark.parametrize("K", [128, 256])
+def test_kbest_with_full_tree_equals_ml(K):
+    """K >= P^(n-1) keeps every node, so K-best is ML (4x4 4-QAM: n=8, P=2)."""
+    w = wl.generate(8, 300, 4, 4, 4, 6.0)
+    kb = oracle.detect_batch("kbest", w["H"], w["y"], w["noise_var"], 4, K=K)
+    ml = oracle.detect_batch("ml", w["H"], w["y"], w["noise_var"], 4)
+    np.testing.assert_array_equal(kb["sym"], ml["sym"])
+
+
+def _babai(R, ybar, qam):
+    """Closed form of successive interference cancellation with clipping:
+    x_i = clip(round(c_i / R_ii)) in the PAM grid, top row first."""
+    n = R.shape[0]
+    P = wl.pam_size(qam)
+    alpha = np.sqrt(3.0 / (2.0 * (qam - 1)))
+    k = np.zeros(n, dtype=np.int32)
+    for i in range(n - 1, -1, -1):
+        c = ybar[i] - sum(R[i, j] * (2 * k[j] - (P - 1)) * alpha for j in range(i + 1, n))
+        u = (c / R[i, i] / alpha + (P - 1)) / 2.0
+        k[i] = int(np.clip(np.floor(u + 0.5), 0, P - 1))
+    return k
+
+
+@pytest.mark.parametrize("qam", [4, 16, 64])
+def test_kbest_k1_is_babai(qam):
+    for seed in range(20):
+        w, Hr, yr, f = _system(300 + seed, 8, 6, qam, 10.0)
+        r = oracle.kbest(f["R"], f["ybar"], qam, 1)
+        np.testing.assert_array_equal(r["k"], _babai(f["R"], f["ybar"], qam))
+
+
+def _visited_formula(levels, branching, K):
+    """Root plus, for every later level l = 1..levels-1, min(K, branching^l)."""
+    return 1 + sum(min(K, branching ** l) for l in range(1, levels))
+
+
+def test_kbest_node_count_formula_matches_paper_counts():
+    """The paper's K-best counts on the complex tree (Sec. VI; 151 and 481
+    nodes for 16x16 64-QAM at K = 10 and 32) fix the counting convention:
+    the root counts, leaves do not."""
+    g = json.load(open(os.path.join(GOLDEN, "kbest_visited_nodes.json")))["complex_tree"]
+    for K, visited in g["points"]:
+        assert _visited_formula(g["M"], g["qam"], K) == visited
+
+
+@pytest.mark.parametrize("n_tx,qam,K", [(16, 16, 16), (16, 16, 64), (4, 4, 3), (8, 64, 32)])
+def test_kbest_real_tree_node_count(n_tx, qam, K):
+    w, Hr, yr, f = _system(9, n_tx, n_tx, qam, 12.0)
+    r = oracle.kbest(f["R"], f["ybar"], qam, K)
+    assert r["nodes"] == _visited_formula(2 * n_tx, wl.pam_size(qam), K)
+    assert r["peds"] == r["nodes"] * wl.pam_size(qam)
+    if (n_tx, qam, K) == (16, 16, 16):
+        assert r["nodes"] == 485
+
+
+def test_kbest_radius_keeps_the_unpruned_answer():
+    """With strict pruning and partial distances that only grow along a path,
+    the kept set under a radius is the unpruned kept set inside the sphere:
+    K-best(r) returns K-best(inf) whenever that leaf lies inside r."""
+    for seed in range(20):
+        w, Hr, yr, f = _system(400 + seed, 8, 8, 16, 10.0)
+        free = oracle.kbest(f["R"], f["ybar"], 16, 8)
+        inside = oracle.kbest(f["R"], f["ybar"], 16, 8, r2=free["d1"] * 1.000001)
+        np.testing.assert_array_equal(inside["k"], free["k"])
+        assert inside["nodes"] <= free["nodes"]
+        outside = oracle.kbest(f["R"], f["ybar"], 16, 8, r2=free["d1"])
+        assert outside["status"] == oracle.V_EMPTY_RETRIED
+
+
+# -------------------------------------------------------------------------------- hybrid
+
+
+def test_hybrid_is_independent_of_prefix_order():
+    """The hybrid's answer is the best K-best leaf over all depth-d prefixes
+    inside the initial sphere, whatever order the master hands them out in."""
+    for seed in range(15):
+        w, Hr, yr, f = _system(500 + seed, 8, 8, 64, 16.0)
+        r2 = 8 * 8 * w["noise_var"][0]
+        outs = [oracle.hybrid(f["R"], f["ybar"], 64, 4, 4, r2=r2, order=o, seed=seed)
+                for o in ("se", "reversed", "random", "natural")]
+        for o in outs[1:]:
+            np.testing.assert_array_equal(o["k"], outs[0]["k"])
+
+
+def test_hybrid_limits():
+    for seed in range(10):
+        w, Hr, yr, f = _system(600 + seed, 5, 5, 16, 9.0)
+        R, yb = f["R"], f["ybar"]
+        r2 = 25 * w["noise_var"][0]
+        # d = 0: the master hands the root over, so it is K-best with the radius
+        h0 = oracle.hybrid(R, yb, 16, 6, 0, r2=r2)
+        kb = oracle.kbest(R, yb, 16, 6, r2=r2)
+        np.testing.assert_array_equal(h0["k"], kb["k"])
+        # d = n: the master reaches the leaves, so it is the sphere decoder
+        hn = oracle.hybrid(R, yb, 16, 6, 10, r2=r2)
+        sd = oracle.sd(R, yb, 16, r2=r2)
+        np.testing.assert_array_equal(hn["k"], sd["k"])
+        # K >= P^(n-d-1): the workers keep everything, so the answer is ML
+        hf = oracle.hybrid(R, yb, 16, 4 ** 5, 4, r2=np.inf)
+        np.testing.assert_array_equal(hf["k"], sd["k"])
+
+
+# ------------------------------------------------------------------------ error counting
+
+
+def test_gray_bits_between_neighbours():
+    """Adjacent PAM levels differ in exactly one Gray bit; the count is
+    symmetric and zero on the diagonal."""
+    for qam in (4, 16, 64):
+        P = wl.pam_size(qam)
+        for kre in range(P):
+            for kim in range(P - 1):
+                a = np.array([[kre * P + kim]], dtype=np.uint8)
+                b = np.array([[kre * P + kim + 1]], dtype=np.uint8)
+                assert oracle.count_errors(a, b, qam) == (1, 1)
+                c = np.array([[kim * P + kre]], dtype=np.uint8)
+                d = np.array([[(kim + 1) * P + kre]], dtype=np.uint8)
+                assert oracle.count_errors(c, d, qam) == (1, 1)
+        q = np.arange(qam, dtype=np.uint8)[None, :]
+        assert oracle.count_errors(q, q, qam) == (0, 0)
+
+
+def test_bit_errors_explicit_16qam():
+    # Gray codes of the 4-PAM indices 0..3: 00, 01, 11, 10.
+    gray = {0: 0b00, 1: 0b01, 2: 0b11, 3: 0b10}
+    rng = np.random.default_rng(0)
+    a = rng.integers(0, 16, size=(50, 4)).astype(np.uint8)
+    b = rng.integers(0, 16, size=(50, 4)).astype(np.uint8)
+    bits = sum(bin(gray[x // 4] ^ gray[y // 4]).count("1") + bin(gray[x % 4] ^ gray[y % 4]).count("1")
+               for x, y in zip(a.ravel(), b.ravel()))
+    assert oracle.count_errors(a, b, 16) == (bits, int(np.sum(a != b)))
+
+
+# ------------------------------------------------------------- ML SER against the paper
+
+
+def test_ml_ser_curves_match_paper_shape():
+    """The exact detector's symbol error rate against the paper's ML curves
+    (10x10 and 16x16 16-QAM).  The paper does not state its SNR convention;
+    with sigma^2 = 10^(-SNR/10) per complex entry and unit-energy symbols the
+    oracle's curves sit 5.5 dB to the left of the printed ones, by the same
+    amount for both sizes.  A wrong detector (not ML, or a wrong metric)
+    changes the slope or the spacing of the two curves and fails here."""
+    g = json.load(open(os.path.join(GOLDEN, "fig9a_ml_ser.json")))
+    shift = 5.5
+    checks = [("10", 10, 2000), ("10", 12, 3000), ("10", 14, 20000), ("16", 10, 300)]
+    for size, snr_paper, B in checks:
+        paper = dict(g["curves"][size])[snr_paper]
+        M = int(size)
+        w = wl.generate(1000 + snr_paper, B, M, M, 16, snr_paper - shift)
+        r = oracle.detect_batch("sd", w["H"], w["y"], w["noise_var"], 16, radius="paper")
+        ser = np.mean(r["sym"] != w["sym"])
+        assert paper / 2.0 < ser < paper * 2.0, (size, snr_paper, ser, paper)
+    # and the convention with total transmit power normalised
+    # (sigma^2 = M 10^(-SNR/10)) lands far from the printed curve
+    w = wl.generate(77, 500, 10, 10, 16, 12.0 - 10.0)
+    r = oracle.detect_batch("sd", w["H"], w["y"], w["noise_var"], 16, radius="paper")
+    assert np.mean(r["sym"] != w["sym"]) > 4 * dict(g["curves"]["10"])[12]
