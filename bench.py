@@ -1,0 +1,352 @@
+#!/usr/bin/env python3
+"""Throughput benchmark of the batched MIMO tree-search detectors.
+
+One step = one pass of the detection path over one batch of synthetic
+received vectors resident in device memory: FP64 QR, the tree search
+(FP32 partial distances), FP64 re-scoring of the final leaves, and the
+Gray-coded bit/symbol error count of the batch.  The default workload is
+16x16 MIMO, 16-QAM, exact sphere decoding with the paper's initial radius
+r^2 = N M sigma^2, 100,000 vectors per step with the SNR points 4, 6, ..., 20
+dB interleaved (vector b at point b mod 9).
+
+Prints one JSON line (rank 0).  Launch: python bench.py [--gpus N] [--steps K]
+[--warmup W] [--workload NAME] [--impl mdx|reference]; for N > 1 under
+torch.distributed.run, one rank per GPU, each rank detecting its own shard.
+"""
+
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+SWEEP_16 = [4.0, 6.0, 8.0, 10.0, 12.0, 14.0, 16.0, 18.0, 20.0]
+WORKLOADS = {
+    "16x16-16qam-sd": dict(n=16, qam=16, snr=SWEEP_16, vectors=100_000, detector="sd", radius="paper",
+                           K=0, depth=0),
+    "16x16-16qam-kbest64": dict(n=16, qam=16, snr=SWEEP_16, vectors=100_000, detector="kbest",
+                                radius=math.inf, K=64, depth=0),
+    "16x16-16qam-kbest256": dict(n=16, qam=16, snr=SWEEP_16, vectors=100_000, detector="kbest",
+                                 radius=math.inf, K=256, depth=0),
+    "100x100-64qam-hybrid32": dict(n=100, qam=64, snr=[20.0, 24.0, 28.0, 32.0], vectors=10_000,
+                                   detector="hybrid", radius="paper", K=32, depth=4),
+    "100x100-64qam-hybrid128": dict(n=100, qam=64, snr=[20.0, 24.0, 28.0, 32.0], vectors=10_000,
+                                    detector="hybrid", radius="paper", K=128, depth=4),
+}
+METRIC = "decoded vectors/s at matched BER (16x16 16QAM, 100x100 64QAM), learned vs plain"
+FP32_LANES_PER_SM = 128  # FP32 FMA lanes per SM (4 sub-partitions x 32)
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="mdx", choices=["mdx", "reference"])
+    ap.add_argument("--workload", default="16x16-16qam-sd", choices=sorted(WORKLOADS))
+    ap.add_argument("--vectors", type=int, default=0, help="override vectors per step (per GPU)")
+    ap.add_argument("--snr", type=str, default="", help="comma-separated SNR points (override)")
+    ap.add_argument("--seed", type=int, default=1)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0, help="target CPU-baseline duration")
+    return ap.parse_args()
+
+
+def workload_of(args):
+    w = dict(WORKLOADS[args.workload])
+    if args.vectors:
+        w["vectors"] = args.vectors
+    if args.snr:
+        w["snr"] = [float(s) for s in args.snr.split(",")]
+    return w
+
+
+def generate(w, seed, count, start=0):
+    from paper_2002_09561_gb300 import workload as wl
+
+    snr = np.asarray(w["snr"])[np.arange(start, start + count) % len(w["snr"])]
+    return wl.generate(seed, count, w["n"], w["n"], w["qam"], snr, start=start)
+
+
+def load_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            return json.load(f)
+    except OSError:
+        return {}
+
+
+class ClockSampler:
+    """nvidia-smi samples every 200 ms while the timed region runs."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.rows = []
+        self.proc = None
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits", "-lms", "200",
+                 "-i", str(self.index)], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 9:
+                self.rows.append(parts)
+
+    def stop(self):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+        if self.thread is not None:
+            self.thread.join(timeout=5)
+
+    def summary(self):
+        if not self.rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"], "samples": 0}
+
+        def num(x):
+            try:
+                return float(x)
+            except ValueError:
+                return None
+
+        sm = [num(r[1]) for r in self.rows if num(r[1]) is not None]
+        mx = [num(r[2]) for r in self.rows if num(r[2]) is not None]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in self.rows for i in range(4) if r[5 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(self.rows)}
+
+
+def cpu_baseline(w, seed, target_s, start_offset):
+    """The FP64 oracle on the host cores over a bounded sample of the same
+    workload: vectors taken round-robin over the SNR points, in chunks, until
+    target_s seconds have been spent."""
+    import oracle
+
+    cores = oracle.max_threads()
+    algo = w["detector"]
+    done = 0
+    t0 = time.perf_counter()
+    chunk = max(cores, 16)
+    pos = start_offset
+    while time.perf_counter() - t0 < target_s and done < w["vectors"]:
+        d = generate(w, seed, chunk, start=pos)
+        oracle.detect_batch(algo, d["H"], d["y"], d["noise_var"], w["qam"], radius=w["radius"],
+                            K=max(w["K"], 1), depth=w["depth"])
+        done += chunk
+        pos += chunk
+    dt = time.perf_counter() - t0
+    return {"value": done / dt, "unit": "vectors/s", "cores": cores, "kind": "oracle",
+            "sample": f"{done} vectors of the same workload ({w['n']}x{w['n']} {w['qam']}-QAM "
+                      f"{algo}, SNR points round-robin) in {dt:.1f} s on {cores} threads"}
+
+
+def run_reference(args, w, rank, world):
+    if rank != 0:
+        return
+    steps, warm = args.steps, args.warmup
+    target = max(2.0, min(args.cpu_seconds, 60.0 / max(1, steps + warm)))
+    for _ in range(warm):
+        cpu_baseline(w, args.seed, target / 4, 0)
+    vals = []
+    t0 = time.perf_counter()
+    for k in range(steps):
+        vals.append(cpu_baseline(w, args.seed, target, 0))
+    wall = time.perf_counter() - t0
+    value = float(np.mean([v["value"] for v in vals]))
+    base = dict(vals[-1])
+    base["value"] = value
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "vectors/s", "n_gpus": world,
+            "steps": steps, "warmup": warm, "ms_per_step": 1e3 * wall / steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": config_of(args, w, world), "cpu_baseline": base,
+            "e2e": {"value": value, "unit": "vectors/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def config_of(args, w, world):
+    return {"workload": args.workload, "n_tx": w["n"], "n_rx": w["n"], "qam": w["qam"],
+            "detector": w["detector"], "K": w["K"] or None, "hybrid_depth": w["depth"] or None,
+            "initial_radius": "r^2 = N M sigma^2" if w["radius"] == "paper" else "none",
+            "snr_db": w["snr"], "vectors_per_step_per_gpu": w["vectors"], "global_batch": w["vectors"] * world,
+            "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
+            "l2": "inputs larger than L2 (no flush)"}
+
+
+def main():
+    args = parse()
+    w = workload_of(args)
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", str(args.gpus)))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1 and "RANK" not in os.environ:
+        raise SystemExit("for --gpus > 1 launch under torch.distributed.run")
+
+    if args.impl == "reference":
+        if world > 1:
+            import torch.distributed as dist
+
+            dist.init_process_group("gloo")
+        run_reference(args, w, rank, world)
+        if world > 1:
+            dist.barrier()
+            dist.destroy_process_group()
+        return
+
+    import torch
+
+    import __graft_entry__
+
+    __graft_entry__.build()
+    from paper_2002_09561_gb300 import mdx
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", device_id=dev)
+
+    B, n, qam = w["vectors"], w["n"], w["qam"]
+    data = generate(w, args.seed, B, start=rank * B)
+    H = torch.from_numpy(data["H"]).to(dev)
+    y = torch.from_numpy(data["y"]).to(dev)
+    nv = torch.from_numpy(data["noise_var"]).to(dev)
+    truth = torch.from_numpy(data["sym"]).to(dev)
+    ctx = mdx.Context(local, max_batch=B, max_n_rx=n, max_n_tx=n)
+    params = mdx.make_params(n, n, qam, radius=w["radius"], K=max(w["K"], 1), depth=w["depth"])
+    algo = w["detector"]
+    out = mdx._outputs(B, n, dev, True)
+    stream = torch.cuda.current_stream(dev)
+
+    def step():
+        mdx.detect(algo, ctx, params, H, y, nv, stream=stream, out=out)
+        return mdx.count_errors(ctx, out[0], truth, qam, stream=stream)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize(dev)
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize(dev)
+
+    sampler = ClockSampler(local)
+    sampler.start()
+    ctx.profile(True)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        errs = step()
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize(dev)
+    sampler.stop()
+    ms = e0.elapsed_time(e1)
+    qr_ms, search_ms, calls = ctx.profile_read()
+    ctx.profile(False)
+    if dist is not None:
+        t = torch.tensor([ms], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    value = B * world * args.steps / (ms / 1e3)
+
+    stats = out[3].cpu().numpy()
+    vst = out[2].cpu().numpy()
+    bit_err, sym_err = (int(v) for v in errs.cpu().tolist())
+    P = int(round(qam ** 0.5))
+    bits = B * n * 2 * int(round(math.log2(P)))
+
+    # dominant kernel: the tree search; algorithmic FP32 flops per launch from the
+    # kernel's own count, sum over branched nodes at row i of 2(n-1-i) + 4P
+    peaks = load_peaks()
+    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    peak = sms * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
+    flops = float(stats[:, 4].sum())
+    per_launch_s = (search_ms / max(calls, 1)) / 1e3
+    achieved = flops / per_launch_s / 1e12 if per_launch_s > 0 else 0.0
+    roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+            "traffic": None, "kernel": f"{algo} search", "search_ms_per_launch": 1e3 * per_launch_s,
+            "qr_ms_per_launch": qr_ms / max(calls, 1),
+            "peak_source": f"derived: {sms} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 x {sm_max:.0f} MHz"}
+
+    e2e = None
+    if not args.no_e2e:
+        # the same metric through the C ABI with host buffers: pinned host inputs
+        # copied in and results copied out inside the timed region
+        pin = lambda a: torch.from_numpy(a).pin_memory().numpy()  # noqa: E731
+        hH, hy, hnv = pin(data["H"]), pin(data["y"]), pin(data["noise_var"])
+        hsym = torch.empty((B, n), dtype=torch.uint8).pin_memory().numpy()
+        hmet = torch.empty(B, dtype=torch.float64).pin_memory().numpy()
+        hvst = torch.empty(B, dtype=torch.int32).pin_memory().numpy()
+        mdx.detect_host(algo, ctx, params, hH, hy, hnv, hsym, hmet, hvst, stream=stream)
+        if dist is not None:
+            dist.barrier()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            mdx.detect_host(algo, ctx, params, hH, hy, hnv, hsym, hmet, hvst, stream=stream)
+        el = time.perf_counter() - t0
+        if dist is not None:
+            t = torch.tensor([el], device=dev, dtype=torch.float64)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            el = float(t.item())
+        e2e = {"value": B * world * args.steps / el, "unit": "vectors/s",
+               "h2d_bytes_per_step": int(hH.nbytes + hy.nbytes + hnv.nbytes),
+               "d2h_bytes_per_step": int(hsym.nbytes + hmet.nbytes + hvst.nbytes)}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(w, args.seed, args.cpu_seconds, 0)
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": "vectors/s", "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f32 search, f64 QR and re-scoring",
+                "data": "synthetic (seeded Rayleigh channels, uniform QAM symbols, AWGN)",
+                "config": config_of(args, w, world), "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
+                "gpu_launches": 3 * args.steps, "clocks": sampler.summary(),
+                "quality": {"ber": bit_err / bits, "ser": sym_err / (B * n),
+                            "budget_exceeded": int((vst == 2).sum()), "radius_doublings": int((vst == 1).sum()),
+                            "mean_nodes": float(stats[:, 0].mean()), "max_nodes": int(stats[:, 0].max())}}
+        print(json.dumps(line), flush=True)
+    ctx.close()
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,185 @@
+/*
+ * mimo_detect.h -- C ABI of the GB300 (sm_103a) batched MIMO tree-search
+ * detectors: sphere decoding, K-best and the hybrid SD / K-best of
+ * "Performance/Complexity Trade-offs of the Sphere Decoder Algorithm for
+ * Massive MIMO Systems" (arXiv 2002.09561).
+ *
+ * Problem (Sec. III-A, Eq. 1): for each of `batch` independent received
+ * vectors, y = H s + n with H an n_rx x n_tx complex channel, s a vector of
+ * n_tx symbols from a unit-energy square QAM alphabet and n white noise of
+ * variance noise_var per complex entry.  Every detector first reduces the
+ * problem by a QR factorisation (Sec. III-B) and then searches the tree of
+ * Eq. 4 over the real-valued, interleaved decomposition (real index 2j is
+ * Re s_j, 2j+1 is Im s_j; rows are expanded from the last one, 2 n_tx - 1,
+ * down to 0).
+ *
+ * Memory.  Unless a call sets MDX_HOST_BUFFERS in mdx_params.flags, every
+ * array argument is a DEVICE pointer on the context's device, owned by the
+ * caller; the library never frees caller memory and never keeps a caller
+ * pointer beyond the call.  With MDX_HOST_BUFFERS, the same arguments are
+ * host pointers (pinned memory gives asynchronous copies); the library
+ * stages them through buffers it allocated in mdx_create and returns after
+ * the results are back in host memory.
+ *
+ * Layouts (all row-major, C order):
+ *   H          double [batch][n_rx][n_tx][2]   (re, im) pairs
+ *   y          double [batch][n_rx][2]
+ *   noise_var  double [batch]                  sigma^2 per complex entry
+ *   sym_out    uint8  [batch][n_tx]            complex index q = k_re*P + k_im,
+ *                                              P = sqrt(qam), PAM level
+ *                                              (2k-(P-1))*sqrt(3/(2(qam-1)))
+ *   metric_out double [batch]                  ||ybar - R s_hat||^2 in FP64
+ *   vstatus    int32  [batch]                  MDX_V_* per vector
+ *   stats      int64  [batch][5]               nodes branched, partial distances
+ *                                              evaluated, radius doublings,
+ *                                              leaves re-scored in FP64, and the
+ *                                              algorithmic FP32 flops of the search,
+ *                                              sum over branched nodes at row i of
+ *                                              2 (n-1-i) + 4 P; may be NULL
+ *
+ * Streams.  `stream` is a cudaStream_t passed as void* (NULL = the legacy
+ * default stream).  Device-pointer calls only enqueue work and return; a
+ * CUDA error raised by an earlier asynchronous launch is reported by the
+ * next call as MDX_ECUDA.  A context is not thread-safe: one host thread
+ * (or external serialisation) per context.
+ *
+ * Errors.  Every entry point validates its arguments before enqueuing
+ * anything and returns MDX_EINVAL (bad pointer, size or parameter),
+ * MDX_EUNSUPPORTED (a size beyond what the context was created for or the
+ * kernels support) or MDX_ECUDA; on any error nothing has been written to
+ * the outputs.  mdx_strerror() names a status; mdx_last_error() returns a
+ * one-line description of the last failure of this context.
+ */
+#ifndef MIMO_DETECT_H
+#define MIMO_DETECT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct mdx_ctx mdx_ctx;
+
+typedef enum {
+  MDX_OK = 0,
+  MDX_EINVAL = -1,
+  MDX_EUNSUPPORTED = -2,
+  MDX_ENOMEM = -3,
+  MDX_ECUDA = -4
+} mdx_status;
+
+/* Per-vector outcome written to vstatus. */
+enum {
+  MDX_V_OK = 0,              /* searched to completion */
+  MDX_V_EMPTY_RETRIED = 1,   /* the initial sphere held no leaf; the radius was doubled
+                                (r^2 <- 4 r^2) until one did; the answer is still exact
+                                for detect_sd */
+  MDX_V_BUDGET_EXCEEDED = 2, /* node_budget ran out; best leaf found so far (or the
+                                first leaf reached) is returned */
+  MDX_V_SINGULAR = 3         /* R has a zero diagonal entry; outputs are zero */
+};
+
+/* mdx_params.flags */
+enum {
+  MDX_HOST_BUFFERS = 1 << 0, /* array arguments are host pointers (see Memory) */
+  MDX_NO_RESCORE = 1 << 1,   /* skip the FP64 re-scoring of the final leaf candidates;
+                                metric_out is then the FP32 partial distance */
+  MDX_LEARNED_RADIUS = 1 << 2 /* initial radius from the context's MLP (mdx_mlp_load) */
+};
+
+/* Largest sizes the kernels support. */
+#define MDX_MAX_TX 100   /* n_tx (real tree depth 2*n_tx <= 200) */
+#define MDX_MAX_RX 128
+#define MDX_MAX_K 256
+
+typedef struct {
+  int n_rx;              /* N >= n_tx */
+  int n_tx;              /* M, 1 <= M <= MDX_MAX_TX */
+  int qam;               /* 4, 16 or 64 */
+  double init_radius_sq; /* initial squared radius r^2 of the sphere (Sec. III-B):
+                            INFINITY = no radius; < 0 = the paper's r^2 = N M sigma^2
+                            (per vector, from noise_var); > 0 = this value */
+  int K;                 /* survivors kept per level, 1 <= K <= MDX_MAX_K
+                            (detect_kbest, detect_hybrid) */
+  int hybrid_depth;      /* real rows explored by the hybrid's SD master (Sec. VI),
+                            0..min(2 n_tx, 12) with sqrt(qam)^depth <= 4096 */
+  long long node_budget; /* per-vector cap on branched nodes (detect_sd, detect_hybrid);
+                            0 = none */
+  int flags;             /* MDX_* flags above */
+} mdx_params;
+
+/* Context: selects `device`, allocates the workspace for up to max_batch
+ * vectors of at most max_n_rx x max_n_tx (QR outputs, candidate buffers and
+ * host-staging buffers).  No later call allocates device memory.
+ * Returns MDX_ENOMEM if the workspace does not fit. */
+mdx_status mdx_create(mdx_ctx** ctx, int device, int max_batch, int max_n_rx, int max_n_tx);
+mdx_status mdx_destroy(mdx_ctx* ctx);
+const char* mdx_strerror(mdx_status s);
+const char* mdx_last_error(const mdx_ctx* ctx);
+/* Bytes of device workspace this context holds. */
+size_t mdx_workspace_bytes(const mdx_ctx* ctx);
+
+/* QR preprocessing alone (Sec. III-B): H = Q R with a real positive diagonal,
+ * ybar = Q^H y, both returned in the real interleaved form of size n = 2 n_tx.
+ *   R_out    double [batch][n][n], row-major, zero below the diagonal
+ *   ybar_out double [batch][n]
+ * Computed in FP64 (complex Householder reflections). */
+mdx_status mdx_qr(mdx_ctx* ctx, int batch, int n_rx, int n_tx, const double* H, const double* y,
+                  double* R_out, double* ybar_out, int flags, void* stream);
+
+/* Exact sphere decoder (Sec. III-B, Algorithm 1) with the Best-FS /
+ * Schnorr-Euchner order (Sec. IV-A) and incremental partial distances
+ * (Sec. IV-C, Eq. inc): depth-first, children visited in increasing partial
+ * distance, a child is pruned when its partial distance is >= r^2, and every
+ * leaf reached shrinks r^2 to its distance.  Partial distances are FP32 with
+ * a small pruning slack; the final leaf candidates are re-scored in FP64, so
+ * the answer is the maximum-likelihood point of Eq. 2 (up to FP64 ties).
+ * Uses p->init_radius_sq, p->node_budget, p->flags. */
+mdx_status detect_sd(mdx_ctx* ctx, const mdx_params* p, int batch, const double* H,
+                     const double* y, const double* noise_var, uint8_t* sym_out,
+                     double* metric_out, int32_t* vstatus, int64_t* stats, void* stream);
+
+/* K-best (Sec. VI): breadth-first; at every row all children of the
+ * surviving nodes are evaluated and the K with the smallest partial distance
+ * (among those inside the radius, if one is given) survive; the best final
+ * leaf is returned.  FP32 partial distances, FP64 re-scoring of the final
+ * candidates.  Uses p->K, p->init_radius_sq, p->flags. */
+mdx_status detect_kbest(mdx_ctx* ctx, const mdx_params* p, int batch, const double* H,
+                        const double* y, const double* noise_var, uint8_t* sym_out,
+                        double* metric_out, int32_t* vstatus, int64_t* stats, void* stream);
+
+/* Hybrid SD / K-best (Sec. VI): a Best-FS sphere decoder explores the top
+ * p->hybrid_depth rows; every node it reaches at that depth inside the
+ * current sphere is finished by a K-best(p->K) worker that prunes with the
+ * shared, shrinking radius, stops when all its survivors leave the sphere and
+ * shrinks the radius with its best leaf.  The result equals the best K-best
+ * leaf over all depth-d prefixes inside the initial sphere, independent of the
+ * order in which workers take them.  Uses p->K, p->hybrid_depth,
+ * p->init_radius_sq, p->node_budget, p->flags. */
+mdx_status detect_hybrid(mdx_ctx* ctx, const mdx_params* p, int batch, const double* H,
+                         const double* y, const double* noise_var, uint8_t* sym_out,
+                         double* metric_out, int32_t* vstatus, int64_t* stats, void* stream);
+
+/* Bit and symbol errors of detected against transmitted indices (the error
+ * rates plotted in Sec. VII), with a Gray code per PAM dimension of
+ * q = k_re*P + k_im.  counts_out int64[2] = {bit errors, symbol errors},
+ * overwritten (not accumulated). */
+mdx_status mdx_count_errors(mdx_ctx* ctx, int batch, int n_tx, int qam, const uint8_t* sym_hat,
+                            const uint8_t* sym_true, int64_t* counts_out, int flags,
+                            void* stream);
+
+/* Kernel timing for benchmarks.  While enabled, every call records CUDA
+ * events on its stream around the QR kernel and the search kernel (up to
+ * 1024 calls are kept).  mdx_profile_read waits for those events, writes
+ * ms_out[0] = summed QR time, ms_out[1] = summed search time (milliseconds),
+ * ms_out[2] = number of calls recorded, and clears the record.  Not part of
+ * the detection path; enable = 0 turns it off. */
+mdx_status mdx_profile(mdx_ctx* ctx, int enable);
+mdx_status mdx_profile_read(mdx_ctx* ctx, double* ms_out);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

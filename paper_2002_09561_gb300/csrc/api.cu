@@ -1,0 +1,484 @@
+// C ABI of libmdx (include/mimo_detect.h): context and workspace, argument
+// checks, host staging, and the launch sequence QR -> search -> FP64
+// re-scoring of every detect_* call.  Also the Gray-coded error counter.
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include "mdx_internal.cuh"
+
+struct mdx_ctx {
+  int device = 0;
+  int num_sms = 0;
+  int max_batch = 0, max_rx = 0, max_tx = 0;
+  size_t bytes = 0;
+  // QR outputs and search scratch
+  double* R64 = nullptr;
+  double* yb64 = nullptr;
+  float* R32 = nullptr;
+  float* yb32 = nullptr;
+  int* singular = nullptr;
+  unsigned int* counter = nullptr;
+  unsigned long long* counts = nullptr;
+  // staging for MDX_HOST_BUFFERS
+  double* sH = nullptr;
+  double* sy = nullptr;
+  double* snv = nullptr;
+  uint8_t* ssym = nullptr;
+  uint8_t* ssym2 = nullptr;
+  double* smet = nullptr;
+  int32_t* svst = nullptr;
+  int64_t* sstats = nullptr;
+  // optional kernel timing (mdx_profile)
+  static constexpr int kProfSlots = 1024;
+  bool prof = false;
+  int prof_n = 0;
+  cudaEvent_t prof_ev[kProfSlots][3] = {};
+  char err[320] = {0};
+};
+
+namespace {
+
+using namespace mdx;
+
+mdx_status fail(mdx_ctx* c, mdx_status s, const char* fmt, ...) {
+  if (c) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(c->err, sizeof(c->err), fmt, ap);
+    va_end(ap);
+  }
+  return s;
+}
+
+mdx_status cuda_fail(mdx_ctx* c, cudaError_t e, const char* where) {
+  return fail(c, MDX_ECUDA, "%s: %s", where, cudaGetErrorString(e));
+}
+
+// Switches to the context's device for the lifetime of the guard.
+struct DeviceGuard {
+  int prev = -1;
+  explicit DeviceGuard(int dev) {
+    if (cudaGetDevice(&prev) == cudaSuccess && prev != dev) cudaSetDevice(dev);
+    else prev = -1;
+  }
+  ~DeviceGuard() {
+    if (prev >= 0) cudaSetDevice(prev);
+  }
+};
+
+int pam_of(int qam) {
+  switch (qam) {
+    case 4: return 2;
+    case 16: return 4;
+    case 64: return 8;
+    default: return -1;
+  }
+}
+
+bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
+
+// True when p is memory the device can address (device or managed memory).
+bool is_device_ptr(const void* p, int device) {
+  cudaPointerAttributes at;
+  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  if (at.type == cudaMemoryTypeManaged) return true;
+  return at.type == cudaMemoryTypeDevice && at.device == device;
+}
+
+template <typename T>
+cudaError_t alloc(mdx_ctx* c, T** p, size_t count) {
+  const size_t b = sizeof(T) * (count ? count : 1);
+  cudaError_t e = cudaMalloc(reinterpret_cast<void**>(p), b);
+  if (e == cudaSuccess) c->bytes += b;
+  return e;
+}
+
+void free_all(mdx_ctx* c) {
+  for (int i = 0; i < mdx_ctx::kProfSlots; ++i)
+    for (int k = 0; k < 3; ++k)
+      if (c->prof_ev[i][k]) cudaEventDestroy(c->prof_ev[i][k]);
+  void* ptrs[] = {c->R64, c->yb64, c->R32, c->yb32, c->singular, c->counter, c->counts,
+                  c->sH,  c->sy,   c->snv, c->ssym, c->ssym2,    c->smet,    c->svst,
+                  c->sstats};
+  for (void* p : ptrs)
+    if (p) cudaFree(p);
+}
+
+enum Algo { ALGO_SD = 0, ALGO_KBEST = 1, ALGO_HYBRID = 2 };
+
+size_t kbest_layout_bytes(int n, int K, int P, int keys_cap) {
+  // mirrors KbLayout::init in kbest.cu
+  int w = round_up(n, 4) / 4;
+  if ((w & 1) == 0) ++w;
+  const size_t pp = 4 * (size_t)w;
+  size_t o = sizeof(uint64_t) * keys_cap + sizeof(float) * tri_stride32(n) +
+             sizeof(float) * round_up(n, 4) + 2 * sizeof(float) * round_up(K, 4) +
+             sizeof(float) * 8 + 64 + pp * (2 * (size_t)K + 8);
+  return (size_t)round_up((int)o, 16);
+}
+
+mdx_status run_detect(int algo, mdx_ctx* c, const mdx_params* p, int batch, const double* H,
+                      const double* y, const double* nv, uint8_t* sym, double* met, int32_t* vst,
+                      int64_t* stats, void* stream) {
+  if (!c) return MDX_EINVAL;
+  if (!p) return fail(c, MDX_EINVAL, "params is NULL");
+  if (batch < 0) return fail(c, MDX_EINVAL, "batch %d < 0", batch);
+  if (batch == 0) return MDX_OK;
+  if (batch > c->max_batch)
+    return fail(c, MDX_EUNSUPPORTED, "batch %d > context max_batch %d", batch, c->max_batch);
+  const int M = p->n_tx, N = p->n_rx, P = pam_of(p->qam);
+  if (M < 1 || N < M) return fail(c, MDX_EINVAL, "need n_rx >= n_tx >= 1 (got %d, %d)", N, M);
+  if (M > c->max_tx || N > c->max_rx)
+    return fail(c, MDX_EUNSUPPORTED, "%dx%d exceeds the context's %dx%d", N, M, c->max_rx, c->max_tx);
+  if (P < 0) return fail(c, MDX_EINVAL, "qam %d not in {4, 16, 64}", p->qam);
+  const int n = 2 * M;
+  const double r0 = p->init_radius_sq;
+  if (isnan(r0) || r0 == 0.0) return fail(c, MDX_EINVAL, "init_radius_sq must be > 0, < 0 or INFINITY");
+  int radius_mode = isinf(r0) ? (r0 > 0 ? RADIUS_NONE : RADIUS_PAPER) : (r0 < 0 ? RADIUS_PAPER : RADIUS_VALUE);
+  if (p->flags & MDX_LEARNED_RADIUS)
+    return fail(c, MDX_EUNSUPPORTED, "MDX_LEARNED_RADIUS needs a loaded model");
+  if (p->node_budget < 0) return fail(c, MDX_EINVAL, "node_budget < 0");
+  if (algo != ALGO_SD) {
+    if (p->K < 1 || p->K > MDX_MAX_K) return fail(c, MDX_EINVAL, "K %d not in 1..%d", p->K, MDX_MAX_K);
+  }
+  int keys_cap = pow2ceil(algo == ALGO_SD ? 2 : p->K * P);
+  if (algo == ALGO_HYBRID) {
+    const int d = p->hybrid_depth;
+    if (d < 0 || d > n || d > 12) return fail(c, MDX_EINVAL, "hybrid_depth %d not in 0..min(n, 12)", d);
+    long long np = 1;
+    for (int l = 0; l < d; ++l) np *= P;
+    if (np > 4096) return fail(c, MDX_EUNSUPPORTED, "P^depth = %lld > 4096 prefixes", np);
+    keys_cap += pow2ceil(np < 2 ? 2 : (int)np);
+  }
+  if (algo != ALGO_SD && kbest_layout_bytes(n, p->K, P, keys_cap) > 227 * 1024)
+    return fail(c, MDX_EUNSUPPORTED, "K=%d at n=%d, P=%d needs more than 227 KB of shared memory", p->K,
+                n, P);
+  const bool host = (p->flags & MDX_HOST_BUFFERS) != 0;
+  if (!H || !y || !sym || !met || !vst) return fail(c, MDX_EINVAL, "NULL input or output pointer");
+  if (radius_mode == RADIUS_PAPER && !nv) return fail(c, MDX_EINVAL, "noise_var needed for the paper radius");
+  if (!host) {
+    if (!aligned16(H) || !aligned16(y)) return fail(c, MDX_EINVAL, "H and y must be 16-byte aligned");
+    const void* ptrs[] = {H, y, sym, met, vst};
+    for (const void* q : ptrs)
+      if (!is_device_ptr(q, c->device))
+        return fail(c, MDX_EINVAL, "pointer %p is not device memory of device %d", q, c->device);
+    if (nv && !is_device_ptr(nv, c->device)) return fail(c, MDX_EINVAL, "noise_var is not device memory");
+    if (stats && !is_device_ptr(stats, c->device)) return fail(c, MDX_EINVAL, "stats is not device memory");
+  }
+
+  DeviceGuard g(c->device);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail(c, e, "earlier asynchronous error");
+
+  const double* dH = H;
+  const double* dy = y;
+  const double* dnv = nv;
+  uint8_t* dsym = sym;
+  double* dmet = met;
+  int32_t* dvst = vst;
+  int64_t* dstats = stats;
+  if (host) {
+    e = cudaMemcpyAsync(c->sH, H, sizeof(double) * 2 * (size_t)batch * N * M, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(c->sy, y, sizeof(double) * 2 * (size_t)batch * N, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess && nv)
+      e = cudaMemcpyAsync(c->snv, nv, sizeof(double) * batch, cudaMemcpyHostToDevice, s);
+    if (e != cudaSuccess) return cuda_fail(c, e, "host-to-device staging");
+    dH = c->sH;
+    dy = c->sy;
+    dnv = nv ? c->snv : nullptr;
+    dsym = c->ssym;
+    dmet = c->smet;
+    dvst = c->svst;
+    dstats = stats ? c->sstats : nullptr;
+  }
+
+  cudaEvent_t* ev = nullptr;
+  if (c->prof && c->prof_n < mdx_ctx::kProfSlots) {
+    ev = c->prof_ev[c->prof_n++];
+    cudaEventRecord(ev[0], s);
+  }
+  QrOut q{c->R64, c->yb64, c->R32, c->yb32, nullptr, nullptr, c->singular};
+  e = launch_qr(batch, N, M, dH, dy, q, s);
+  if (e != cudaSuccess) return cuda_fail(c, e, "QR launch");
+
+  SearchArgs a{};
+  a.batch = batch;
+  a.n = n;
+  a.P = P;
+  a.n_rx = N;
+  a.n_tx = M;
+  a.alpha64 = sqrt(3.0 / (2.0 * (p->qam - 1)));
+  a.alpha = (float)a.alpha64;
+  a.R32 = c->R32;
+  a.yb32 = c->yb32;
+  a.R64 = c->R64;
+  a.yb64 = c->yb64;
+  a.singular = c->singular;
+  a.noise_var = dnv;
+  a.r2_vec = nullptr;
+  a.radius_mode = radius_mode;
+  a.radius_value = r0;
+  a.K = p->K;
+  a.depth = p->hybrid_depth;
+  a.budget = p->node_budget;
+  a.flags = p->flags;
+  a.work_counter = c->counter;
+  a.sym_out = dsym;
+  a.metric_out = dmet;
+  a.vstatus = dvst;
+  a.stats = dstats;
+  e = cudaMemsetAsync(c->counter, 0, sizeof(unsigned int), s);
+  if (e != cudaSuccess) return cuda_fail(c, e, "work counter reset");
+  if (ev) cudaEventRecord(ev[1], s);
+  if (algo == ALGO_SD) e = launch_sd(a, c->num_sms, s);
+  else if (algo == ALGO_KBEST) e = launch_kbest(a, c->num_sms, s);
+  else e = launch_hybrid(a, c->num_sms, s);
+  if (e == cudaErrorInvalidConfiguration)
+    return fail(c, MDX_EUNSUPPORTED, "no launch configuration fits this size");
+  if (e != cudaSuccess) return cuda_fail(c, e, "search launch");
+  if (ev) cudaEventRecord(ev[2], s);
+
+  if (host) {
+    e = cudaMemcpyAsync(sym, c->ssym, (size_t)batch * M, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(met, c->smet, sizeof(double) * batch, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(vst, c->svst, sizeof(int32_t) * batch, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess && stats)
+      e = cudaMemcpyAsync(stats, c->sstats, sizeof(int64_t) * kStats * (size_t)batch, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_fail(c, e, "device-to-host results");
+  }
+  return MDX_OK;
+}
+
+// Gray-coded bit errors and symbol errors, one thread per symbol.
+__global__ void count_errors_kernel(long long total, int P, const uint8_t* __restrict__ a,
+                                    const uint8_t* __restrict__ b, unsigned long long* counts) {
+  unsigned long long be = 0, se = 0;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
+       t += (long long)gridDim.x * blockDim.x) {
+    const int x = a[t], z = b[t];
+    se += (x != z);
+    const int xr = x / P, xi = x % P, zr = z / P, zi = z % P;
+    be += __popc((xr ^ (xr >> 1)) ^ (zr ^ (zr >> 1))) + __popc((xi ^ (xi >> 1)) ^ (zi ^ (zi >> 1)));
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    be += __shfl_xor_sync(0xffffffffu, be, o);
+    se += __shfl_xor_sync(0xffffffffu, se, o);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    atomicAdd(&counts[0], be);
+    atomicAdd(&counts[1], se);
+  }
+}
+
+}  // namespace
+
+namespace mdx {
+cudaError_t launch_count_errors(int batch, int n_tx, int qam, const uint8_t* a, const uint8_t* b,
+                                unsigned long long* counts, cudaStream_t s) {
+  const long long total = (long long)batch * n_tx;
+  int grid = (int)((total + 255) / 256);
+  if (grid > 4096) grid = 4096;
+  if (grid < 1) grid = 1;
+  count_errors_kernel<<<grid, 256, 0, s>>>(total, pam_of(qam), a, b, counts);
+  return cudaGetLastError();
+}
+}  // namespace mdx
+
+extern "C" {
+
+const char* mdx_strerror(mdx_status s) {
+  switch (s) {
+    case MDX_OK: return "ok";
+    case MDX_EINVAL: return "invalid argument";
+    case MDX_EUNSUPPORTED: return "unsupported size or parameter";
+    case MDX_ENOMEM: return "out of device memory";
+    case MDX_ECUDA: return "CUDA error";
+  }
+  return "unknown status";
+}
+
+const char* mdx_last_error(const mdx_ctx* ctx) { return ctx ? ctx->err : "no context"; }
+
+size_t mdx_workspace_bytes(const mdx_ctx* ctx) { return ctx ? ctx->bytes : 0; }
+
+mdx_status mdx_create(mdx_ctx** out, int device, int max_batch, int max_n_rx, int max_n_tx) {
+  if (!out) return MDX_EINVAL;
+  *out = nullptr;
+  if (max_batch < 1 || max_n_tx < 1 || max_n_rx < max_n_tx || max_n_tx > MDX_MAX_TX ||
+      max_n_rx > MDX_MAX_RX)
+    return MDX_EINVAL;
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) {
+    cudaGetLastError();
+    return MDX_EINVAL;
+  }
+  mdx_ctx* c = new mdx_ctx();
+  c->device = device;
+  c->max_batch = max_batch;
+  c->max_rx = max_n_rx;
+  c->max_tx = max_n_tx;
+  DeviceGuard g(device);
+  cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, device);
+  const size_t B = (size_t)max_batch;
+  const int n = 2 * max_n_tx;
+  cudaError_t e = cudaSuccess;
+  auto chk = [&](cudaError_t r) {
+    if (e == cudaSuccess) e = r;
+  };
+  chk(alloc(c, &c->R64, B * tri_stride64(n)));
+  chk(alloc(c, &c->yb64, B * vec_stride64(n)));
+  chk(alloc(c, &c->R32, B * tri_stride32(n)));
+  chk(alloc(c, &c->yb32, B * vec_stride32(n)));
+  chk(alloc(c, &c->singular, B));
+  chk(alloc(c, &c->counter, 4));
+  chk(alloc(c, &c->counts, 2));
+  chk(alloc(c, &c->sH, B * max_n_rx * max_n_tx * 2));
+  chk(alloc(c, &c->sy, B * max_n_rx * 2));
+  chk(alloc(c, &c->snv, B));
+  chk(alloc(c, &c->ssym, B * max_n_tx));
+  chk(alloc(c, &c->ssym2, B * max_n_tx));
+  chk(alloc(c, &c->smet, B));
+  chk(alloc(c, &c->svst, B));
+  chk(alloc(c, &c->sstats, B * kStats));
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    free_all(c);
+    delete c;
+    return MDX_ENOMEM;
+  }
+  *out = c;
+  return MDX_OK;
+}
+
+mdx_status mdx_destroy(mdx_ctx* ctx) {
+  if (!ctx) return MDX_EINVAL;
+  DeviceGuard g(ctx->device);
+  free_all(ctx);
+  delete ctx;
+  return MDX_OK;
+}
+
+mdx_status mdx_qr(mdx_ctx* c, int batch, int n_rx, int n_tx, const double* H, const double* y,
+                  double* R_out, double* ybar_out, int flags, void* stream) {
+  if (!c) return MDX_EINVAL;
+  if (flags & MDX_HOST_BUFFERS) return fail(c, MDX_EUNSUPPORTED, "mdx_qr takes device pointers only");
+  if (batch < 0) return fail(c, MDX_EINVAL, "batch < 0");
+  if (batch == 0) return MDX_OK;
+  if (n_tx < 1 || n_rx < n_tx) return fail(c, MDX_EINVAL, "need n_rx >= n_tx >= 1");
+  if (n_tx > MDX_MAX_TX || n_rx > MDX_MAX_RX) return fail(c, MDX_EUNSUPPORTED, "size beyond %dx%d", MDX_MAX_RX, MDX_MAX_TX);
+  if (!H || !y || !R_out || !ybar_out) return fail(c, MDX_EINVAL, "NULL pointer");
+  if (!aligned16(H) || !aligned16(y)) return fail(c, MDX_EINVAL, "H and y must be 16-byte aligned");
+  const void* ptrs[] = {H, y, R_out, ybar_out};
+  for (const void* q : ptrs)
+    if (!is_device_ptr(q, c->device)) return fail(c, MDX_EINVAL, "pointer %p is not device memory", q);
+  DeviceGuard g(c->device);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail(c, e, "earlier asynchronous error");
+  QrOut q{nullptr, nullptr, nullptr, nullptr, R_out, ybar_out, nullptr};
+  e = launch_qr(batch, n_rx, n_tx, H, y, q, static_cast<cudaStream_t>(stream));
+  if (e != cudaSuccess) return cuda_fail(c, e, "QR launch");
+  return MDX_OK;
+}
+
+mdx_status detect_sd(mdx_ctx* ctx, const mdx_params* p, int batch, const double* H, const double* y,
+                     const double* noise_var, uint8_t* sym_out, double* metric_out, int32_t* vstatus,
+                     int64_t* stats, void* stream) {
+  return run_detect(ALGO_SD, ctx, p, batch, H, y, noise_var, sym_out, metric_out, vstatus, stats, stream);
+}
+
+mdx_status detect_kbest(mdx_ctx* ctx, const mdx_params* p, int batch, const double* H,
+                        const double* y, const double* noise_var, uint8_t* sym_out,
+                        double* metric_out, int32_t* vstatus, int64_t* stats, void* stream) {
+  return run_detect(ALGO_KBEST, ctx, p, batch, H, y, noise_var, sym_out, metric_out, vstatus, stats,
+                    stream);
+}
+
+mdx_status detect_hybrid(mdx_ctx* ctx, const mdx_params* p, int batch, const double* H,
+                         const double* y, const double* noise_var, uint8_t* sym_out,
+                         double* metric_out, int32_t* vstatus, int64_t* stats, void* stream) {
+  return run_detect(ALGO_HYBRID, ctx, p, batch, H, y, noise_var, sym_out, metric_out, vstatus, stats,
+                    stream);
+}
+
+mdx_status mdx_count_errors(mdx_ctx* c, int batch, int n_tx, int qam, const uint8_t* sym_hat,
+                            const uint8_t* sym_true, int64_t* counts_out, int flags, void* stream) {
+  if (!c) return MDX_EINVAL;
+  if (batch < 0 || n_tx < 1) return fail(c, MDX_EINVAL, "bad batch or n_tx");
+  if (pam_of(qam) < 0) return fail(c, MDX_EINVAL, "qam %d not in {4, 16, 64}", qam);
+  if (!sym_hat || !sym_true || !counts_out) return fail(c, MDX_EINVAL, "NULL pointer");
+  const bool host = (flags & MDX_HOST_BUFFERS) != 0;
+  if (host && ((size_t)batch > (size_t)c->max_batch || n_tx > c->max_tx))
+    return fail(c, MDX_EUNSUPPORTED, "batch beyond the staging buffers");
+  if (!host) {
+    const void* ptrs[] = {sym_hat, sym_true, counts_out};
+    for (const void* q : ptrs)
+      if (!is_device_ptr(q, c->device)) return fail(c, MDX_EINVAL, "pointer %p is not device memory", q);
+  }
+  DeviceGuard g(c->device);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail(c, e, "earlier asynchronous error");
+  const uint8_t* a = sym_hat;
+  const uint8_t* b = sym_true;
+  if (host) {
+    e = cudaMemcpyAsync(c->ssym, sym_hat, (size_t)batch * n_tx, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(c->ssym2, sym_true, (size_t)batch * n_tx, cudaMemcpyHostToDevice, s);
+    if (e != cudaSuccess) return cuda_fail(c, e, "staging");
+    a = c->ssym;
+    b = c->ssym2;
+  }
+  e = cudaMemsetAsync(c->counts, 0, 2 * sizeof(unsigned long long), s);
+  if (e == cudaSuccess && batch > 0) e = launch_count_errors(batch, n_tx, qam, a, b, c->counts, s);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(counts_out, c->counts, 2 * sizeof(int64_t),
+                        host ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice, s);
+  if (e == cudaSuccess && host) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return cuda_fail(c, e, "error count");
+  return MDX_OK;
+}
+
+mdx_status mdx_profile(mdx_ctx* c, int enable) {
+  if (!c) return MDX_EINVAL;
+  DeviceGuard g(c->device);
+  if (enable && !c->prof_ev[0][0]) {
+    for (int i = 0; i < mdx_ctx::kProfSlots; ++i)
+      for (int k = 0; k < 3; ++k) {
+        cudaError_t e = cudaEventCreate(&c->prof_ev[i][k]);
+        if (e != cudaSuccess) return cuda_fail(c, e, "event create");
+      }
+  }
+  c->prof = enable != 0;
+  c->prof_n = 0;
+  return MDX_OK;
+}
+
+mdx_status mdx_profile_read(mdx_ctx* c, double* ms_out) {
+  if (!c || !ms_out) return MDX_EINVAL;
+  DeviceGuard g(c->device);
+  double qr = 0.0, search = 0.0;
+  for (int i = 0; i < c->prof_n; ++i) {
+    cudaError_t e = cudaEventSynchronize(c->prof_ev[i][2]);
+    if (e != cudaSuccess) return cuda_fail(c, e, "event sync");
+    float a = 0.f, b = 0.f;
+    cudaEventElapsedTime(&a, c->prof_ev[i][0], c->prof_ev[i][1]);
+    cudaEventElapsedTime(&b, c->prof_ev[i][1], c->prof_ev[i][2]);
+    qr += a;
+    search += b;
+  }
+  ms_out[0] = qr;
+  ms_out[1] = search;
+  ms_out[2] = c->prof_n;
+  c->prof_n = 0;
+  return MDX_OK;
+}
+
+}  // extern "C"

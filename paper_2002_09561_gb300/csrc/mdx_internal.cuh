@@ -1,0 +1,158 @@
+// Internal declarations shared by the CUDA translation units of libmdx.
+// Device-side data layout (per received vector b, real dimension n = 2 n_tx):
+//   R (upper triangular, n x n) is stored column-packed: column c holds rows
+//   0..c contiguously at offset c (c + 1) / 2, so the entries a row update
+//   needs (column c, rows below the current level) are contiguous and the
+//   diagonal R_cc sits at the end of its column.  The per-vector stride is
+//   rounded up to 16 bytes (tri_stride32 / tri_stride64).
+//   ybar has n entries per vector (stride n rounded up to 16 bytes).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "mimo_detect.h"
+
+#define MDX_MAX_N (2 * MDX_MAX_TX)
+
+namespace mdx {
+
+__host__ __device__ __forceinline__ int col_off(int c) { return c * (c + 1) / 2; }
+__host__ __device__ __forceinline__ int tri(int n) { return n * (n + 1) / 2; }
+__host__ __device__ __forceinline__ int round_up(int x, int m) { return (x + m - 1) / m * m; }
+__host__ __device__ __forceinline__ int tri_stride32(int n) { return round_up(tri(n), 4); }
+__host__ __device__ __forceinline__ int tri_stride64(int n) { return round_up(tri(n), 2); }
+__host__ __device__ __forceinline__ int vec_stride32(int n) { return round_up(n, 4); }
+__host__ __device__ __forceinline__ int vec_stride64(int n) { return round_up(n, 2); }
+
+// Per-vector statistics slots (nodes, peds, restarts, rescored, flops).
+constexpr int kStats = 5;
+
+// Radius modes derived from mdx_params.init_radius_sq.
+enum { RADIUS_NONE = 0, RADIUS_PAPER = 1, RADIUS_VALUE = 2, RADIUS_PER_VECTOR = 3 };
+
+// Outputs of the QR kernel (any pointer may be null).
+struct QrOut {
+  double* R64;      // column-packed, stride tri_stride64(n)
+  double* yb64;     // stride vec_stride64(n)
+  float* R32;       // column-packed, stride tri_stride32(n)
+  float* yb32;      // stride vec_stride32(n)
+  double* Rdense;   // [n][n] row-major (mdx_qr)
+  double* ybdense;  // [n]
+  int* singular;    // [batch] 1 if a diagonal entry of R is zero
+};
+
+// Everything the search kernels read and write for one launch.
+struct SearchArgs {
+  int batch, n, P, n_rx, n_tx;
+  float alpha;    // PAM spacing factor sqrt(3 / (2 (qam - 1)))
+  double alpha64;
+  const float* R32;
+  const float* yb32;
+  const double* R64;
+  const double* yb64;
+  const int* singular;
+  const double* noise_var;
+  const float* r2_vec;  // per-vector initial r^2 (RADIUS_PER_VECTOR), else null
+  int radius_mode;
+  double radius_value;
+  int K;
+  int depth;           // hybrid master depth
+  long long budget;    // per-vector branched-node cap, 0 = none
+  int flags;
+  unsigned int* work_counter;  // dynamic vector queue (zeroed before launch)
+  uint8_t* sym_out;
+  double* metric_out;
+  int32_t* vstatus;
+  int64_t* stats;
+};
+
+cudaError_t launch_qr(int batch, int n_rx, int n_tx, const double* H, const double* y, QrOut out,
+                      cudaStream_t s);
+cudaError_t launch_sd(const SearchArgs& a, int num_sms, cudaStream_t s);
+cudaError_t launch_kbest(const SearchArgs& a, int num_sms, cudaStream_t s);
+cudaError_t launch_hybrid(const SearchArgs& a, int num_sms, cudaStream_t s);
+cudaError_t launch_count_errors(int batch, int n_tx, int qam, const uint8_t* a, const uint8_t* b,
+                                unsigned long long* counts, cudaStream_t s);
+
+// ---------------------------------------------------------------------------------------
+// Device helpers shared by the search kernels.
+
+// FP32 rounding unit.
+constexpr float kU32 = 5.9604645e-8f;
+
+// Bound under which an FP32 partial distance may still belong to a point
+// whose exact distance is below r2.  E is the per-vector error scale
+// u * sqrt(sum_i ((n - i + 1) T_i)^2) with T_i = |ybar_i| + a_max sum_j |R_ij|:
+// the absolute error of an FP32 partial distance D is at most about
+// 2 sqrt(D) E + 2 n u D (first-order bound of the FMA chains).
+__device__ __forceinline__ float prune_bound(float r2, float E, int n) {
+  if (!(r2 < INFINITY)) return INFINITY;
+  return r2 + 4.0f * sqrtf(r2) * E + 4.0f * (float)n * kU32 * r2;
+}
+
+__device__ __forceinline__ float warp_sum(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+}  // namespace mdx
+
+namespace mdx {
+
+// ||ybar - R x||^2 in FP64 for the PAM-index path x (n <= 224), computed by
+// the calling warp (all 32 lanes) column by column: lane l accumulates the
+// residual of rows l, l+32, ...  Every lane returns the same value.
+__device__ __forceinline__ double rescore_fp64_warp(int n, int P, double alpha64,
+                                                     const double* __restrict__ R64,
+                                                     const double* __restrict__ y64,
+                                                     const uint8_t* x, int lane) {
+  double rr[7];
+#pragma unroll
+  for (int t = 0; t < 7; ++t) {
+    const int r = lane + 32 * t;
+    rr[t] = (r < n) ? y64[r] : 0.0;
+  }
+  for (int j = 0; j < n; ++j) {
+    const double xj = (double)(2 * (int)x[j] - (P - 1)) * alpha64;
+    const double* col = R64 + col_off(j);
+#pragma unroll
+    for (int t = 0; t < 7; ++t) {
+      const int r = lane + 32 * t;
+      if (r <= j) rr[t] = fma(-col[r], xj, rr[t]);
+    }
+  }
+  double s = 0.0;
+#pragma unroll
+  for (int t = 0; t < 7; ++t) s = fma(rr[t], rr[t], s);
+  return __shfl_sync(0xffffffffu, warp_sum(s), 0);
+}
+
+// FP32 error scale E of one vector (see prune_bound), computed by one warp
+// from the FP32 R (column-packed, shared memory) and ybar.
+__device__ __forceinline__ float error_scale_warp(int n, int P, float alpha, const float* Rc,
+                                                  const float* yb, int lane) {
+  const float amax = alpha * (float)(P - 1);
+  float e2 = 0.0f;
+  for (int r = lane; r < n; r += 32) {
+    float T = fabsf(yb[r]);
+    for (int j = r; j < n; ++j) T += amax * fabsf(Rc[col_off(j) + r]);
+    const float w = (float)(n - r + 1) * T;
+    e2 += w * w;
+  }
+  return __shfl_sync(0xffffffffu, sqrtf(warp_sum(e2)) * kU32, 0);
+}
+
+__host__ __device__ __forceinline__ int pow2ceil(int x) {
+  int p = 1;
+  while (p < x) p <<= 1;
+  return p;
+}
+
+}  // namespace mdx

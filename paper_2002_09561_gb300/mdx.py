@@ -1,0 +1,229 @@
+"""Thin Python binding of libmdx (include/mimo_detect.h).
+
+Argument marshalling only: every step of detection runs in the CUDA library.
+The raw entry points take integer addresses; the helpers below take torch
+CUDA tensors (torch is used for device memory and streams) or numpy arrays in
+pinned host memory (MDX_HOST_BUFFERS).  There is no CPU fallback: if the
+library is missing or no GPU is present, every call raises.
+"""
+
+from __future__ import annotations
+
+import ctypes
+import math
+import os
+import threading
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libmdx.so")
+
+MDX_OK, MDX_EINVAL, MDX_EUNSUPPORTED, MDX_ENOMEM, MDX_ECUDA = 0, -1, -2, -3, -4
+MDX_V_OK, MDX_V_EMPTY_RETRIED, MDX_V_BUDGET_EXCEEDED, MDX_V_SINGULAR = 0, 1, 2, 3
+MDX_HOST_BUFFERS, MDX_NO_RESCORE, MDX_LEARNED_RADIUS = 1, 2, 4
+MDX_MAX_TX, MDX_MAX_RX, MDX_MAX_K = 100, 128, 256
+
+# Every symbol the header declares; the library must export all of them.
+EXPORTS = ["mdx_create", "mdx_destroy", "mdx_strerror", "mdx_last_error", "mdx_workspace_bytes",
+           "mdx_qr", "detect_sd", "detect_kbest", "detect_hybrid", "mdx_count_errors",
+           "mdx_profile", "mdx_profile_read"]
+STATS = 5  # per-vector stats: nodes, peds, restarts, rescored, algorithmic FP32 flops
+
+
+class MdxError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{msg} (status {status})")
+        self.status = status
+
+
+class Params(ctypes.Structure):
+    _fields_ = [("n_rx", ctypes.c_int), ("n_tx", ctypes.c_int), ("qam", ctypes.c_int),
+                ("init_radius_sq", ctypes.c_double), ("K", ctypes.c_int),
+                ("hybrid_depth", ctypes.c_int), ("node_budget", ctypes.c_longlong),
+                ("flags", ctypes.c_int)]
+
+
+def make_params(n_rx, n_tx, qam, radius=math.inf, K=16, depth=4, budget=0, flags=0) -> Params:
+    """radius: float r^2 (inf = none) or 'paper' for r^2 = N M sigma^2."""
+    r = -1.0 if isinstance(radius, str) else float(radius)
+    return Params(int(n_rx), int(n_tx), int(qam), r, int(K), int(depth), int(budget), int(flags))
+
+
+_lock = threading.Lock()
+_lib = None
+
+
+def lib():
+    """Load libmdx.so (raises if it has not been built)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(LIB_PATH):
+                raise MdxError(MDX_ECUDA, f"{LIB_PATH} is missing: run __graft_entry__.build()")
+            L = ctypes.CDLL(LIB_PATH)
+            vp, i, ll = ctypes.c_void_p, ctypes.c_int, ctypes.c_longlong
+            L.mdx_create.argtypes = [ctypes.POINTER(vp), i, i, i, i]
+            L.mdx_create.restype = i
+            L.mdx_destroy.argtypes = [vp]
+            L.mdx_destroy.restype = i
+            L.mdx_strerror.argtypes = [i]
+            L.mdx_strerror.restype = ctypes.c_char_p
+            L.mdx_last_error.argtypes = [vp]
+            L.mdx_last_error.restype = ctypes.c_char_p
+            L.mdx_workspace_bytes.argtypes = [vp]
+            L.mdx_workspace_bytes.restype = ctypes.c_size_t
+            L.mdx_qr.argtypes = [vp, i, i, i, vp, vp, vp, vp, i, vp]
+            L.mdx_qr.restype = i
+            for name in ("detect_sd", "detect_kbest", "detect_hybrid"):
+                f = getattr(L, name)
+                f.argtypes = [vp, ctypes.POINTER(Params), i, vp, vp, vp, vp, vp, vp, vp, vp]
+                f.restype = i
+            L.mdx_count_errors.argtypes = [vp, i, i, i, vp, vp, vp, i, vp]
+            L.mdx_count_errors.restype = i
+            L.mdx_profile.argtypes = [vp, i]
+            L.mdx_profile.restype = i
+            L.mdx_profile_read.argtypes = [vp, vp]
+            L.mdx_profile_read.restype = i
+            _lib = L
+    return _lib
+
+
+class Context:
+    """Owns an mdx_ctx (device workspace for up to max_batch vectors)."""
+
+    def __init__(self, device: int = 0, max_batch: int = 1024, max_n_rx: int = 16, max_n_tx: int = 16):
+        self._h = ctypes.c_void_p()
+        st = lib().mdx_create(ctypes.byref(self._h), device, max_batch, max_n_rx, max_n_tx)
+        if st != MDX_OK:
+            raise MdxError(st, f"mdx_create: {lib().mdx_strerror(st).decode()}")
+        self.device, self.max_batch, self.max_n_rx, self.max_n_tx = device, max_batch, max_n_rx, max_n_tx
+
+    @property
+    def handle(self):
+        return self._h
+
+    def workspace_bytes(self) -> int:
+        return int(lib().mdx_workspace_bytes(self._h))
+
+    def check(self, st: int, what: str):
+        if st != MDX_OK:
+            msg = lib().mdx_last_error(self._h).decode(errors="replace")
+            raise MdxError(st, f"{what}: {lib().mdx_strerror(st).decode()}: {msg}")
+
+    def profile(self, enable: bool = True):
+        """Record CUDA events around the QR and search kernels of each call."""
+        self.check(lib().mdx_profile(self._h, int(enable)), "mdx_profile")
+
+    def profile_read(self):
+        """(QR ms, search ms, calls) summed since the last read."""
+        import numpy as np
+
+        out = np.zeros(3)
+        self.check(lib().mdx_profile_read(self._h, ctypes.c_void_p(out.ctypes.data)), "mdx_profile_read")
+        return float(out[0]), float(out[1]), int(out[2])
+
+    def close(self):
+        if self._h:
+            lib().mdx_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    if hasattr(t, "data_ptr"):
+        return ctypes.c_void_p(t.data_ptr())
+    if hasattr(t, "ctypes"):
+        return ctypes.c_void_p(t.ctypes.data)
+    return ctypes.c_void_p(int(t))
+
+
+def _stream(stream):
+    if stream is None:
+        import torch
+
+        return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    if hasattr(stream, "cuda_stream"):
+        return ctypes.c_void_p(stream.cuda_stream)
+    return ctypes.c_void_p(int(stream))
+
+
+def _call_detect(name, ctx, params, batch, H, y, noise_var, sym, metric, vstatus, stats, stream):
+    f = getattr(lib(), name)
+    st = f(ctx.handle, ctypes.byref(params), int(batch), _ptr(H), _ptr(y), _ptr(noise_var), _ptr(sym),
+           _ptr(metric), _ptr(vstatus), _ptr(stats), _stream(stream))
+    ctx.check(st, name)
+
+
+def _outputs(batch, n_tx, device, want_stats):
+    import torch
+
+    sym = torch.empty((batch, n_tx), dtype=torch.uint8, device=device)
+    met = torch.empty(batch, dtype=torch.float64, device=device)
+    vst = torch.empty(batch, dtype=torch.int32, device=device)
+    stats = torch.empty((batch, STATS), dtype=torch.int64, device=device) if want_stats else None
+    return sym, met, vst, stats
+
+
+def detect(algo: str, ctx: Context, params: Params, H, y, noise_var, stream=None, want_stats=True,
+           out=None):
+    """Run detect_<algo> on torch CUDA tensors H [B][N][M][2], y [B][N][2],
+    noise_var [B] (float64).  Returns (sym, metric, vstatus, stats) tensors."""
+    B = int(H.shape[0])
+    if out is None:
+        out = _outputs(B, params.n_tx, H.device, want_stats)
+    sym, met, vst, stats = out
+    _call_detect(f"detect_{algo}", ctx, params, B, H, y, noise_var, sym, met, vst, stats, stream)
+    return sym, met, vst, stats
+
+
+def detect_sd(ctx, params, H, y, noise_var, **kw):
+    return detect("sd", ctx, params, H, y, noise_var, **kw)
+
+
+def detect_kbest(ctx, params, H, y, noise_var, **kw):
+    return detect("kbest", ctx, params, H, y, noise_var, **kw)
+
+
+def detect_hybrid(ctx, params, H, y, noise_var, **kw):
+    return detect("hybrid", ctx, params, H, y, noise_var, **kw)
+
+
+def detect_host(algo: str, ctx: Context, params: Params, H, y, noise_var, sym, metric, vstatus,
+                stats=None, stream=None):
+    """detect_<algo> on numpy host arrays (outputs preallocated); the library
+    stages them through its device buffers (MDX_HOST_BUFFERS) and returns
+    when the results are in host memory."""
+    p = Params(params.n_rx, params.n_tx, params.qam, params.init_radius_sq, params.K,
+               params.hybrid_depth, params.node_budget, params.flags | MDX_HOST_BUFFERS)
+    _call_detect(f"detect_{algo}", ctx, p, H.shape[0], H, y, noise_var, sym, metric, vstatus, stats,
+                 stream)
+
+
+def qr(ctx: Context, H, y, stream=None):
+    """Dense R [B][n][n] and ybar [B][n] (float64 torch tensors) of H, y."""
+    import torch
+
+    B, N, M = int(H.shape[0]), int(H.shape[1]), int(H.shape[2])
+    R = torch.empty((B, 2 * M, 2 * M), dtype=torch.float64, device=H.device)
+    yb = torch.empty((B, 2 * M), dtype=torch.float64, device=H.device)
+    st = lib().mdx_qr(ctx.handle, B, N, M, _ptr(H), _ptr(y), _ptr(R), _ptr(yb), 0, _stream(stream))
+    ctx.check(st, "mdx_qr")
+    return R, yb
+
+
+def count_errors(ctx: Context, sym_hat, sym_true, qam: int, stream=None):
+    """(bit errors, symbol errors) of uint8 CUDA tensors [B][M] (Gray map)."""
+    import torch
+
+    out = torch.zeros(2, dtype=torch.int64, device=sym_hat.device)
+    B, M = int(sym_hat.shape[0]), int(sym_hat.shape[1])
+    st = lib().mdx_count_errors(ctx.handle, B, M, int(qam), _ptr(sym_hat), _ptr(sym_true), _ptr(out), 0,
+                                _stream(stream))
+    ctx.check(st, "mdx_count_errors")
+    return out

@@ -1,0 +1,259 @@
+"""CUDA detectors against the FP64 oracle, element by element, through the C ABI.
+
+Acceptance (the tolerance of mixed-precision detection): detected indices
+identical to the oracle's on every vector except those the oracle marks as
+near-ties (sphere decoder: best/second-best leaf gap below 1e-6 relative;
+K-best and hybrid: a K / K+1 selection gap or final gap below 1e-5 relative,
+where an FP32 partial distance may legitimately order the pair the other
+way); FP64-rescored metrics within 1e-5 relative wherever the indices agree.
+"""
+
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2002_09561_gb300 import workload as wl
+
+pytestmark = pytest.mark.gpu
+
+SD_GAP = 1e-6
+KB_GAP = 1e-5
+MET_RTOL = 1e-5
+
+
+@pytest.fixture(scope="module")
+def env():
+    import torch
+
+    import __graft_entry__
+
+    __graft_entry__.build()
+    from paper_2002_09561_gb300 import mdx
+
+    ctx = mdx.Context(0, max_batch=4096, max_n_rx=100, max_n_tx=100)
+    yield torch, mdx, ctx
+    ctx.close()
+
+
+def _run(env, algo, w, qam, radius=math.inf, K=16, depth=4, budget=0, flags=0):
+    torch, mdx, ctx = env
+    dev = torch.device("cuda:0")
+    H = torch.from_numpy(w["H"]).to(dev)
+    y = torch.from_numpy(w["y"]).to(dev)
+    nv = torch.from_numpy(w["noise_var"]).to(dev)
+    N, M = w["H"].shape[1], w["H"].shape[2]
+    p = mdx.make_params(N, M, qam, radius=radius, K=K, depth=depth, budget=budget, flags=flags)
+    sym, met, vst, stats = mdx.detect(algo, ctx, p, H, y, nv)
+    torch.cuda.synchronize()
+    return sym.cpu().numpy(), met.cpu().numpy(), vst.cpu().numpy(), stats.cpu().numpy()
+
+
+def _compare(gpu, ref, gap_tol, max_mismatch=0.01, label=""):
+    """Indices must agree outside near-ties; where FP32 may legitimately
+    order a near-tie the other way the vector may differ, but such
+    differences must stay rare.  Returns (agreement, near-tie fraction)."""
+    sym, met = gpu[0], gpu[1]
+    same = (sym == ref["sym"]).all(axis=1)
+    exempt = ref["gap"] < gap_tol
+    bad = np.flatnonzero(~same & ~exempt)
+    print(f"PARITY {label}: vectors {len(same)}, identical {same.mean():.4f}, "
+          f"near-ties {exempt.mean():.4f}, differing near-ties {(~same & exempt).sum()}")
+    assert bad.size == 0, f"{bad.size} mismatches outside near-ties, e.g. vector {bad[:5]}"
+    assert (~same).mean() <= max_mismatch, f"{(~same).sum()} differing vectors"
+    rel = np.abs(met[same] - ref["metric"][same]) / np.maximum(ref["metric"][same], 1e-300)
+    assert rel.size == 0 or rel.max() < MET_RTOL, rel.max()
+    return same.mean(), exempt.mean()
+
+
+# ----------------------------------------------------------------------------------- QR
+
+
+@pytest.mark.parametrize("N,M,B", [(4, 4, 64), (16, 16, 256), (12, 8, 33), (40, 24, 9),
+                                   (100, 100, 3), (1, 1, 5)])
+def test_qr_matches_oracle(env, N, M, B):
+    torch, mdx, ctx = env
+    w = wl.generate(21, B, N, M, 16, 10.0)
+    R, yb = mdx.qr(ctx, torch.from_numpy(w["H"]).cuda(), torch.from_numpy(w["y"]).cuda())
+    torch.cuda.synchronize()
+    Ro, ybo = oracle.qr_batch(w["H"], w["y"])
+    scale = np.abs(Ro).max()
+    np.testing.assert_allclose(R.cpu().numpy(), Ro, atol=1e-12 * scale * max(1, M / 4), rtol=0)
+    np.testing.assert_allclose(yb.cpu().numpy(), ybo, atol=1e-12 * np.abs(ybo).max() * max(1, M / 4))
+
+
+# ------------------------------------------------------------------------- sphere decoder
+
+
+def test_sd_4x4_4qam_equals_brute_force(env):
+    w = wl.generate(0, 1000, 4, 4, 4, 10.0)
+    gpu = _run(env, "sd", w, 4)
+    ml = oracle.detect_batch("ml", w["H"], w["y"], w["noise_var"], 4)
+    agree, _ = _compare(gpu, ml, SD_GAP)
+    assert agree > 0.999
+    assert (gpu[2] == 0).all()
+
+
+@pytest.mark.parametrize("snr,B", [(8.0, 48), (12.0, 300), (16.0, 600), (20.0, 600)])
+def test_sd_16x16_16qam(env, snr, B):
+    w = wl.generate(int(snr) + 100, B, 16, 16, 16, snr)
+    gpu = _run(env, "sd", w, 16, radius="paper")
+    ref = oracle.detect_batch("sd", w["H"], w["y"], w["noise_var"], 16, radius="paper", want_gap=True)
+    _compare(gpu, ref, SD_GAP, label=f"sd 16x16 16-QAM {snr} dB")
+    # visited nodes: the FP32 slack can only add nodes near the sphere's surface
+    g_nodes, o_nodes = gpu[3][:, 0], ref["stats"][:, 0]
+    assert np.all(g_nodes >= 1)
+    assert abs(g_nodes.sum() / o_nodes.sum() - 1.0) < 0.05
+
+
+@pytest.mark.parametrize("N,M,qam,snr,B", [(5, 3, 16, 9.0, 37), (1, 1, 64, 12.0, 50),
+                                           (9, 7, 4, 3.0, 65), (24, 20, 16, 22.0, 40),
+                                           (2, 2, 64, 0.0, 33)])
+def test_sd_ragged_sizes(env, N, M, qam, snr, B):
+    w = wl.generate(31, B, N, M, qam, snr)
+    gpu = _run(env, "sd", w, qam, radius="paper")
+    ref = oracle.detect_batch("sd", w["H"], w["y"], w["noise_var"], qam, radius="paper", want_gap=True)
+    _compare(gpu, ref, SD_GAP)
+
+
+def test_sd_radius_doubling(env):
+    """A radius far below the ML metric leaves the sphere empty; the detector
+    doubles it until a leaf appears and still returns the ML point."""
+    w = wl.generate(41, 200, 6, 6, 16, 10.0)
+    gpu = _run(env, "sd", w, 16, radius=1e-4)
+    ref = oracle.detect_batch("sd", w["H"], w["y"], w["noise_var"], 16, radius=1e-4, want_gap=True)
+    _compare(gpu, ref, SD_GAP)
+    assert (gpu[2] == 1).mean() > 0.9
+    np.testing.assert_array_equal(gpu[3][:, 2] > 0, ref["stats"][:, 2] > 0)
+
+
+def test_sd_budget(env):
+    w = wl.generate(42, 64, 16, 16, 16, 4.0)
+    gpu = _run(env, "sd", w, 16, radius="paper", budget=100)
+    assert (gpu[3][:, 0] <= 100).all()
+    assert (gpu[2] == 2).mean() > 0.5
+
+
+# ----------------------------------------------------------------------------------- K-best
+
+
+@pytest.mark.parametrize("K", [16, 64, 256])
+@pytest.mark.parametrize("snr", [6.0, 14.0])
+def test_kbest_16x16_16qam(env, K, snr):
+    w = wl.generate(200 + K + int(snr), 300, 16, 16, 16, snr)
+    gpu = _run(env, "kbest", w, 16, K=K)
+    ref = oracle.detect_batch("kbest", w["H"], w["y"], w["noise_var"], 16, K=K)
+    _compare(gpu, ref, KB_GAP, label=f"kbest 16x16 16-QAM K={K} {snr} dB")
+    # fixed complexity: 1 + sum_l min(K, P^l) branched nodes
+    expect = 1 + sum(min(K, 4 ** l) for l in range(1, 32))
+    assert (gpu[3][:, 0] == expect).all()
+
+
+def test_kbest_full_tree_is_ml(env):
+    w = wl.generate(8, 300, 4, 4, 4, 6.0)
+    gpu = _run(env, "kbest", w, 4, K=128)
+    ml = oracle.detect_batch("ml", w["H"], w["y"], w["noise_var"], 4)
+    _compare(gpu, ml, SD_GAP)
+
+
+@pytest.mark.parametrize("N,M,qam,K", [(6, 5, 64, 7), (3, 3, 16, 1), (20, 16, 64, 32)])
+def test_kbest_ragged(env, N, M, qam, K):
+    w = wl.generate(51, 45, N, M, qam, 15.0)
+    gpu = _run(env, "kbest", w, qam, K=K)
+    ref = oracle.detect_batch("kbest", w["H"], w["y"], w["noise_var"], qam, K=K)
+    _compare(gpu, ref, KB_GAP, label=f"kbest {N}x{M} {qam}-QAM K={K}")
+
+
+def test_kbest_with_radius(env):
+    w = wl.generate(52, 300, 10, 10, 16, 9.0)
+    gpu = _run(env, "kbest", w, 16, K=8, radius="paper")
+    ref = oracle.detect_batch("kbest", w["H"], w["y"], w["noise_var"], 16, K=8, radius="paper")
+    _compare(gpu, ref, KB_GAP)
+
+
+# ----------------------------------------------------------------------------------- hybrid
+
+
+@pytest.mark.parametrize("K,d", [(4, 2), (8, 4), (16, 0)])
+def test_hybrid_8x8_64qam(env, K, d):
+    w = wl.generate(61 + d, 200, 8, 8, 64, 18.0)
+    gpu = _run(env, "hybrid", w, 64, K=K, depth=d, radius="paper")
+    ref = oracle.detect_batch("hybrid", w["H"], w["y"], w["noise_var"], 64, K=K, depth=d, radius="paper")
+    _compare(gpu, ref, KB_GAP, label=f"hybrid 8x8 64-QAM K={K} d={d}")
+
+
+def test_hybrid_100x100_64qam_sample(env):
+    w = wl.generate(71, 6, 100, 100, 64, 28.0)
+    gpu = _run(env, "hybrid", w, 64, K=32, depth=4, radius="paper")
+    ref = oracle.detect_batch("hybrid", w["H"], w["y"], w["noise_var"], 64, K=32, depth=4, radius="paper")
+    same = (gpu[0] == ref["sym"]).all(axis=1)
+    assert same.mean() >= 5 / 6
+    rel = np.abs(gpu[1] - ref["metric"]) / ref["metric"]
+    assert rel[same].max() < MET_RTOL
+
+
+# ------------------------------------------------------------------------ errors and I/O
+
+
+def test_count_errors_matches_oracle(env):
+    torch, mdx, ctx = env
+    rng = np.random.default_rng(3)
+    for qam in (4, 16, 64):
+        a = rng.integers(0, qam, size=(777, 13)).astype(np.uint8)
+        b = a.copy()
+        flip = rng.random(a.shape) < 0.1
+        b[flip] = rng.integers(0, qam, size=flip.sum())
+        got = mdx.count_errors(ctx, torch.from_numpy(a).cuda(), torch.from_numpy(b).cuda(), qam)
+        assert tuple(got.cpu().tolist()) == oracle.count_errors(a, b, qam)
+
+
+def test_host_buffers_match_device_path(env):
+    torch, mdx, ctx = env
+    w = wl.generate(81, 100, 16, 16, 16, 14.0)
+    dev = _run(env, "kbest", w, 16, K=16)
+    sym = np.zeros((100, 16), np.uint8)
+    met = np.zeros(100)
+    vst = np.zeros(100, np.int32)
+    st = np.zeros((100, mdx.STATS), np.int64)
+    p = mdx.make_params(16, 16, 16, K=16)
+    mdx.detect_host("kbest", ctx, p, w["H"], w["y"], w["noise_var"], sym, met, vst, st)
+    np.testing.assert_array_equal(sym, dev[0])
+    np.testing.assert_array_equal(met, dev[1])
+
+
+def test_invalid_arguments_are_rejected(env):
+    torch, mdx, ctx = env
+    w = wl.generate(1, 4, 4, 4, 4, 10.0)
+    H = torch.from_numpy(w["H"]).cuda()
+    y = torch.from_numpy(w["y"]).cuda()
+    nv = torch.from_numpy(w["noise_var"]).cuda()
+    with pytest.raises(mdx.MdxError) as e:
+        mdx.detect("sd", ctx, mdx.make_params(4, 4, 8), H, y, nv)
+    assert e.value.status == mdx.MDX_EINVAL
+    with pytest.raises(mdx.MdxError) as e:
+        mdx.detect("kbest", ctx, mdx.make_params(4, 4, 4, K=0), H, y, nv)
+    assert e.value.status == mdx.MDX_EINVAL
+    # host memory passed without MDX_HOST_BUFFERS
+    sym = np.zeros((4, 4), np.uint8)
+    with pytest.raises(mdx.MdxError) as e:
+        mdx._call_detect("detect_sd", ctx, mdx.make_params(4, 4, 4), 4, w["H"], w["y"], w["noise_var"],
+                         sym, np.zeros(4), np.zeros(4, np.int32), None, None)
+    assert e.value.status == mdx.MDX_EINVAL
+    small = mdx.Context(0, max_batch=2, max_n_rx=4, max_n_tx=4)
+    with pytest.raises(mdx.MdxError) as e:
+        mdx.detect("sd", small, mdx.make_params(4, 4, 4), H, y, nv)
+    assert e.value.status == mdx.MDX_EUNSUPPORTED
+    small.close()
+    # the context still works after rejected calls
+    out = mdx.detect("sd", ctx, mdx.make_params(4, 4, 4), H, y, nv)
+    torch.cuda.synchronize()
+    assert out[2].cpu().numpy().tolist() == [0, 0, 0, 0]
+
+
+def test_empty_batch(env):
+    torch, mdx, ctx = env
+    z = torch.zeros((0, 4, 4, 2), dtype=torch.float64, device="cuda")
+    out = mdx.detect("sd", ctx, mdx.make_params(4, 4, 4), z, torch.zeros((0, 4, 2), dtype=torch.float64,
+                     device="cuda"), torch.zeros(0, dtype=torch.float64, device="cuda"))
+    assert out[0].shape == (0, 4)
