@@ -170,6 +170,33 @@ mdx_status mdx_count_errors(mdx_ctx* ctx, int batch, int n_tx, int qam, const ui
                             const uint8_t* sym_true, int64_t* counts_out, int flags,
                             void* stream);
 
+/* K-best detection for callers that may not allocate device memory.
+ * (The paper has no counterpart; this is a deployment variant of
+ * detect_kbest.)  Some callers cannot allocate once they are running: a
+ * real-time receiver that fixes its memory at start-up, or a process whose
+ * device memory is held by another allocator.  They cannot create an
+ * mdx_ctx, which allocates its workspace.  This entry point takes no
+ * context and allocates nothing: it computes exactly what detect_kbest
+ * computes (same kernels, same outputs), on the current device, with its
+ * scratch (QR outputs, flags, work counter) in one static device array of
+ * MDX_NOALLOC_SCRATCH_BYTES that the library reserves on every GPU it is
+ * loaded on until the process exits.
+ *   - Device pointers only (MDX_HOST_BUFFERS and MDX_LEARNED_RADIUS are
+ *     rejected with MDX_EUNSUPPORTED); arguments as for detect_kbest.
+ *   - A batch whose scratch exceeds the array returns MDX_EUNSUPPORTED
+ *     (about 6.7 KB per vector at 16x16, 243 KB at 100x100).
+ *   - All calls share the array and it keeps the last call's contents; the
+ *     call clears what must start at zero itself.  Calls whose work
+ *     overlaps on the GPU (other streams, other host threads) race:
+ *     serialise them on one stream.
+ *   - The first call on each device looks up the array's address with that
+ *     device current; make that first call before any stream capture.
+ * Errors are reported by the return value only (there is no context). */
+#define MDX_NOALLOC_SCRATCH_BYTES (16u << 20)
+mdx_status detect_kbest_noalloc(const mdx_params* p, int batch, const double* H, const double* y,
+                                const double* noise_var, uint8_t* sym_out, double* metric_out,
+                                int32_t* vstatus, int64_t* stats, void* stream);
+
 /* Kernel timing for benchmarks.  While enabled, every call records CUDA
  * events on its stream around the QR kernel and the search kernel (up to
  * 1024 calls are kept).  mdx_profile_read waits for those events, writes

@@ -25,7 +25,8 @@ MDX_MAX_TX, MDX_MAX_RX, MDX_MAX_K = 100, 128, 256
 # Every symbol the header declares; the library must export all of them.
 EXPORTS = ["mdx_create", "mdx_destroy", "mdx_strerror", "mdx_last_error", "mdx_workspace_bytes",
            "mdx_qr", "detect_sd", "detect_kbest", "detect_hybrid", "mdx_count_errors",
-           "mdx_profile", "mdx_profile_read"]
+           "mdx_profile", "mdx_profile_read", "detect_kbest_noalloc"]
+NOALLOC_SCRATCH_BYTES = 16 << 20
 STATS = 5  # per-vector stats: nodes, peds, restarts, rescored, algorithmic FP32 flops
 
 
@@ -79,6 +80,8 @@ def lib():
                 f.restype = i
             L.mdx_count_errors.argtypes = [vp, i, i, i, vp, vp, vp, i, vp]
             L.mdx_count_errors.restype = i
+            L.detect_kbest_noalloc.argtypes = [ctypes.POINTER(Params), i, vp, vp, vp, vp, vp, vp, vp, vp]
+            L.detect_kbest_noalloc.restype = i
             L.mdx_profile.argtypes = [vp, i]
             L.mdx_profile.restype = i
             L.mdx_profile_read.argtypes = [vp, vp]
