@@ -86,7 +86,10 @@ enum {
   MDX_HOST_BUFFERS = 1 << 0, /* array arguments are host pointers (see Memory) */
   MDX_NO_RESCORE = 1 << 1,   /* skip the FP64 re-scoring of the final leaf candidates;
                                 metric_out is then the FP32 partial distance */
-  MDX_LEARNED_RADIUS = 1 << 2 /* initial radius from the context's MLP (mdx_mlp_load) */
+  MDX_LEARNED_RADIUS = 1 << 2, /* initial radius from the context's MLP (mdx_mlp_load) */
+  MDX_SEQUENTIAL_SEARCH = 1 << 3 /* detect_sd: one warp searches each vector's whole tree
+                                    (no subtree splitting between warps), so visited-node
+                                    counts are those of the sequential search */
 };
 
 /* Largest sizes the kernels support. */
@@ -201,7 +204,9 @@ mdx_status detect_kbest_noalloc(const mdx_params* p, int batch, const double* H,
  * events on its stream around the QR kernel and the search kernel (up to
  * 1024 calls are kept).  mdx_profile_read waits for those events, writes
  * ms_out[0] = summed QR time, ms_out[1] = summed search time (milliseconds),
- * ms_out[2] = number of calls recorded, and clears the record.  Not part of
+ * ms_out[2] = number of calls recorded, ms_out[3] = the error word of the
+ * last detect_sd launch (non-zero if a bounded wait inside it expired), and
+ * clears the record.  Not part of
  * the detection path; enable = 0 turns it off. */
 mdx_status mdx_profile(mdx_ctx* ctx, int enable);
 mdx_status mdx_profile_read(mdx_ctx* ctx, double* ms_out);

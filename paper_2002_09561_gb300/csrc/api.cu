@@ -21,6 +21,11 @@ struct mdx_ctx {
   int* singular = nullptr;
   unsigned int* counter = nullptr;
   unsigned long long* counts = nullptr;
+  // sphere-decoder task queue
+  void* sd_shared = nullptr;
+  void* sd_queue = nullptr;
+  unsigned char* sd_vstate = nullptr;
+  unsigned long long sd_epoch = 0;
   // staging for MDX_HOST_BUFFERS
   double* sH = nullptr;
   double* sy = nullptr;
@@ -102,14 +107,17 @@ void free_all(mdx_ctx* c) {
   for (int i = 0; i < mdx_ctx::kProfSlots; ++i)
     for (int k = 0; k < 3; ++k)
       if (c->prof_ev[i][k]) cudaEventDestroy(c->prof_ev[i][k]);
-  void* ptrs[] = {c->R64, c->yb64, c->R32, c->yb32, c->singular, c->counter, c->counts,
-                  c->sH,  c->sy,   c->snv, c->ssym, c->ssym2,    c->smet,    c->svst,
-                  c->sstats};
+  void* ptrs[] = {c->R64, c->yb64, c->R32,  c->yb32, c->singular, c->counter,  c->counts,
+                  c->sH,  c->sy,   c->snv,  c->ssym, c->ssym2,    c->smet,     c->svst,
+                  c->sstats, c->sd_shared, c->sd_queue, c->sd_vstate};
   for (void* p : ptrs)
     if (p) cudaFree(p);
 }
 
 enum Algo { ALGO_SD = 0, ALGO_KBEST = 1, ALGO_HYBRID = 2 };
+
+// Task-queue slots of the sphere decoder (tasks exist only while warps are idle).
+constexpr unsigned int kSdQueueSlots = 1u << 16;
 
 size_t kbest_layout_bytes(int n, int K, int P, int keys_cap) {
   // mirrors KbLayout::init in kbest.cu
@@ -237,7 +245,10 @@ mdx_status run_detect(int algo, mdx_ctx* c, const mdx_params* p, int batch, cons
   e = cudaMemsetAsync(c->counter, 0, sizeof(unsigned int), s);
   if (e != cudaSuccess) return cuda_fail(c, e, "work counter reset");
   if (ev) cudaEventRecord(ev[1], s);
-  if (algo == ALGO_SD) e = launch_sd(a, c->num_sms, s);
+  if (algo == ALGO_SD) {
+    SdWorkspace w{c->sd_shared, c->sd_queue, kSdQueueSlots, c->sd_vstate, ++c->sd_epoch};
+    e = launch_sd(a, w, c->num_sms, s);
+  }
   else if (algo == ALGO_KBEST) e = launch_kbest(a, c->num_sms, s);
   else e = launch_hybrid(a, c->num_sms, s);
   if (e == cudaErrorInvalidConfiguration)
@@ -349,11 +360,22 @@ mdx_status mdx_create(mdx_ctx** out, int device, int max_batch, int max_n_rx, in
   chk(alloc(c, &c->smet, B));
   chk(alloc(c, &c->svst, B));
   chk(alloc(c, &c->sstats, B * kStats));
+  chk(alloc(c, reinterpret_cast<unsigned char**>(&c->sd_shared), sd_shared_bytes()));
+  chk(alloc(c, reinterpret_cast<unsigned char**>(&c->sd_queue), sd_task_bytes() * kSdQueueSlots));
+  chk(alloc(c, &c->sd_vstate, B * sd_vec_state_bytes(n)));
   if (e != cudaSuccess) {
     cudaGetLastError();
     free_all(c);
     delete c;
     return MDX_ENOMEM;
+  }
+  // task slots are published by sequence numbers that never equal zero
+  if (cudaMemset(c->sd_queue, 0, sd_task_bytes() * kSdQueueSlots) != cudaSuccess ||
+      cudaDeviceSynchronize() != cudaSuccess) {
+    cudaGetLastError();
+    free_all(c);
+    delete c;
+    return MDX_ECUDA;
   }
   *out = c;
   return MDX_OK;
@@ -474,9 +496,14 @@ mdx_status mdx_profile_read(mdx_ctx* c, double* ms_out) {
     qr += a;
     search += b;
   }
+  int err = 0;
+  cudaError_t e = cudaMemcpy(&err, static_cast<char*>(c->sd_shared) + sd_error_offset(), sizeof(int),
+                             cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return cuda_fail(c, e, "error word");
   ms_out[0] = qr;
   ms_out[1] = search;
   ms_out[2] = c->prof_n;
+  ms_out[3] = err;
   c->prof_n = 0;
   return MDX_OK;
 }

@@ -69,7 +69,19 @@ struct SearchArgs {
 
 cudaError_t launch_qr(int batch, int n_rx, int n_tx, const double* H, const double* y, QrOut out,
                       cudaStream_t s);
-cudaError_t launch_sd(const SearchArgs& a, int num_sms, cudaStream_t s);
+// Global workspace of the sphere decoder's task queue (see sd.cu).
+struct SdWorkspace {
+  void* shared;          // sd_shared_bytes()
+  void* queue;           // qcap task records of sd_task_bytes()
+  unsigned int qcap;     // power of two
+  unsigned char* vstate; // batch x sd_vec_state_bytes(n)
+  unsigned long long epoch;  // distinct per launch on this workspace
+};
+size_t sd_shared_bytes();
+size_t sd_error_offset();
+size_t sd_task_bytes();
+size_t sd_vec_state_bytes(int n);
+cudaError_t launch_sd(const SearchArgs& a, const SdWorkspace& w, int num_sms, cudaStream_t s);
 cudaError_t launch_kbest(const SearchArgs& a, int num_sms, cudaStream_t s);
 cudaError_t launch_hybrid(const SearchArgs& a, int num_sms, cudaStream_t s);
 cudaError_t launch_count_errors(int batch, int n_tx, int qam, const uint8_t* a, const uint8_t* b,

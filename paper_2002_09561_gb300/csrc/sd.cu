@@ -1,51 +1,182 @@
 // Exact sphere decoder (Sec. III-B, Algorithm 1) with Best-FS /
-// Schnorr-Euchner child order (Sec. IV-A) and incremental partial distances
-// (Sec. IV-C, Eq. inc), one warp per received vector.
+// Schnorr-Euchner child order (Sec. IV-A), incremental partial distances
+// (Sec. IV-C, Eq. inc) and dynamic subtree splitting between warps (the
+// load balancing of the paper's parallel SD, Sec. V-C, recast for a GPU).
 //
-// Mapping.  Lane l owns the rows r = l + 32 t (t < ROWS).  For the node at
-// level i (rows n-1..i+1 fixed) the residual of every lower row,
+// Unit of work: a task = one tree node (rows n-1..L+1 fixed, row L to
+// expand) of one vector, explored depth-first by one warp.  A vector starts
+// as its root task.  Warps take work in this order: a queued task, else a
+// fresh vector, else they wait (idle).  While any warp is idle, a busy warp
+// checks every kSplitEvery nodes and donates all untried children of its
+// top-most open level as new tasks, marking that level exhausted.  The only
+// state the tasks of a vector share is its radius (an FP32 r^2 in global
+// memory, shrunk with atomicMin) and its leaf-candidate list; a per-vector
+// count of unfinished tasks tells the warp finishing the last one to
+// re-score the candidates in FP64 and write the result.  Every answer is the
+// one the sequential search gives: the subtrees partition the tree and
+// pruning only ever uses a radius that some leaf of the vector has reached.
+//
+// One node step.  Lane l owns the rows r = l + 32 t (t < ROWS).  For the
+// node at level i (rows n-1..i+1 fixed) the residual of every lower row,
 //   z_r = ybar_r - sum_{j > i} R_rj x_j   (r <= i),
-// sits in a shared-memory stack zs[level i][r]; descending into child x_i = a
-// costs one FMA per row below (z_r -= R_ri a), and the interference of row i
-// is simply c_i = z_i.  Each partial distance is built by one FMA chain in a
-// fixed order (j = n-1 down to i+1), so FP32 results do not depend on the
-// warp's reduction shape.  The control state of the current level (parent
-// partial distance, c_i, zig-zag pointers) is warp-uniform and lives in
-// registers; it is pushed to shared memory on descent and popped on
-// backtrack.
+// is kept in a shared-memory stack zs[level i][r]; descending into child
+// x_i = a costs one FMA per row below (z_r -= R_ri a), and the interference
+// of the next row is the owner lane's updated z, broadcast by one shuffle.
+// Each partial distance is one FMA chain in a fixed order (j = n-1 down to
+// i+1), identical whether a node is reached by descent or rebuilt from a
+// task's path.  The control state of the current level is warp-uniform and
+// lives in registers; it is pushed to shared memory on descent and popped on
+// backtrack.  Children are visited in increasing (c_i - R_ii a_k)^2 by a
+// zig-zag around u_i = c_i / (2 alpha R_ii) + (P-1)/2 in PAM-index space,
+// ties to the lower index; a child reaching the pruning bound ends the level.
 //
-// Children are visited in increasing (c_i - R_ii a_k)^2 by a zig-zag around
-// u_i = c_i / (R_ii alpha) in PAM-index space, ties to the lower index; a
-// child whose partial distance reaches the pruning bound ends the level (all
-// later children are farther).  A leaf inside the bound shrinks the radius
-// and is recorded in a small candidate list; at the end the candidates within
-// FP32 error of the best are re-scored in FP64 against the FP64 R and ybar.
-// Vectors are taken from a global counter, so a warp that finishes an easy
-// vector immediately starts the next one.
+// The task queue is a ring: a consumer claims an index, waits for the
+// producer's sequence number, copies the record and marks the slot free; a
+// producer that wraps onto a slot waits for that mark before writing.
+// Every spin-wait is bounded: a claimed slot that never becomes ready, a slot
+// that is never freed or a candidate lock that is never released sets the
+// launch's error word and the warp moves on; an idle warp that waits too
+// long simply exits (the busy warps drain the queue themselves before they
+// finish).
 #include "mdx_internal.cuh"
 
 namespace mdx {
+
+// Global state of one SD launch (zeroed before the launch).
+struct SdShared {
+  unsigned int vec_next;
+  unsigned int q_head;
+  unsigned int q_tail;
+  int outstanding;  // tasks queued or running (root tasks included)
+  int idle;         // warps waiting for work
+  int error;        // a bounded wait expired
+  int pad[10];
+};
+
 namespace {
 
-constexpr int kWarps = 4;  // warps per CTA
-constexpr int kCand = 8;   // leaf candidates kept per vector
+constexpr int kWarpsMax = 4;     // warps per CTA
+constexpr int kCand = 8;         // leaf candidates kept per vector
+constexpr int kSplitEvery = 128; // nodes between split / radius checks
+constexpr int kTaskPath = 224;   // path bytes in a task record (n <= 224)
+constexpr int kMinSplitLevel = 3; // donate only children with at least 3 rows below
+
+struct SdTask {
+  unsigned long long seq;  // (epoch << 32) | (slot index + 1) once written
+  int v;
+  int level;  // row to expand; rows level+1..n-1 fixed in x[]
+  float ped;
+  int pad;
+  uint8_t x[kTaskPath];
+};
+static_assert(sizeof(SdTask) == 248, "task record layout");
+
+// Per-vector state in global memory.
+struct SdVec {
+  unsigned int r2bits;  // FP32 r^2 bits (non-negative floats order like uints)
+  int pending;          // unfinished tasks of this vector
+  int lock;             // candidate-list lock
+  int ncand;
+  unsigned long long nodes, peds, flops;
+  int restarts;
+  int budget_hit;
+  float E;
+  float r2_start;  // radius of the current pass (for doubling)
+  float cand_ped[kCand];
+  // followed by kCand paths of path_pad(n) bytes
+};
 
 __host__ __device__ inline int path_pad(int n) { return round_up(n, 16); }
+__host__ __device__ inline size_t vec_state_bytes(int n) {
+  return round_up((int)(sizeof(SdVec) + (size_t)kCand * path_pad(n)), 16);
+}
 
-// Shared-memory bytes per warp for real dimension n, a multiple of 16 so that
-// every warp's region (staged with 16-byte vector stores) starts aligned.
 __host__ __device__ inline size_t sd_warp_bytes(int n) {
-  const size_t b = sizeof(float) * (2 * (size_t)tri_stride32(n) + 4 * (size_t)n + kCand) +
-                   sizeof(int) * (size_t)n + (size_t)path_pad(n) * (1 + kCand);
+  const size_t b = sizeof(float) * (2 * (size_t)tri_stride32(n) + 5 * (size_t)n) +
+                   sizeof(int) * (size_t)n + (size_t)path_pad(n);
   return (b + 15) / 16 * 16;
 }
 
+struct SdArgs {
+  SearchArgs a;
+  SdShared* sh;
+  SdTask* queue;
+  unsigned int qcap;  // power of two
+  unsigned char* vstate;
+  size_t vstride;
+  unsigned long long epoch;
+};
+
+__device__ __forceinline__ SdVec* vec_of(const SdArgs& g, int v) {
+  return reinterpret_cast<SdVec*>(g.vstate + (size_t)v * g.vstride);
+}
+__device__ __forceinline__ uint8_t* cand_path(SdVec* vs, int q, int n) {
+  return reinterpret_cast<uint8_t*>(vs + 1) + (size_t)q * path_pad(n);
+}
+
+// Claim a queued task (lane 0); returns the slot index or -1 if the queue is empty.
+__device__ long long queue_pop(const SdArgs& g) {
+  volatile unsigned int* head = &g.sh->q_head;
+  volatile unsigned int* tail = &g.sh->q_tail;
+  for (int tries = 0; tries < 64; ++tries) {
+    const unsigned int h = *head;
+    if (h >= *tail) return -1;
+    if (atomicCAS(&g.sh->q_head, h, h + 1) == h) return (long long)h;
+  }
+  return -1;
+}
+
+// Reserve cnt consecutive slots (lane 0); -1 if the ring has no room.  The
+// head is read before the tail: the head never passes a tail read after it,
+// so tail - head cannot underflow.
+__device__ long long queue_reserve(const SdArgs& g, int cnt) {
+  for (int tries = 0; tries < 4096; ++tries) {
+    const unsigned int h = *(volatile unsigned int*)&g.sh->q_head;
+    const unsigned int t = *(volatile unsigned int*)&g.sh->q_tail;
+    if (t - h + (unsigned)cnt > g.qcap) return -1;
+    if (atomicCAS(&g.sh->q_tail, t, t + (unsigned)cnt) == t) return (long long)t;
+    __nanosleep(16);
+  }
+  return -1;
+}
+
+// A slot used before in this launch (index >= qcap) may be written only
+// after the consumer of its previous occupant has copied it out and marked
+// it free ((epoch << 32) | 0).  Lane 0; false if that never happened.
+__device__ bool slot_writable(const SdArgs& g, SdTask* t, unsigned long long idx) {
+  if (idx < g.qcap) return true;
+  const unsigned long long freed = g.epoch << 32;
+  for (int it = 0; it < (1 << 22); ++it) {
+    if (*(volatile unsigned long long*)&t->seq == freed) {
+      __threadfence();
+      return true;
+    }
+    __nanosleep(32);
+  }
+  return false;
+}
+
+__device__ __forceinline__ bool lock_acquire(int* lk) {
+  for (int it = 0; it < (1 << 22); ++it) {
+    if (atomicCAS(lk, 0, 1) == 0) {
+      __threadfence();
+      return true;
+    }
+    __nanosleep(64);
+  }
+  return false;
+}
+__device__ __forceinline__ void lock_release(int* lk) {
+  __threadfence();
+  atomicExch(lk, 0);
+}
+
 template <int ROWS>
-__global__ void __launch_bounds__(kWarps * 32) sd_kernel(SearchArgs a) {
+__global__ void __launch_bounds__(kWarpsMax * 32) sd_kernel(SdArgs g) {
   extern __shared__ __align__(16) unsigned char smem[];
+  const SearchArgs& a = g.a;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int n = a.n, P = a.P;
-  (void)kWarps;
   const int ts = tri_stride32(n);
   unsigned char* base = smem + warp * sd_warp_bytes(n);
   float* Rc = reinterpret_cast<float*>(base);  // column-packed R (FP32)
@@ -54,269 +185,583 @@ __global__ void __launch_bounds__(kWarps * 32) sd_kernel(SearchArgs a) {
   float* lv_c = lv_ped + n;                     // c_i
   float* lv_u = lv_c + n;                       // u_i
   float* lv_rinv = lv_u + n;                    // 1 / (2 alpha R_ii)
-  float* cand_ped = lv_rinv + n;                // kCand
-  int* lv_lohi = reinterpret_cast<int*>(cand_ped + kCand);
+  float* lv_rii = lv_rinv + n;                  // R_ii
+  int* lv_lohi = reinterpret_cast<int*>(lv_rii + n);
   uint8_t* xs = reinterpret_cast<uint8_t*>(lv_lohi + n);  // current path
-  uint8_t* cand_x = xs + path_pad(n);                       // kCand paths
-  const int pp = path_pad(n);
   const float alpha = a.alpha;
   const float uoff = 0.5f * (float)(P - 1);
-  const float amax = alpha * (float)(P - 1);
+  int staged = -1;  // vector whose R is in shared memory
 
   for (;;) {
-    int v = 0;
-    if (lane == 0) v = (int)atomicAdd(a.work_counter, 1u);
-    v = __shfl_sync(0xffffffffu, v, 0);
-    if (v >= a.batch) break;
-
-    if (a.singular && a.singular[v]) {
-      for (int j = lane; j < a.n_tx; j += 32) a.sym_out[(size_t)v * a.n_tx + j] = 0;
-      if (lane == 0) {
-        a.metric_out[v] = 0.0;
-        a.vstatus[v] = MDX_V_SINGULAR;
-        if (a.stats)
-          for (int q = 0; q < kStats; ++q) a.stats[(size_t)v * kStats + q] = 0;
+    // ------------------------------------------------------------- get work
+    int v = -1, top = n - 1;
+    float top_ped = 0.0f;
+    bool fresh = false;
+    {
+      long long slot = -1;
+      if (lane == 0) slot = queue_pop(g);
+      slot = __shfl_sync(0xffffffffu, slot, 0);
+      if (slot >= 0) {
+        SdTask* t = g.queue + ((unsigned)slot & (g.qcap - 1));
+        const unsigned long long want = (g.epoch << 32) | ((unsigned long long)slot + 1ull);
+        int ok = 1;
+        if (lane == 0) {
+          ok = 0;
+          for (int it = 0; it < (1 << 22); ++it) {
+            if (*(volatile unsigned long long*)&t->seq == want) {
+              ok = 1;
+              break;
+            }
+            __nanosleep(32);
+          }
+          if (!ok) atomicExch(&g.sh->error, 1);
+          __threadfence();
+        }
+        ok = __shfl_sync(0xffffffffu, ok, 0);
+        if (!ok) continue;  // a producer never published: error recorded, skip
+        __threadfence();
+        v = __shfl_sync(0xffffffffu, lane == 0 ? *(volatile int*)&t->v : 0, 0);
+        top = __shfl_sync(0xffffffffu, lane == 0 ? *(volatile int*)&t->level : 0, 0);
+        top_ped = __shfl_sync(0xffffffffu, lane == 0 ? *(volatile float*)&t->ped : 0.0f, 0);
+        const bool valid = v >= 0 && v < a.batch && top >= 0 && top < n;
+        if (valid)
+          for (int j = top + 1 + lane; j < n; j += 32) xs[j] = ((volatile uint8_t*)t->x)[j];
+        __syncwarp();
+        if (lane == 0) {
+          __threadfence();
+          atomicExch(&t->seq, g.epoch << 32);  // copied out: the slot may be reused
+        }
+        if (!valid) {
+          if (lane == 0) atomicExch(&g.sh->error, 2);
+          continue;
+        }
+      } else {
+        if (lane == 0) v = (int)atomicAdd(&g.sh->vec_next, 1u);
+        v = __shfl_sync(0xffffffffu, v, 0);
+        if (v < a.batch) {
+          fresh = true;
+        } else {
+          // idle: wait until a task is queued or everything is finished
+          int leave = 0;
+          if (lane == 0) {
+            atomicAdd(&g.sh->idle, 1);
+            for (int it = 0; it < (1 << 22); ++it) {
+              if (*(volatile unsigned int*)&g.sh->q_head < *(volatile unsigned int*)&g.sh->q_tail) break;
+              if (*(volatile int*)&g.sh->outstanding == 0) {
+                leave = 1;
+                break;
+              }
+              __nanosleep(500);
+              if (it == (1 << 22) - 1) leave = 1;
+            }
+            atomicSub(&g.sh->idle, 1);
+          }
+          leave = __shfl_sync(0xffffffffu, leave, 0);
+          if (leave) break;
+          continue;
+        }
       }
-      continue;
     }
+    SdVec* vs = vec_of(g, v);
 
-    // stage R (FP32) and the top residual level (= ybar)
-    const float4* src = reinterpret_cast<const float4*>(a.R32 + (size_t)v * ts);
-    for (int t = lane; t < ts / 4; t += 32) reinterpret_cast<float4*>(Rc)[t] = src[t];
+    // --------------------------------------------------- stage the vector
+    if (staged != v) {
+      const float4* src = reinterpret_cast<const float4*>(a.R32 + (size_t)v * ts);
+      for (int t = lane; t < ts / 4; t += 32) reinterpret_cast<float4*>(Rc)[t] = src[t];
+      __syncwarp();
+      for (int r = lane; r < n; r += 32) {
+        const float rr = Rc[col_off(r) + r];
+        lv_rii[r] = rr;
+        lv_rinv[r] = 0.5f / (alpha * rr);
+      }
+      staged = v;
+    }
     const float* yb = a.yb32 + (size_t)v * vec_stride32(n);
-    for (int r = lane; r < n; r += 32) zs[col_off(n - 1) + r] = yb[r];
-    __syncwarp();
-    for (int r = lane; r < n; r += 32) lv_rinv[r] = 0.5f / (alpha * Rc[col_off(r) + r]);
 
-    // FP32 error scale of this vector (see prune_bound)
-    float e2 = 0.0f;
+    if (fresh) {
+      if (a.singular && a.singular[v]) {
+        for (int j = lane; j < a.n_tx; j += 32) a.sym_out[(size_t)v * a.n_tx + j] = 0;
+        if (lane == 0) {
+          a.metric_out[v] = 0.0;
+          a.vstatus[v] = MDX_V_SINGULAR;
+          if (a.stats)
+            for (int q = 0; q < kStats; ++q) a.stats[(size_t)v * kStats + q] = 0;
+        }
+        continue;
+      }
+      __syncwarp();
+      const float E0 = error_scale_warp(n, P, alpha, Rc, yb, lane);
+      float r2;
+      if (a.radius_mode == RADIUS_NONE) r2 = INFINITY;
+      else if (a.radius_mode == RADIUS_PAPER) r2 = (float)((double)a.n_rx * a.n_tx * a.noise_var[v]);
+      else if (a.radius_mode == RADIUS_PER_VECTOR) r2 = a.r2_vec[v];
+      else r2 = (float)a.radius_value;
+      if (!(r2 > 0.0f)) r2 = INFINITY;
+      if (lane == 0) {
+        vs->r2bits = __float_as_uint(r2);
+        vs->pending = 1;
+        vs->lock = 0;
+        vs->ncand = 0;
+        vs->nodes = vs->peds = vs->flops = 0ull;
+        vs->restarts = 0;
+        vs->budget_hit = 0;
+        vs->E = E0;
+        vs->r2_start = r2;
+        __threadfence();
+        atomicAdd(&g.sh->outstanding, 1);
+      }
+      top = n - 1;
+      top_ped = 0.0f;
+    }
+    __syncwarp();
+    // values other warps may change are read by lane 0 and broadcast, so that
+    // every lane of the warp takes the same decisions
+    const float E = __shfl_sync(0xffffffffu, lane == 0 ? *(volatile float*)&vs->E : 0.0f, 0);
+
+    // ------------------------------------------- residuals of the task node
+    // z_r = ybar_r - sum_{j > top} R_rj x_j, r <= top, as one FMA chain from j = n-1 down
 #pragma unroll
     for (int t = 0; t < ROWS; ++t) {
       const int r = lane + 32 * t;
-      if (r < n) {
-        float T = fabsf(yb[r]);
-        for (int j = r; j < n; ++j) T += amax * fabsf(Rc[col_off(j) + r]);
-        const float w = (float)(n - r + 1) * T;
-        e2 += w * w;
+      if (r <= top) {
+        float z = yb[r];
+        for (int j = n - 1; j > top; --j)
+          z = fmaf(-Rc[col_off(j) + r], (float)(2 * (int)xs[j] - (P - 1)) * alpha, z);
+        zs[col_off(top) + r] = z;
       }
     }
-    // broadcast so that every lane takes identical pruning decisions
-    const float E = __shfl_sync(0xffffffffu, sqrtf(warp_sum(e2)) * kU32, 0);
-
-    float r2;
-    if (a.radius_mode == RADIUS_NONE) r2 = INFINITY;
-    else if (a.radius_mode == RADIUS_PAPER) r2 = (float)((double)a.n_rx * a.n_tx * a.noise_var[v]);
-    else if (a.radius_mode == RADIUS_PER_VECTOR) r2 = a.r2_vec[v];
-    else r2 = (float)a.radius_value;
-    if (!(r2 > 0.0f)) r2 = INFINITY;  // zero or NaN radius: search without one
-
-    long long nodes = 0, peds = 0, restarts = 0, flops = 0;
-    int ncand = 0;
-    bool budget_hit = false;
-    float best = INFINITY;
     __syncwarp();
 
-    for (;;) {  // radius-doubling loop
-      float bnd = prune_bound(r2, E, n);
-      int i = n - 1;
-      float ped_par = 0.0f;
-      float c = zs[col_off(n - 1) + n - 1];
-      float rii = Rc[col_off(n - 1) + n - 1];
-      float u = fmaf(c, lv_rinv[n - 1], uoff);
-      int lo = min(max((int)ceilf(u - 0.5f), 0), P - 1);
-      int hi = lo + 1;
-      nodes += 1;
-      for (;;) {
-        // next child of the node at level i in Schnorr-Euchner order
-        int k = -1;
-        if (lo >= 0 || hi < P) {
-          if (hi >= P || (lo >= 0 && fabsf(u - (float)lo) <= fabsf((float)hi - u))) k = lo--;
-          else k = hi++;
-        }
-        float ped = INFINITY;
-        if (k >= 0) {
-          const float d = fmaf(-rii, (float)(2 * k - (P - 1)) * alpha, c);
-          ped = fmaf(d, d, ped_par);
-          ++peds;
-        }
-        if (k < 0 || !(ped < bnd)) {
-          if (i == n - 1) break;  // root exhausted
-          ++i;                    // backtrack: pop level i
-          ped_par = lv_ped[i];
-          c = lv_c[i];
-          u = lv_u[i];
-          const int lh = lv_lohi[i];
-          lo = (lh & 0xffff) - 1;
-          hi = lh >> 16;
-          rii = Rc[col_off(i) + i];
-          continue;
-        }
-        if (i == 0) {
-          // leaf inside the sphere: record it, shrink the radius (Alg. 1)
-          if (lane == 0) xs[0] = (uint8_t)k;
-          __syncwarp();
-          int slot = -1;
-          if (ncand < kCand) {
-            slot = ncand++;
-          } else {
-            float worst = -1.0f;
-            for (int q = 0; q < kCand; ++q)
-              if (cand_ped[q] > worst) {
-                worst = cand_ped[q];
-                slot = q;
-              }
-            if (!(ped < worst)) slot = -1;
-          }
-          if (slot >= 0) {
-            for (int r = lane; r < n; r += 32) cand_x[slot * pp + r] = xs[r];
-            if (lane == 0) cand_ped[slot] = ped;
-          }
-          __syncwarp();
-          if (ped < best) best = ped;
-          if (ped < r2) {
-            r2 = ped;
-            bnd = prune_bound(r2, E, n);
-          }
-          continue;
-        }
-        if (a.budget > 0 && nodes >= a.budget) {
-          budget_hit = true;
-          break;
-        }
-        // descend into child k: push level i, update the residuals of the rows below
-        const float av = (float)(2 * k - (P - 1)) * alpha;
-        if (lane == 0) {
-          lv_ped[i] = ped_par;
-          lv_c[i] = c;
-          lv_u[i] = u;
-          lv_lohi[i] = (lo + 1) | (hi << 16);
-          xs[i] = (uint8_t)k;
-        }
-        const float* zin = zs + col_off(i);
-        float* zout = zs + col_off(i - 1);
-        const float* rc = Rc + col_off(i);
-#pragma unroll
-        for (int t = 0; t < ROWS; ++t) {
-          const int r = lane + 32 * t;
-          if (r < i) zout[r] = fmaf(-rc[r], av, zin[r]);
-        }
-        __syncwarp();
-        --i;
-        ped_par = ped;
-        c = zout[i];
-        rii = Rc[col_off(i) + i];
-        u = fmaf(c, lv_rinv[i], uoff);
-        lo = min(max((int)ceilf(u - 0.5f), 0), P - 1);
-        hi = lo + 1;
-        ++nodes;
-        flops += 2 * (n - 1 - i) + 4 * P;
-      }
-      if (ncand > 0 || budget_hit || !(r2 < INFINITY) || restarts >= 64) break;
-      r2 *= 4.0f;  // empty sphere: double the radius and search again
-      ++restarts;
+    // -------------------------------------------------- depth-first search
+    long long nodes = 0, peds = 0, flops = 0, since = 0;
+    // nodes of this vector already counted by finished or committed tasks
+    long long committed = 0;
+    if (a.budget > 0) {
+      committed = (long long)__shfl_sync(0xffffffffu, lane == 0 ? *(volatile unsigned long long*)&vs->nodes : 0ull, 0);
     }
-
-    // FP64 re-scoring of the candidates within FP32 error of the best
-    const double* R64 = a.R64 + (size_t)v * tri_stride64(n);
-    const double* y64 = a.yb64 + (size_t)v * vec_stride64(n);
-    const float keep = prune_bound(best, E, n);
-    const double alpha64 = a.alpha64;
-    int win = -1;
-    double win_m = INFINITY;
-    long long rescored = 0;
-    for (int q = 0; q < ncand; ++q) {
-      if (!(cand_ped[q] <= keep)) continue;
-      double m;
-      if (a.flags & MDX_NO_RESCORE) {
-        m = (double)cand_ped[q];
-      } else {
-        double rr[ROWS];
-#pragma unroll
-        for (int t = 0; t < ROWS; ++t) {
-          const int r = lane + 32 * t;
-          rr[t] = (r < n) ? y64[r] : 0.0;
-        }
-        for (int j = 0; j < n; ++j) {
-          const double xj = (double)(2 * (int)cand_x[q * pp + j] - (P - 1)) * alpha64;
-          const double* col = R64 + col_off(j);
-#pragma unroll
-          for (int t = 0; t < ROWS; ++t) {
-            const int r = lane + 32 * t;
-            if (r <= j) rr[t] = fma(-col[r], xj, rr[t]);
+    float r2 = __uint_as_float(
+        __shfl_sync(0xffffffffu, lane == 0 ? *(volatile unsigned int*)&vs->r2bits : 0u, 0));
+    float bnd = prune_bound(r2, E, n);
+    bool stop = __shfl_sync(0xffffffffu, lane == 0 ? *(volatile int*)&vs->budget_hit : 0, 0) != 0;
+    int i = top;
+    float ped_par = top_ped;
+    float c = zs[col_off(top) + top];
+    float rii = lv_rii[top];
+    float u = fmaf(c, lv_rinv[top], uoff);
+    int lo = min(max((int)ceilf(u - 0.5f), 0), P - 1);
+    int hi = lo + 1;
+    nodes = 1;
+    flops = 2 * (n - 1 - top) + 4 * P;
+    while (!stop) {
+      // next child of the node at level i in Schnorr-Euchner order
+      int k = -1;
+      if (lo >= 0 || hi < P) {
+        if (hi >= P || (lo >= 0 && fabsf(u - (float)lo) <= fabsf((float)hi - u))) k = lo--;
+        else k = hi++;
+      }
+      float ped = INFINITY;
+      if (k >= 0) {
+        const float d = fmaf(-rii, (float)(2 * k - (P - 1)) * alpha, c);
+        ped = fmaf(d, d, ped_par);
+        ++peds;
+      }
+      if (k < 0 || !(ped < bnd)) {
+        if (i == top) break;  // the task's node is exhausted
+        ++i;                  // backtrack: pop level i
+        ped_par = lv_ped[i];
+        c = lv_c[i];
+        u = lv_u[i];
+        rii = lv_rii[i];
+        const int lh = lv_lohi[i];
+        lo = (lh & 0xffff) - 1;
+        hi = lh >> 16;
+        continue;
+      }
+      if (i == 0) {
+        // leaf inside the sphere: record it in the vector's list, shrink the radius
+        if (lane == 0) xs[0] = (uint8_t)k;
+        __syncwarp();
+        int slot = -1;
+        if (lane == 0) {
+          if (lock_acquire(&vs->lock)) {
+            volatile SdVec* vv = vs;
+            const int nc = vv->ncand;
+            if (nc < kCand) {
+              slot = nc;
+              vv->ncand = nc + 1;
+            } else {
+              float worst = -1.0f;
+              int w = -1;
+              for (int q = 0; q < kCand; ++q)
+                if (vv->cand_ped[q] > worst) {
+                  worst = vv->cand_ped[q];
+                  w = q;
+                }
+              if (ped < worst) slot = w;
+            }
+            if (slot < 0) lock_release(&vs->lock);
+          } else {
+            atomicExch(&g.sh->error, 1);
           }
         }
-        double s = 0.0;
-#pragma unroll
-        for (int t = 0; t < ROWS; ++t) s = fma(rr[t], rr[t], s);
-        m = __shfl_sync(0xffffffffu, warp_sum(s), 0);
-        ++rescored;
+        slot = __shfl_sync(0xffffffffu, slot, 0);
+        if (slot >= 0) {
+          uint8_t* dst = cand_path(vs, slot, n);
+          for (int r = lane; r < n; r += 32) dst[r] = xs[r];
+          __syncwarp();
+          if (lane == 0) {
+            vs->cand_ped[slot] = ped;
+            lock_release(&vs->lock);
+          }
+        }
+        if (lane == 0) atomicMin(&vs->r2bits, __float_as_uint(ped));
+        if (ped < r2) {
+          r2 = ped;
+          bnd = prune_bound(r2, E, n);
+        }
+        continue;
       }
-      bool better = m < win_m;
-      if (!better && m == win_m && win >= 0) {
-        // tie: lexicographically smaller index vector, top row first
-        for (int j = n - 1; j >= 0; --j) {
-          const int x1 = cand_x[q * pp + j], x2 = cand_x[win * pp + j];
-          if (x1 != x2) {
-            better = x1 < x2;
+      if (a.budget > 0 && committed + nodes >= a.budget) {
+        if (lane == 0) atomicExch(&vs->budget_hit, 1);
+        break;
+      }
+      // descend into child k: push level i, update the residuals of the rows below
+      const float av = (float)(2 * k - (P - 1)) * alpha;
+      if (lane == 0) {
+        lv_ped[i] = ped_par;
+        lv_c[i] = c;
+        lv_u[i] = u;
+        lv_lohi[i] = (lo + 1) | (hi << 16);
+        xs[i] = (uint8_t)k;
+      }
+      const float* zin = zs + col_off(i);
+      float* zout = zs + col_off(i - 1);
+      const float* rc = Rc + col_off(i);
+      float cnext = 0.0f;
+#pragma unroll
+      for (int t = 0; t < ROWS; ++t) {
+        const int r = lane + 32 * t;
+        if (r < i) {
+          const float z = fmaf(-rc[r], av, zin[r]);
+          zout[r] = z;
+          if (r == i - 1) cnext = z;
+        }
+      }
+      --i;
+      c = __shfl_sync(0xffffffffu, cnext, i & 31);
+      __syncwarp();
+      ped_par = ped;
+      rii = lv_rii[i];
+      u = fmaf(c, lv_rinv[i], uoff);
+      lo = min(max((int)ceilf(u - 0.5f), 0), P - 1);
+      hi = lo + 1;
+      ++nodes;
+      flops += 2 * (n - 1 - i) + 4 * P;
+
+      // periodic: radius refresh, budget, and splitting while warps are idle
+      if (++since >= kSplitEvery) {
+        since = 0;
+        const float gr2 = __uint_as_float(
+            __shfl_sync(0xffffffffu, lane == 0 ? *(volatile unsigned int*)&vs->r2bits : 0u, 0));
+        if (gr2 < r2) {
+          r2 = gr2;
+          bnd = prune_bound(r2, E, n);
+        }
+        if (a.budget > 0) {
+          unsigned long long tot = 0;
+          if (lane == 0) {
+            tot = atomicAdd(&vs->nodes, (unsigned long long)nodes) + (unsigned long long)nodes;
+            if (tot >= (unsigned long long)a.budget) atomicExch(&vs->budget_hit, 1);
+          }
+          int bh = 0;
+          if (lane == 0) bh = *(volatile int*)&vs->budget_hit;
+          tot = __shfl_sync(0xffffffffu, tot, 0);
+          bh = __shfl_sync(0xffffffffu, bh, 0);
+          nodes = 0;
+          committed = (long long)tot;
+          if (tot >= (unsigned long long)a.budget || bh) {
+            stop = true;
             break;
           }
         }
-      }
-      if (better) {
-        win = q;
-        win_m = m;
+        const int idle = (a.flags & MDX_SEQUENTIAL_SEARCH)
+                             ? 0
+                             : __shfl_sync(0xffffffffu, lane == 0 ? *(volatile int*)&g.sh->idle : 0, 0);
+        if (idle > 0) {
+          // top-most level (>= 1) with untried children, counting the current one
+          int lsplit = -1;
+          for (int l = top; l >= i && l >= kMinSplitLevel; --l) {
+            int llo, lhi;
+            if (l == i) {
+              llo = lo;
+              lhi = hi;
+            } else {
+              const int lh = lv_lohi[l];
+              llo = (lh & 0xffff) - 1;
+              lhi = lh >> 16;
+            }
+            if (llo >= 0 || lhi < P) {
+              lsplit = l;
+              break;
+            }
+          }
+          if (lsplit >= kMinSplitLevel) {
+            int llo, lhi;
+            float lc, lu, lped, lrii;
+            if (lsplit == i) {
+              llo = lo;
+              lhi = hi;
+              lc = c;
+              lu = u;
+              lped = ped_par;
+              lrii = rii;
+            } else {
+              const int lh = lv_lohi[lsplit];
+              llo = (lh & 0xffff) - 1;
+              lhi = lh >> 16;
+              lc = lv_c[lsplit];
+              lu = lv_u[lsplit];
+              lped = lv_ped[lsplit];
+              lrii = lv_rii[lsplit];
+            }
+            // remaining children inside the sphere, in SE order (warp-uniform):
+            // counted first, then written, so no per-child arrays are needed
+            int cnt = 0;
+            {
+              int a_lo = llo, a_hi = lhi;
+              while (a_lo >= 0 || a_hi < P) {
+                int kk;
+                if (a_hi >= P || (a_lo >= 0 && fabsf(lu - (float)a_lo) <= fabsf((float)a_hi - lu))) kk = a_lo--;
+                else kk = a_hi++;
+                const float d = fmaf(-lrii, (float)(2 * kk - (P - 1)) * alpha, lc);
+                if (!(fmaf(d, d, lped) < bnd)) break;
+                ++cnt;
+              }
+            }
+            long long base_slot = -1;
+            if (cnt > 0 && lane == 0) {
+              atomicAdd(&vs->pending, cnt);
+              atomicAdd(&g.sh->outstanding, cnt);
+              base_slot = queue_reserve(g, cnt);
+              if (base_slot < 0) {
+                atomicSub(&vs->pending, cnt);
+                atomicSub(&g.sh->outstanding, cnt);
+              }
+            }
+            base_slot = __shfl_sync(0xffffffffu, base_slot, 0);
+            if (base_slot >= 0) {
+              for (int q = 0; q < cnt; ++q) {
+                int kk;
+                if (lhi >= P || (llo >= 0 && fabsf(lu - (float)llo) <= fabsf((float)lhi - lu))) kk = llo--;
+                else kk = lhi++;
+                const float d = fmaf(-lrii, (float)(2 * kk - (P - 1)) * alpha, lc);
+                const float pd = fmaf(d, d, lped);
+                const unsigned long long sl = (unsigned long long)base_slot + q;
+                SdTask* t = g.queue + ((unsigned)sl & (g.qcap - 1));
+                int wok = 1;
+                if (lane == 0) {
+                  wok = slot_writable(g, t, sl);
+                  if (!wok) {
+                    // error recorded; the task is dropped (this task still holds the
+                    // vector open, so its pending count cannot reach zero here)
+                    atomicExch(&g.sh->error, 3);
+                    atomicSub(&vs->pending, 1);
+                    atomicSub(&g.sh->outstanding, 1);
+                  }
+                }
+                wok = __shfl_sync(0xffffffffu, wok, 0);
+                if (!wok) continue;
+                for (int j = lsplit + 1 + lane; j < n; j += 32) t->x[j] = xs[j];
+                if (lane == 0) {
+                  t->x[lsplit] = (uint8_t)kk;
+                  t->v = v;
+                  t->level = lsplit - 1;
+                  t->ped = pd;
+                }
+                __threadfence();
+                __syncwarp();
+                if (lane == 0) atomicExch(&t->seq, (g.epoch << 32) | (sl + 1ull));
+              }
+              // the donated children are gone from this warp's search
+              if (lsplit == i) {
+                lo = -1;
+                hi = P;
+              } else if (lane == 0) {
+                lv_lohi[lsplit] = 0 | (P << 16);
+              }
+              __syncwarp();
+            }
+          }
+        }
       }
     }
 
-    for (int j = lane; j < a.n_tx; j += 32) {
-      uint8_t s = 0;
-      if (win >= 0) s = (uint8_t)(cand_x[win * pp + 2 * j] * P + cand_x[win * pp + 2 * j + 1]);
-      a.sym_out[(size_t)v * a.n_tx + j] = s;
-    }
+    // ------------------------------------------------ task done: account
     if (lane == 0) {
-      a.metric_out[v] = (win >= 0) ? win_m : (double)INFINITY;
-      a.vstatus[v] = budget_hit ? MDX_V_BUDGET_EXCEEDED : (restarts > 0 ? MDX_V_EMPTY_RETRIED : MDX_V_OK);
-      if (a.stats) {
-        a.stats[(size_t)v * kStats + 0] = nodes;
-        a.stats[(size_t)v * kStats + 1] = peds;
-        a.stats[(size_t)v * kStats + 2] = restarts;
-        a.stats[(size_t)v * kStats + 3] = rescored;
-        a.stats[(size_t)v * kStats + 4] = flops;
+      atomicAdd(&vs->nodes, (unsigned long long)nodes);
+      atomicAdd(&vs->peds, (unsigned long long)peds);
+      atomicAdd(&vs->flops, (unsigned long long)flops);
+      __threadfence();
+    }
+    int last = 0;
+    if (lane == 0) last = (atomicSub(&vs->pending, 1) == 1);
+    last = __shfl_sync(0xffffffffu, last, 0);
+    if (last) {
+      __threadfence();
+      volatile SdVec* vv = vs;
+      const int nc = __shfl_sync(0xffffffffu, lane == 0 ? vv->ncand : 0, 0);
+      const bool bh = __shfl_sync(0xffffffffu, lane == 0 ? vv->budget_hit : 0, 0) != 0;
+      const float r2s = __shfl_sync(0xffffffffu, lane == 0 ? vv->r2_start : 0.0f, 0);
+      const int rs = __shfl_sync(0xffffffffu, lane == 0 ? vv->restarts : 0, 0);
+      if (nc == 0 && !bh && r2s < INFINITY && rs < 64) {
+        // empty sphere: double the radius (r^2 <- 4 r^2) and search again
+        int requeued = 0;
+        if (lane == 0) {
+          const float nr2 = 4.0f * r2s;
+          vs->r2_start = nr2;
+          vs->r2bits = __float_as_uint(nr2);
+          vs->restarts += 1;
+          vs->pending = 1;
+          __threadfence();
+          // re-queue the root as a task of this vector
+          long long sl = queue_reserve(g, 1);
+          SdTask* t = sl >= 0 ? g.queue + ((unsigned)sl & (g.qcap - 1)) : nullptr;
+          if (t && !slot_writable(g, t, (unsigned long long)sl)) {
+            atomicExch(&g.sh->error, 3);
+            t = nullptr;
+          }
+          if (t) {
+            t->v = v;
+            t->level = n - 1;
+            t->ped = 0.0f;
+            __threadfence();
+            atomicExch(&t->seq, (g.epoch << 32) | ((unsigned long long)sl + 1ull));
+            requeued = 1;
+          } else {
+            vs->pending = 0;
+            atomicExch(&g.sh->error, 4);
+          }
+        }
+        requeued = __shfl_sync(0xffffffffu, requeued, 0);
+        __syncwarp();
+        if (requeued) continue;  // outstanding stays: the re-queued root replaces this task
+      }
+      // FP64 re-scoring of the candidates within FP32 error of the best
+      float best = INFINITY;
+      for (int q = 0; q < nc; ++q) best = fminf(best, vv->cand_ped[q]);
+      const float keep = prune_bound(best, E, n);
+      const double* R64 = a.R64 + (size_t)v * tri_stride64(n);
+      const double* y64 = a.yb64 + (size_t)v * vec_stride64(n);
+      // candidates are read through L2 (other warps wrote them) into this
+      // warp's path buffer; the winner's indices are kept in registers
+      int win = -1;
+      double win_m = INFINITY;
+      long long rescored = 0;
+      uint8_t wsym[(MDX_MAX_TX + 31) / 32 * 2];
+      for (int q = 0; q < nc; ++q) {
+        if (!(vv->cand_ped[q] <= keep)) continue;
+        const uint8_t* cx = cand_path(vs, q, n);
+        __syncwarp();
+        for (int r = lane; r < n; r += 32) xs[r] = __ldcg(cx + r);
+        __syncwarp();
+        double m;
+        if (a.flags & MDX_NO_RESCORE) {
+          m = (double)vv->cand_ped[q];
+        } else {
+          m = rescore_fp64_warp(n, P, a.alpha64, R64, y64, xs, lane);
+          ++rescored;
+        }
+        bool better = m < win_m;
+        if (!better && m == win_m && win >= 0) {
+          // tie: lexicographically smaller index vector, top row first
+          const uint8_t* wx = cand_path(vs, win, n);
+          for (int j = n - 1; j >= 0; --j) {
+            const uint8_t w1 = xs[j], w2 = __ldcg(wx + j);
+            if (w1 != w2) {
+              better = w1 < w2;
+              break;
+            }
+          }
+        }
+        if (better) {
+          win = q;
+          win_m = m;
+#pragma unroll
+          for (int t = 0; t < (MDX_MAX_TX + 31) / 32; ++t) {
+            const int j = lane + 32 * t;
+            if (j < a.n_tx) {
+              wsym[2 * t] = xs[2 * j];
+              wsym[2 * t + 1] = xs[2 * j + 1];
+            }
+          }
+        }
+      }
+#pragma unroll
+      for (int t = 0; t < (MDX_MAX_TX + 31) / 32; ++t) {
+        const int j = lane + 32 * t;
+        if (j < a.n_tx)
+          a.sym_out[(size_t)v * a.n_tx + j] = win >= 0 ? (uint8_t)(wsym[2 * t] * P + wsym[2 * t + 1]) : 0;
+      }
+      if (lane == 0) {
+        a.metric_out[v] = (win >= 0) ? win_m : (double)INFINITY;
+        a.vstatus[v] = bh ? MDX_V_BUDGET_EXCEEDED : (vv->restarts > 0 ? MDX_V_EMPTY_RETRIED : MDX_V_OK);
+        if (a.stats) {
+          a.stats[(size_t)v * kStats + 0] = (long long)vv->nodes;
+          a.stats[(size_t)v * kStats + 1] = (long long)vv->peds;
+          a.stats[(size_t)v * kStats + 2] = vv->restarts;
+          a.stats[(size_t)v * kStats + 3] = rescored;
+          a.stats[(size_t)v * kStats + 4] = (long long)vv->flops;
+        }
       }
     }
     __syncwarp();
+    if (lane == 0) atomicSub(&g.sh->outstanding, 1);
   }
 }
 
 template <int ROWS>
-cudaError_t launch_rows(const SearchArgs& a, int num_sms, cudaStream_t s) {
-  // as many warps per CTA (up to kWarps) as fit in 200 KB of shared memory
-  int wpc = (int)((200u * 1024u) / sd_warp_bytes(a.n));
-  if (wpc > kWarps) wpc = kWarps;
+cudaError_t launch_rows(const SdArgs& g, int num_sms, cudaStream_t s) {
+  // as many warps per CTA (up to kWarpsMax) as fit in 200 KB of shared memory
+  int wpc = (int)((200u * 1024u) / sd_warp_bytes(g.a.n));
+  if (wpc > kWarpsMax) wpc = kWarpsMax;
   if (wpc < 1) return cudaErrorInvalidConfiguration;
-  const size_t smem = sd_warp_bytes(a.n) * wpc;
-  cudaError_t e = cudaFuncSetAttribute(sd_kernel<ROWS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)smem);
+  const size_t smem = sd_warp_bytes(g.a.n) * wpc;
+  cudaError_t e = cudaFuncSetAttribute(sd_kernel<ROWS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   int per_sm = 0;
   e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, sd_kernel<ROWS>, wpc * 32, smem);
   if (e != cudaSuccess) return e;
   if (per_sm < 1) return cudaErrorInvalidConfiguration;
-  int grid = per_sm * num_sms;
-  const int need = (a.batch + wpc - 1) / wpc;
-  if (grid > need) grid = need;
-  sd_kernel<ROWS><<<grid, wpc * 32, smem, s>>>(a);
+  // a persistent grid: every warp stays until the queue and the vectors are done
+  const int grid = per_sm * num_sms;
+  sd_kernel<ROWS><<<grid, wpc * 32, smem, s>>>(g);
   return cudaGetLastError();
 }
 
 }  // namespace
 
-cudaError_t launch_sd(const SearchArgs& a, int num_sms, cudaStream_t s) {
+size_t sd_vec_state_bytes(int n) { return vec_state_bytes(n); }
+size_t sd_task_bytes() { return sizeof(SdTask); }
+size_t sd_shared_bytes() { return sizeof(SdShared); }
+size_t sd_error_offset() { return offsetof(SdShared, error); }
+
+cudaError_t launch_sd(const SearchArgs& a, const SdWorkspace& w, int num_sms, cudaStream_t s) {
   if (a.batch <= 0) return cudaSuccess;
-  if (a.n <= 32) return launch_rows<1>(a, num_sms, s);
-  if (a.n <= 64) return launch_rows<2>(a, num_sms, s);
-  if (a.n <= 128) return launch_rows<4>(a, num_sms, s);
-  return launch_rows<7>(a, num_sms, s);
+  if (a.n > kTaskPath) return cudaErrorInvalidConfiguration;
+  SdArgs g;
+  g.a = a;
+  g.sh = reinterpret_cast<SdShared*>(w.shared);
+  g.queue = reinterpret_cast<SdTask*>(w.queue);
+  g.qcap = w.qcap;
+  g.vstate = w.vstate;
+  g.vstride = vec_state_bytes(a.n);
+  g.epoch = w.epoch;
+  cudaError_t e = cudaMemsetAsync(w.shared, 0, sizeof(SdShared), s);
+  if (e != cudaSuccess) return e;
+  if (a.n <= 32) return launch_rows<1>(g, num_sms, s);
+  if (a.n <= 64) return launch_rows<2>(g, num_sms, s);
+  if (a.n <= 128) return launch_rows<4>(g, num_sms, s);
+  return launch_rows<7>(g, num_sms, s);
 }
 
 }  // namespace mdx

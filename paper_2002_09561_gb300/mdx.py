@@ -19,7 +19,7 @@ LIB_PATH = os.path.join(HERE, "libmdx.so")
 
 MDX_OK, MDX_EINVAL, MDX_EUNSUPPORTED, MDX_ENOMEM, MDX_ECUDA = 0, -1, -2, -3, -4
 MDX_V_OK, MDX_V_EMPTY_RETRIED, MDX_V_BUDGET_EXCEEDED, MDX_V_SINGULAR = 0, 1, 2, 3
-MDX_HOST_BUFFERS, MDX_NO_RESCORE, MDX_LEARNED_RADIUS = 1, 2, 4
+MDX_HOST_BUFFERS, MDX_NO_RESCORE, MDX_LEARNED_RADIUS, MDX_SEQUENTIAL_SEARCH = 1, 2, 4, 8
 MDX_MAX_TX, MDX_MAX_RX, MDX_MAX_K = 100, 128, 256
 
 # Every symbol the header declares; the library must export all of them.
@@ -117,11 +117,13 @@ class Context:
         self.check(lib().mdx_profile(self._h, int(enable)), "mdx_profile")
 
     def profile_read(self):
-        """(QR ms, search ms, calls) summed since the last read."""
+        """(QR ms, search ms, calls) summed since the last read; the error word
+        of the last sphere-decoder launch is kept in self.last_sd_error."""
         import numpy as np
 
-        out = np.zeros(3)
+        out = np.zeros(4)
         self.check(lib().mdx_profile_read(self._h, ctypes.c_void_p(out.ctypes.data)), "mdx_profile_read")
+        self.last_sd_error = int(out[3])
         return float(out[0]), float(out[1]), int(out[2])
 
     def close(self):

@@ -32,7 +32,7 @@ def env():
     __graft_entry__.build()
     from paper_2002_09561_gb300 import mdx
 
-    ctx = mdx.Context(0, max_batch=4096, max_n_rx=100, max_n_tx=100)
+    ctx = mdx.Context(0, max_batch=6000, max_n_rx=100, max_n_tx=100)
     yield torch, mdx, ctx
     ctx.close()
 
@@ -95,14 +95,20 @@ def test_sd_4x4_4qam_equals_brute_force(env):
     assert (gpu[2] == 0).all()
 
 
-@pytest.mark.parametrize("snr,B", [(8.0, 48), (12.0, 300), (16.0, 600), (20.0, 600)])
+@pytest.mark.parametrize("snr,B", [(8.0, 48), (12.0, 300), (16.0, 600), (20.0, 6000)])
 def test_sd_16x16_16qam(env, snr, B):
     w = wl.generate(int(snr) + 100, B, 16, 16, 16, snr)
-    gpu = _run(env, "sd", w, 16, radius="paper")
+    torch, mdx, ctx = env
     ref = oracle.detect_batch("sd", w["H"], w["y"], w["noise_var"], 16, radius="paper", want_gap=True)
+    # subtrees shared between warps: the same exact answers, usually far fewer
+    # nodes (a good leaf found in one subtree shrinks the radius for all)
+    gpu = _run(env, "sd", w, 16, radius="paper")
     _compare(gpu, ref, SD_GAP, label=f"sd 16x16 16-QAM {snr} dB")
-    # visited nodes: the FP32 slack can only add nodes near the sphere's surface
-    g_nodes, o_nodes = gpu[3][:, 0], ref["stats"][:, 0]
+    # one warp per tree: the sequential search, whose visited nodes match the
+    # oracle's up to the FP32 slack near the sphere's surface
+    seq = _run(env, "sd", w, 16, radius="paper", flags=mdx.MDX_SEQUENTIAL_SEARCH)
+    _compare(seq, ref, SD_GAP, label=f"sd sequential 16x16 16-QAM {snr} dB")
+    g_nodes, o_nodes = seq[3][:, 0], ref["stats"][:, 0]
     assert np.all(g_nodes >= 1)
     assert abs(g_nodes.sum() / o_nodes.sum() - 1.0) < 0.05
 
