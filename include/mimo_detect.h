@@ -173,6 +173,51 @@ mdx_status mdx_count_errors(mdx_ctx* ctx, int batch, int n_tx, int qam, const ui
                             const uint8_t* sym_true, int64_t* counts_out, int flags,
                             void* stream);
 
+/* ---------------------------------------------------------------------------
+ * Learned initial radius (the paper has no learned component; its radius is
+ * the fixed r^2 = N M sigma^2 of Sec. III-B).  A multilayer perceptron with
+ * two hidden layers of 256 ReLU units reads, per received vector,
+ *   x = [R upper triangle in column-packed order (entry (r, c), r <= c, at
+ *        c (c + 1) / 2 + r), ybar, SNR_dB / 30]  (zero-padded to d_in)
+ * and outputs o (d_out values, zero-padded): o[0] predicts
+ * log(d_ML / sigma^2), trained with a pinball loss at the 0.9 quantile so
+ * that the radius r^2 = sigma^2 exp(o[0]) usually contains the ML point;
+ * o[1 + r P + k] are logits that real row r of the ML point has PAM index k
+ * (cross-entropy, weight 0.2).  Weights are BF16, accumulation FP32, on the
+ * tensor cores (tcgen05); FP32 master weights and Adam moments are kept on
+ * the device.  detect_sd with MDX_LEARNED_RADIUS starts from the predicted
+ * radius and doubles it on an empty sphere, so its answer is unchanged.
+ * Parameter vector (FP32, this order): W1 [256][d_in], b1 [256],
+ * W2 [256][256], b2 [256], W3 [d_out][256], b3 [d_out].
+ * Models exist for square systems n_rx = n_tx <= 32. */
+size_t mdx_mlp_param_count(int n_tx, int qam);
+mdx_status mdx_mlp_dims(int n_tx, int qam, int* d_in, int* d_out);
+/* Create (or replace) the context's model for n_tx x n_tx, qam, with a
+ * training workspace for batches of up to max_train_batch vectors, weights
+ * drawn He-uniform from `seed`.  Allocates device memory (model, moments,
+ * activations for max(max_batch, max_train_batch) rows). */
+mdx_status mdx_mlp_init(mdx_ctx* ctx, int n_tx, int qam, int max_train_batch, unsigned long long seed);
+/* Copy the FP32 parameter vector from / to HOST memory (count values). */
+mdx_status mdx_mlp_set_params(mdx_ctx* ctx, const float* params, size_t count);
+mdx_status mdx_mlp_get_params(mdx_ctx* ctx, float* params, size_t count);
+/* QR + features + forward pass for `batch` vectors (device pointers, layouts
+ * as for detect_*): out float [batch][d_out]; feat_out float [batch][d_in]
+ * (the features before BF16 rounding) or NULL. */
+mdx_status mdx_mlp_predict(mdx_ctx* ctx, const mdx_params* p, int batch, const double* H, const double* y,
+                           const double* noise_var, float* out, float* feat_out, void* stream);
+/* One training step on `batch` vectors with their ML targets (ml_sym
+ * uint8 [batch][n_tx] and ml_metric double [batch], as returned by
+ * detect_sd): forward, loss, backward on the tensor cores; if `update`,
+ * one Adam step with learning rate lr (beta 0.9 / 0.999).  grad_out float
+ * [param_count] receives the gradient and loss_out float [2] the batch's
+ * (pinball, cross-entropy) losses; both device pointers or NULL. */
+mdx_status mdx_mlp_train_step(mdx_ctx* ctx, const mdx_params* p, int batch, const double* H, const double* y,
+                              const double* noise_var, const uint8_t* ml_sym, const double* ml_metric, float lr,
+                              int update, float* grad_out, float* loss_out, void* stream);
+/* Waits for the device and reports whether a bounded wait inside a model
+ * kernel expired (*err_out != 0). */
+mdx_status mdx_mlp_error(mdx_ctx* ctx, int* err_out);
+
 /* K-best detection for callers that may not allocate device memory.
  * (The paper has no counterpart; this is a deployment variant of
  * detect_kbest.)  Some callers cannot allocate once they are running: a
@@ -205,8 +250,10 @@ mdx_status detect_kbest_noalloc(const mdx_params* p, int batch, const double* H,
  * 1024 calls are kept).  mdx_profile_read waits for those events, writes
  * ms_out[0] = summed QR time, ms_out[1] = summed search time (milliseconds),
  * ms_out[2] = number of calls recorded, ms_out[3] = the error word of the
- * last detect_sd launch (non-zero if a bounded wait inside it expired), and
- * clears the record.  Not part of
+ * last detect_sd launch (non-zero if a bounded wait inside it expired),
+ * ms_out[4..7] = that launch's subtree-splitting counters (checks that saw
+ * idle warps, checks that donated, tasks donated, checks with no level to
+ * split), and clears the record.  ms_out must hold 8 doubles.  Not part of
  * the detection path; enable = 0 turns it off. */
 mdx_status mdx_profile(mdx_ctx* ctx, int enable);
 mdx_status mdx_profile_read(mdx_ctx* ctx, double* ms_out);

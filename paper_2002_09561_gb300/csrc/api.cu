@@ -26,6 +26,8 @@ struct mdx_ctx {
   void* sd_queue = nullptr;
   unsigned char* sd_vstate = nullptr;
   unsigned long long sd_epoch = 0;
+  // learned radius model (mdx_mlp_init), null until created
+  mdx::MlpState* mlp = nullptr;
   // staging for MDX_HOST_BUFFERS
   double* sH = nullptr;
   double* sy = nullptr;
@@ -104,6 +106,10 @@ cudaError_t alloc(mdx_ctx* c, T** p, size_t count) {
 }
 
 void free_all(mdx_ctx* c) {
+  if (c->mlp) {
+    mlp_free(c->mlp);
+    c->mlp = nullptr;
+  }
   for (int i = 0; i < mdx_ctx::kProfSlots; ++i)
     for (int k = 0; k < 3; ++k)
       if (c->prof_ev[i][k]) cudaEventDestroy(c->prof_ev[i][k]);
@@ -148,8 +154,14 @@ mdx_status run_detect(int algo, mdx_ctx* c, const mdx_params* p, int batch, cons
   const double r0 = p->init_radius_sq;
   if (isnan(r0) || r0 == 0.0) return fail(c, MDX_EINVAL, "init_radius_sq must be > 0, < 0 or INFINITY");
   int radius_mode = isinf(r0) ? (r0 > 0 ? RADIUS_NONE : RADIUS_PAPER) : (r0 < 0 ? RADIUS_PAPER : RADIUS_VALUE);
-  if (p->flags & MDX_LEARNED_RADIUS)
-    return fail(c, MDX_EUNSUPPORTED, "MDX_LEARNED_RADIUS needs a loaded model");
+  const bool learned = (p->flags & MDX_LEARNED_RADIUS) != 0;
+  if (learned) {
+    if (algo != ALGO_SD) return fail(c, MDX_EUNSUPPORTED, "MDX_LEARNED_RADIUS applies to detect_sd");
+    if (!c->mlp || mlp_ntx(c->mlp) != M || mlp_qam(c->mlp) != p->qam || N != M)
+      return fail(c, MDX_EUNSUPPORTED, "MDX_LEARNED_RADIUS needs a model for this %dx%d %d-QAM (mdx_mlp_init)", N, M,
+                  p->qam);
+    if (!nv) return fail(c, MDX_EINVAL, "noise_var needed for the learned radius");
+  }
   if (p->node_budget < 0) return fail(c, MDX_EINVAL, "node_budget < 0");
   if (algo != ALGO_SD) {
     if (p->K < 1 || p->K > MDX_MAX_K) return fail(c, MDX_EINVAL, "K %d not in 1..%d", p->K, MDX_MAX_K);
@@ -216,6 +228,15 @@ mdx_status run_detect(int algo, mdx_ctx* c, const mdx_params* p, int batch, cons
   e = launch_qr(batch, N, M, dH, dy, q, s);
   if (e != cudaSuccess) return cuda_fail(c, e, "QR launch");
 
+  if (learned) {
+    // radius proposed by the network: r^2 = sigma^2 exp(o_0)
+    const int rows = round_up(batch, 128);
+    e = mlp_features(c->mlp, batch, rows, c->R32, c->yb32, dnv, false, nullptr, s);
+    if (e == cudaSuccess) e = mlp_forward(c->mlp, rows, false, s);
+    if (e == cudaSuccess) e = mlp_radius(c->mlp, batch, dnv, s);
+    if (e != cudaSuccess) return cuda_fail(c, e, "learned radius");
+    radius_mode = RADIUS_PER_VECTOR;
+  }
   SearchArgs a{};
   a.batch = batch;
   a.n = n;
@@ -230,7 +251,7 @@ mdx_status run_detect(int algo, mdx_ctx* c, const mdx_params* p, int batch, cons
   a.yb64 = c->yb64;
   a.singular = c->singular;
   a.noise_var = dnv;
-  a.r2_vec = nullptr;
+  a.r2_vec = learned ? mlp_r2(c->mlp) : nullptr;
   a.radius_mode = radius_mode;
   a.radius_value = r0;
   a.K = p->K;
@@ -468,6 +489,177 @@ mdx_status mdx_count_errors(mdx_ctx* c, int batch, int n_tx, int qam, const uint
   return MDX_OK;
 }
 
+size_t mdx_mlp_param_count(int n_tx, int qam) {
+  if (n_tx < 1 || n_tx > MDX_MAX_TX || pam_of(qam) < 0) return 0;
+  return (size_t)mlp_count(n_tx, qam);
+}
+
+mdx_status mdx_mlp_dims(int n_tx, int qam, int* d_in, int* d_out) {
+  if (n_tx < 1 || n_tx > MDX_MAX_TX || pam_of(qam) < 0 || !d_in || !d_out) return MDX_EINVAL;
+  mlp_dims(n_tx, qam, d_in, d_out);
+  return MDX_OK;
+}
+
+mdx_status mdx_mlp_init(mdx_ctx* c, int n_tx, int qam, int max_train_batch, unsigned long long seed) {
+  if (!c) return MDX_EINVAL;
+  if (n_tx < 1 || n_tx > c->max_tx || n_tx > 32 || pam_of(qam) < 0)
+    return fail(c, MDX_EINVAL, "the learned radius supports n_tx <= 32 within the context");
+  if (max_train_batch < 0) return fail(c, MDX_EINVAL, "max_train_batch < 0");
+  DeviceGuard g(c->device);
+  if (c->mlp) {
+    mlp_free(c->mlp);
+    c->mlp = nullptr;
+  }
+  const int cap = max_train_batch > c->max_batch ? max_train_batch : c->max_batch;
+  MlpState* m = nullptr;
+  cudaError_t e = mlp_alloc(&m, n_tx, qam, cap);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return fail(c, MDX_ENOMEM, "model workspace: %s", cudaGetErrorString(e));
+  }
+  c->mlp = m;
+  // He-uniform weights from a SplitMix64 stream; zero biases except the radius
+  // head, which starts at log(n_tx) (the mean of d_ML / sigma^2 is about n_tx)
+  int D0, DO;
+  mlp_dims(n_tx, qam, &D0, &DO);
+  const int n = 2 * n_tx, P = pam_of(qam);
+  const int din = n * (n + 1) / 2 + n + 1, dout = 1 + n * P;
+  const long long cnt = mlp_count(n_tx, qam);
+  float* h = new float[cnt]();
+  uint64_t st = seed * 0x9E3779B97F4A7C15ull + 0x5DEECE66Dull;
+  auto uni = [&]() {
+    uint64_t z = (st += 0x9E3779B97F4A7C15ull);
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    z ^= z >> 31;
+    return (double)(z >> 11) * (1.0 / 9007199254740992.0) * 2.0 - 1.0;
+  };
+  const int H = 256;
+  size_t o = 0;
+  const double a1 = sqrt(6.0 / din), a2 = sqrt(6.0 / H), a3 = 0.1 * sqrt(6.0 / H);
+  for (int r = 0; r < H; ++r)
+    for (int k = 0; k < D0; ++k) h[o++] = k < din ? (float)(a1 * uni()) : 0.0f;
+  o += H;  // b1
+  for (int r = 0; r < H; ++r)
+    for (int k = 0; k < H; ++k) h[o++] = (float)(a2 * uni());
+  o += H;  // b2
+  for (int r = 0; r < DO; ++r)
+    for (int k = 0; k < H; ++k) h[o++] = r < dout ? (float)(a3 * uni()) : 0.0f;
+  h[o] = (float)log((double)n_tx);  // b3[0]
+  e = cudaMemcpy(mlp_params(m), h, sizeof(float) * cnt, cudaMemcpyHostToDevice);
+  delete[] h;
+  if (e == cudaSuccess) e = mlp_pack(m, nullptr);
+  if (e == cudaSuccess) e = cudaDeviceSynchronize();
+  if (e != cudaSuccess) return cuda_fail(c, e, "model init");
+  c->bytes += mlp_bytes(m);
+  return MDX_OK;
+}
+
+mdx_status mdx_mlp_set_params(mdx_ctx* c, const float* host, size_t count) {
+  if (!c || !host) return MDX_EINVAL;
+  if (!c->mlp) return fail(c, MDX_EUNSUPPORTED, "no model (mdx_mlp_init)");
+  if (count != (size_t)mlp_count(mlp_ntx(c->mlp), mlp_qam(c->mlp))) return fail(c, MDX_EINVAL, "parameter count");
+  DeviceGuard g(c->device);
+  cudaError_t e = cudaMemcpy(mlp_params(c->mlp), host, sizeof(float) * count, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = mlp_pack(c->mlp, nullptr);
+  if (e == cudaSuccess) e = cudaDeviceSynchronize();
+  if (e != cudaSuccess) return cuda_fail(c, e, "set params");
+  return MDX_OK;
+}
+
+mdx_status mdx_mlp_get_params(mdx_ctx* c, float* host, size_t count) {
+  if (!c || !host) return MDX_EINVAL;
+  if (!c->mlp) return fail(c, MDX_EUNSUPPORTED, "no model (mdx_mlp_init)");
+  if (count != (size_t)mlp_count(mlp_ntx(c->mlp), mlp_qam(c->mlp))) return fail(c, MDX_EINVAL, "parameter count");
+  DeviceGuard g(c->device);
+  cudaError_t e = cudaDeviceSynchronize();
+  if (e == cudaSuccess) e = cudaMemcpy(host, mlp_params(c->mlp), sizeof(float) * count, cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return cuda_fail(c, e, "get params");
+  return MDX_OK;
+}
+
+// QR + features for a batch of device inputs; returns rows (padded batch) or <0.
+static mdx_status mlp_prepare(mdx_ctx* c, const mdx_params* p, int batch, const double* H, const double* y,
+                              const double* nv, bool train, float* feat_out, cudaStream_t s, int* rows_out) {
+  if (!c) return MDX_EINVAL;
+  if (!p) return fail(c, MDX_EINVAL, "params is NULL");
+  if (!c->mlp) return fail(c, MDX_EUNSUPPORTED, "no model (mdx_mlp_init)");
+  if (p->flags & MDX_HOST_BUFFERS) return fail(c, MDX_EUNSUPPORTED, "device pointers only");
+  if (batch < 1 || batch > mlp_cap(c->mlp) || batch > c->max_batch)
+    return fail(c, MDX_EUNSUPPORTED, "batch %d outside 1..%d", batch, c->max_batch);
+  if (p->n_tx != mlp_ntx(c->mlp) || p->n_rx != p->n_tx || p->qam != mlp_qam(c->mlp))
+    return fail(c, MDX_EINVAL, "the model was built for %dx%d %d-QAM", mlp_ntx(c->mlp), mlp_ntx(c->mlp),
+                mlp_qam(c->mlp));
+  if (!H || !y || !nv) return fail(c, MDX_EINVAL, "NULL input");
+  if (!aligned16(H) || !aligned16(y)) return fail(c, MDX_EINVAL, "H and y must be 16-byte aligned");
+  const void* ptrs[] = {H, y, nv};
+  for (const void* q : ptrs)
+    if (!is_device_ptr(q, c->device)) return fail(c, MDX_EINVAL, "pointer %p is not device memory", q);
+  const int rows = round_up(batch, 128);
+  QrOut q{c->R64, c->yb64, c->R32, c->yb32, nullptr, nullptr, c->singular};
+  cudaError_t e = launch_qr(batch, p->n_rx, p->n_tx, H, y, q, s);
+  if (e == cudaSuccess) e = mlp_features(c->mlp, batch, rows, c->R32, c->yb32, nv, train, feat_out, s);
+  if (e != cudaSuccess) return cuda_fail(c, e, "features");
+  *rows_out = rows;
+  return MDX_OK;
+}
+
+mdx_status mdx_mlp_predict(mdx_ctx* c, const mdx_params* p, int batch, const double* H, const double* y,
+                           const double* nv, float* out, float* feat_out, void* stream) {
+  if (!c) return MDX_EINVAL;
+  if (!out) return fail(c, MDX_EINVAL, "NULL output");
+  DeviceGuard g(c->device);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  int rows = 0;
+  mdx_status st = mlp_prepare(c, p, batch, H, y, nv, false, feat_out, s, &rows);
+  if (st != MDX_OK) return st;
+  cudaError_t e = mlp_forward(c->mlp, rows, false, s);
+  int D0, DO;
+  mlp_dims(p->n_tx, p->qam, &D0, &DO);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(out, mlp_outputs(c->mlp), sizeof(float) * DO * (size_t)batch, cudaMemcpyDeviceToDevice, s);
+  if (e != cudaSuccess) return cuda_fail(c, e, "forward");
+  return MDX_OK;
+}
+
+mdx_status mdx_mlp_train_step(mdx_ctx* c, const mdx_params* p, int batch, const double* H, const double* y,
+                              const double* nv, const uint8_t* ml_sym, const double* ml_metric, float lr,
+                              int update, float* grad_out, float* loss_out, void* stream) {
+  if (!c) return MDX_EINVAL;
+  if (!ml_sym || !ml_metric) return fail(c, MDX_EINVAL, "NULL targets");
+  if (!is_device_ptr(ml_sym, c->device) || !is_device_ptr(ml_metric, c->device))
+    return fail(c, MDX_EINVAL, "targets must be device memory");
+  if (!(lr >= 0.0f)) return fail(c, MDX_EINVAL, "learning rate");
+  DeviceGuard g(c->device);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  int rows = 0;
+  mdx_status st = mlp_prepare(c, p, batch, H, y, nv, true, nullptr, s, &rows);
+  if (st != MDX_OK) return st;
+  cudaError_t e = mlp_forward(c->mlp, rows, true, s);
+  if (e == cudaSuccess) e = mlp_backward(c->mlp, batch, rows, ml_metric, nv, ml_sym, s);
+  if (e == cudaSuccess && grad_out)
+    e = cudaMemcpyAsync(grad_out, mlp_grads(c->mlp), sizeof(float) * mlp_count(p->n_tx, p->qam),
+                        cudaMemcpyDeviceToDevice, s);
+  if (e == cudaSuccess && loss_out)
+    e = cudaMemcpyAsync(loss_out, mlp_loss(c->mlp), 2 * sizeof(float), cudaMemcpyDeviceToDevice, s);
+  if (e == cudaSuccess && update) e = mlp_adam(c->mlp, lr, s);
+  if (e != cudaSuccess) return cuda_fail(c, e, "train step");
+  return MDX_OK;
+}
+
+mdx_status mdx_mlp_error(mdx_ctx* c, int* err_out) {
+  if (!c || !err_out) return MDX_EINVAL;
+  if (!c->mlp) {
+    *err_out = 0;
+    return MDX_OK;
+  }
+  DeviceGuard g(c->device);
+  cudaError_t e = cudaDeviceSynchronize();
+  if (e == cudaSuccess) e = cudaMemcpy(err_out, mlp_err(c->mlp), sizeof(int), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return cuda_fail(c, e, "model error word");
+  return MDX_OK;
+}
+
 mdx_status mdx_profile(mdx_ctx* c, int enable) {
   if (!c) return MDX_EINVAL;
   DeviceGuard g(c->device);
@@ -497,9 +689,14 @@ mdx_status mdx_profile_read(mdx_ctx* c, double* ms_out) {
     search += b;
   }
   int err = 0;
+  unsigned int cnt[4] = {0, 0, 0, 0};
   cudaError_t e = cudaMemcpy(&err, static_cast<char*>(c->sd_shared) + sd_error_offset(), sizeof(int),
                              cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess)
+    e = cudaMemcpy(cnt, static_cast<char*>(c->sd_shared) + sd_counters_offset(), sizeof(cnt),
+                   cudaMemcpyDeviceToHost);
   if (e != cudaSuccess) return cuda_fail(c, e, "error word");
+  for (int k = 0; k < 4; ++k) ms_out[4 + k] = cnt[k];
   ms_out[0] = qr;
   ms_out[1] = search;
   ms_out[2] = c->prof_n;

@@ -79,11 +79,38 @@ struct SdWorkspace {
 };
 size_t sd_shared_bytes();
 size_t sd_error_offset();
+size_t sd_counters_offset();
 size_t sd_task_bytes();
 size_t sd_vec_state_bytes(int n);
 cudaError_t launch_sd(const SearchArgs& a, const SdWorkspace& w, int num_sms, cudaStream_t s);
 cudaError_t launch_kbest(const SearchArgs& a, int num_sms, cudaStream_t s);
 cudaError_t launch_hybrid(const SearchArgs& a, int num_sms, cudaStream_t s);
+// Learned radius model (mlp.cu).
+struct MlpState;
+void mlp_dims(int n_tx, int qam, int* D0, int* DO);
+long long mlp_count(int n_tx, int qam);
+cudaError_t mlp_alloc(MlpState** out, int n_tx, int qam, int cap);
+void mlp_free(MlpState* s);
+cudaError_t mlp_pack(MlpState* s, cudaStream_t st);
+cudaError_t mlp_features(MlpState* s, int batch, int rows, const float* R32, const float* yb32, const double* nv,
+                         bool train, float* F, cudaStream_t st);
+cudaError_t mlp_forward(MlpState* s, int rows, bool train, cudaStream_t st);
+cudaError_t mlp_backward(MlpState* s, int batch, int rows, const double* ml_metric, const double* nv,
+                         const uint8_t* ml_sym, cudaStream_t st);
+cudaError_t mlp_adam(MlpState* s, float lr, cudaStream_t st);
+cudaError_t mlp_radius(MlpState* s, int batch, const double* nv, cudaStream_t st);
+// accessors (the struct is private to mlp.cu)
+float* mlp_params(MlpState* s);
+float* mlp_grads(MlpState* s);
+float* mlp_outputs(MlpState* s);
+float* mlp_r2(MlpState* s);
+float* mlp_loss(MlpState* s);
+int* mlp_err(MlpState* s);
+int mlp_cap(MlpState* s);
+int mlp_ntx(MlpState* s);
+int mlp_qam(MlpState* s);
+size_t mlp_bytes(MlpState* s);
+
 cudaError_t launch_count_errors(int batch, int n_tx, int qam, const uint8_t* a, const uint8_t* b,
                                 unsigned long long* counts, cudaStream_t s);
 

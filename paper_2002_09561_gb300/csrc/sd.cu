@@ -8,7 +8,8 @@
 // as its root task.  Warps take work in this order: a queued task, else a
 // fresh vector, else they wait (idle).  While any warp is idle, a busy warp
 // checks every kSplitEvery nodes and donates all untried children of its
-// top-most open level as new tasks, marking that level exhausted.  The only
+// top-most open level whose next child is inside the sphere as new tasks,
+// marking that level exhausted.  The only
 // state the tasks of a vector share is its radius (an FP32 r^2 in global
 // memory, shrunk with atomicMin) and its leaf-candidate list; a per-vector
 // count of unfinished tasks tells the warp finishing the last one to
@@ -50,7 +51,12 @@ struct SdShared {
   int outstanding;  // tasks queued or running (root tasks included)
   int idle;         // warps waiting for work
   int error;        // a bounded wait expired
-  int pad[10];
+  // event counters (read back by mdx_profile_read)
+  unsigned int split_checks;   // periodic checks that saw idle warps
+  unsigned int splits;         // checks that donated at least one task
+  unsigned int donated;        // tasks donated
+  unsigned int no_level;       // checks that found no level to split
+  int pad[6];
 };
 
 namespace {
@@ -60,6 +66,7 @@ constexpr int kCand = 8;         // leaf candidates kept per vector
 constexpr int kSplitEvery = 128; // nodes between split / radius checks
 constexpr int kTaskPath = 224;   // path bytes in a task record (n <= 224)
 constexpr int kMinSplitLevel = 3; // donate only children with at least 3 rows below
+constexpr int kSplitMinNodes = 512; // a task donates only after searching this many nodes
 
 struct SdTask {
   unsigned long long seq;  // (epoch << 32) | (slot index + 1) once written
@@ -334,6 +341,7 @@ __global__ void __launch_bounds__(kWarpsMax * 32) sd_kernel(SdArgs g) {
 
     // -------------------------------------------------- depth-first search
     long long nodes = 0, peds = 0, flops = 0, since = 0;
+    int task_nodes = 0;
     // nodes of this vector already counted by finished or committed tasks
     long long committed = 0;
     if (a.budget > 0) {
@@ -456,6 +464,7 @@ __global__ void __launch_bounds__(kWarpsMax * 32) sd_kernel(SdArgs g) {
       lo = min(max((int)ceilf(u - 0.5f), 0), P - 1);
       hi = lo + 1;
       ++nodes;
+      ++task_nodes;
       flops += 2 * (n - 1 - i) + 4 * P;
 
       // periodic: radius refresh, budget, and splitting while warps are idle
@@ -484,31 +493,22 @@ __global__ void __launch_bounds__(kWarpsMax * 32) sd_kernel(SdArgs g) {
             break;
           }
         }
-        const int idle = (a.flags & MDX_SEQUENTIAL_SEARCH)
+        const int idle = ((a.flags & MDX_SEQUENTIAL_SEARCH) || task_nodes < kSplitMinNodes)
                              ? 0
                              : __shfl_sync(0xffffffffu, lane == 0 ? *(volatile int*)&g.sh->idle : 0, 0);
         if (idle > 0) {
-          // top-most level (>= 1) with untried children, counting the current one
-          int lsplit = -1;
-          for (int l = top; l >= i && l >= kMinSplitLevel; --l) {
-            int llo, lhi;
-            if (l == i) {
-              llo = lo;
-              lhi = hi;
-            } else {
-              const int lh = lv_lohi[l];
-              llo = (lh & 0xffff) - 1;
-              lhi = lh >> 16;
-            }
-            if (llo >= 0 || lhi < P) {
-              lsplit = l;
-              break;
-            }
-          }
-          if (lsplit >= kMinSplitLevel) {
+          if (lane == 0) atomicAdd(&g.sh->split_checks, 1u);
+          // donate the in-sphere children of the top-most open level (at least
+          // kMinSplitLevel rows deep, above the current node unless the warp is at
+          // the task's root): the largest subtrees this warp would reach last.
+          // Levels whose next child is outside the sphere are closed on the way
+          // (their later children are farther).
+          int given = 0;
+          const int lmin = (i == top) ? i : i + 1;  // keep the current node unless it is the task's root
+          for (int l = top; l >= lmin && l >= kMinSplitLevel && given == 0; --l) {
             int llo, lhi;
             float lc, lu, lped, lrii;
-            if (lsplit == i) {
+            if (l == i) {
               llo = lo;
               lhi = hi;
               lc = c;
@@ -516,16 +516,16 @@ __global__ void __launch_bounds__(kWarpsMax * 32) sd_kernel(SdArgs g) {
               lped = ped_par;
               lrii = rii;
             } else {
-              const int lh = lv_lohi[lsplit];
+              const int lh = lv_lohi[l];
               llo = (lh & 0xffff) - 1;
               lhi = lh >> 16;
-              lc = lv_c[lsplit];
-              lu = lv_u[lsplit];
-              lped = lv_ped[lsplit];
-              lrii = lv_rii[lsplit];
+              lc = lv_c[l];
+              lu = lv_u[l];
+              lped = lv_ped[l];
+              lrii = lv_rii[l];
             }
-            // remaining children inside the sphere, in SE order (warp-uniform):
-            // counted first, then written, so no per-child arrays are needed
+            if (llo < 0 && lhi >= P) continue;
+            // children inside the sphere, in SE order: counted first, then written
             int cnt = 0;
             {
               int a_lo = llo, a_hi = lhi;
@@ -546,51 +546,57 @@ __global__ void __launch_bounds__(kWarpsMax * 32) sd_kernel(SdArgs g) {
               if (base_slot < 0) {
                 atomicSub(&vs->pending, cnt);
                 atomicSub(&g.sh->outstanding, cnt);
+              } else {
+                atomicAdd(&g.sh->donated, (unsigned)cnt);
               }
             }
             base_slot = __shfl_sync(0xffffffffu, base_slot, 0);
-            if (base_slot >= 0) {
-              for (int q = 0; q < cnt; ++q) {
-                int kk;
-                if (lhi >= P || (llo >= 0 && fabsf(lu - (float)llo) <= fabsf((float)lhi - lu))) kk = llo--;
-                else kk = lhi++;
-                const float d = fmaf(-lrii, (float)(2 * kk - (P - 1)) * alpha, lc);
-                const float pd = fmaf(d, d, lped);
-                const unsigned long long sl = (unsigned long long)base_slot + q;
-                SdTask* t = g.queue + ((unsigned)sl & (g.qcap - 1));
-                int wok = 1;
-                if (lane == 0) {
-                  wok = slot_writable(g, t, sl);
-                  if (!wok) {
-                    // error recorded; the task is dropped (this task still holds the
-                    // vector open, so its pending count cannot reach zero here)
-                    atomicExch(&g.sh->error, 3);
-                    atomicSub(&vs->pending, 1);
-                    atomicSub(&g.sh->outstanding, 1);
-                  }
+            if (cnt > 0 && base_slot < 0) break;  // queue full: keep the rest
+            for (int q = 0; q < cnt; ++q) {
+              int kk;
+              if (lhi >= P || (llo >= 0 && fabsf(lu - (float)llo) <= fabsf((float)lhi - lu))) kk = llo--;
+              else kk = lhi++;
+              const float d = fmaf(-lrii, (float)(2 * kk - (P - 1)) * alpha, lc);
+              const float pd = fmaf(d, d, lped);
+              const unsigned long long sl = (unsigned long long)base_slot + q;
+              SdTask* t = g.queue + ((unsigned)sl & (g.qcap - 1));
+              int wok = 1;
+              if (lane == 0) {
+                wok = slot_writable(g, t, sl);
+                if (!wok) {
+                  // error recorded; the task is dropped (this task still holds the
+                  // vector open, so its pending count cannot reach zero here)
+                  atomicExch(&g.sh->error, 3);
+                  atomicSub(&vs->pending, 1);
+                  atomicSub(&g.sh->outstanding, 1);
                 }
-                wok = __shfl_sync(0xffffffffu, wok, 0);
-                if (!wok) continue;
-                for (int j = lsplit + 1 + lane; j < n; j += 32) t->x[j] = xs[j];
-                if (lane == 0) {
-                  t->x[lsplit] = (uint8_t)kk;
-                  t->v = v;
-                  t->level = lsplit - 1;
-                  t->ped = pd;
-                }
-                __threadfence();
-                __syncwarp();
-                if (lane == 0) atomicExch(&t->seq, (g.epoch << 32) | (sl + 1ull));
               }
-              // the donated children are gone from this warp's search
-              if (lsplit == i) {
-                lo = -1;
-                hi = P;
-              } else if (lane == 0) {
-                lv_lohi[lsplit] = 0 | (P << 16);
+              wok = __shfl_sync(0xffffffffu, wok, 0);
+              if (!wok) continue;
+              for (int j = l + 1 + lane; j < n; j += 32) t->x[j] = xs[j];
+              if (lane == 0) {
+                t->x[l] = (uint8_t)kk;
+                t->v = v;
+                t->level = l - 1;
+                t->ped = pd;
               }
+              __threadfence();
               __syncwarp();
+              if (lane == 0) atomicExch(&t->seq, (g.epoch << 32) | (sl + 1ull));
             }
+            given += cnt;
+            // the donated (or out-of-sphere) children are gone from this warp's search
+            if (l == i) {
+              lo = -1;
+              hi = P;
+            } else if (lane == 0) {
+              lv_lohi[l] = 0 | (P << 16);
+            }
+            __syncwarp();
+          }
+          if (lane == 0) {
+            if (given > 0) atomicAdd(&g.sh->splits, 1u);
+            else atomicAdd(&g.sh->no_level, 1u);
           }
         }
       }
@@ -744,6 +750,7 @@ size_t sd_vec_state_bytes(int n) { return vec_state_bytes(n); }
 size_t sd_task_bytes() { return sizeof(SdTask); }
 size_t sd_shared_bytes() { return sizeof(SdShared); }
 size_t sd_error_offset() { return offsetof(SdShared, error); }
+size_t sd_counters_offset() { return offsetof(SdShared, split_checks); }
 
 cudaError_t launch_sd(const SearchArgs& a, const SdWorkspace& w, int num_sms, cudaStream_t s) {
   if (a.batch <= 0) return cudaSuccess;

@@ -25,7 +25,9 @@ MDX_MAX_TX, MDX_MAX_RX, MDX_MAX_K = 100, 128, 256
 # Every symbol the header declares; the library must export all of them.
 EXPORTS = ["mdx_create", "mdx_destroy", "mdx_strerror", "mdx_last_error", "mdx_workspace_bytes",
            "mdx_qr", "detect_sd", "detect_kbest", "detect_hybrid", "mdx_count_errors",
-           "mdx_profile", "mdx_profile_read", "detect_kbest_noalloc"]
+           "mdx_profile", "mdx_profile_read", "detect_kbest_noalloc", "mdx_mlp_param_count",
+           "mdx_mlp_dims", "mdx_mlp_init", "mdx_mlp_set_params", "mdx_mlp_get_params", "mdx_mlp_predict",
+           "mdx_mlp_train_step", "mdx_mlp_error"]
 NOALLOC_SCRATCH_BYTES = 16 << 20
 STATS = 5  # per-vector stats: nodes, peds, restarts, rescored, algorithmic FP32 flops
 
@@ -82,6 +84,23 @@ def lib():
             L.mdx_count_errors.restype = i
             L.detect_kbest_noalloc.argtypes = [ctypes.POINTER(Params), i, vp, vp, vp, vp, vp, vp, vp, vp]
             L.detect_kbest_noalloc.restype = i
+            L.mdx_mlp_param_count.argtypes = [i, i]
+            L.mdx_mlp_param_count.restype = ctypes.c_size_t
+            L.mdx_mlp_dims.argtypes = [i, i, vp, vp]
+            L.mdx_mlp_dims.restype = i
+            L.mdx_mlp_init.argtypes = [vp, i, i, i, ctypes.c_ulonglong]
+            L.mdx_mlp_init.restype = i
+            L.mdx_mlp_set_params.argtypes = [vp, vp, ctypes.c_size_t]
+            L.mdx_mlp_set_params.restype = i
+            L.mdx_mlp_get_params.argtypes = [vp, vp, ctypes.c_size_t]
+            L.mdx_mlp_get_params.restype = i
+            L.mdx_mlp_predict.argtypes = [vp, ctypes.POINTER(Params), i, vp, vp, vp, vp, vp, vp]
+            L.mdx_mlp_predict.restype = i
+            L.mdx_mlp_train_step.argtypes = [vp, ctypes.POINTER(Params), i, vp, vp, vp, vp, vp, ctypes.c_float, i,
+                                             vp, vp, vp]
+            L.mdx_mlp_train_step.restype = i
+            L.mdx_mlp_error.argtypes = [vp, vp]
+            L.mdx_mlp_error.restype = i
             L.mdx_profile.argtypes = [vp, i]
             L.mdx_profile.restype = i
             L.mdx_profile_read.argtypes = [vp, vp]
@@ -121,9 +140,11 @@ class Context:
         of the last sphere-decoder launch is kept in self.last_sd_error."""
         import numpy as np
 
-        out = np.zeros(4)
+        out = np.zeros(8)
         self.check(lib().mdx_profile_read(self._h, ctypes.c_void_p(out.ctypes.data)), "mdx_profile_read")
         self.last_sd_error = int(out[3])
+        self.last_sd_split = {"checks": int(out[4]), "splits": int(out[5]), "donated": int(out[6]),
+                              "no_level": int(out[7])}
         return float(out[0]), float(out[1]), int(out[2])
 
     def close(self):
@@ -232,3 +253,73 @@ def count_errors(ctx: Context, sym_hat, sym_true, qam: int, stream=None):
                                 _stream(stream))
     ctx.check(st, "mdx_count_errors")
     return out
+
+
+# ----------------------------------------------------------------------------- learned radius
+
+
+def mlp_dims(n_tx: int, qam: int):
+    a, b = ctypes.c_int(), ctypes.c_int()
+    st = lib().mdx_mlp_dims(n_tx, qam, ctypes.byref(a), ctypes.byref(b))
+    if st != MDX_OK:
+        raise MdxError(st, "mdx_mlp_dims")
+    return a.value, b.value
+
+
+def mlp_param_count(n_tx: int, qam: int) -> int:
+    return int(lib().mdx_mlp_param_count(n_tx, qam))
+
+
+def mlp_init(ctx: Context, n_tx: int, qam: int, max_train_batch: int, seed: int = 0):
+    ctx.check(lib().mdx_mlp_init(ctx.handle, n_tx, qam, max_train_batch, seed), "mdx_mlp_init")
+
+
+def mlp_get_params(ctx: Context, n_tx: int, qam: int):
+    import numpy as np
+
+    out = np.zeros(mlp_param_count(n_tx, qam), dtype=np.float32)
+    ctx.check(lib().mdx_mlp_get_params(ctx.handle, ctypes.c_void_p(out.ctypes.data), out.size), "get_params")
+    return out
+
+
+def mlp_set_params(ctx: Context, params):
+    import numpy as np
+
+    p = np.ascontiguousarray(params, dtype=np.float32)
+    ctx.check(lib().mdx_mlp_set_params(ctx.handle, ctypes.c_void_p(p.ctypes.data), p.size), "set_params")
+
+
+def mlp_predict(ctx: Context, params: Params, H, y, noise_var, want_features=False, stream=None):
+    """Network outputs [B][d_out] (and features [B][d_in]) as torch tensors."""
+    import torch
+
+    B = int(H.shape[0])
+    d_in, d_out = mlp_dims(params.n_tx, params.qam)
+    out = torch.empty((B, d_out), dtype=torch.float32, device=H.device)
+    feat = torch.empty((B, d_in), dtype=torch.float32, device=H.device) if want_features else None
+    st = lib().mdx_mlp_predict(ctx.handle, ctypes.byref(params), B, _ptr(H), _ptr(y), _ptr(noise_var), _ptr(out),
+                               _ptr(feat), _stream(stream))
+    ctx.check(st, "mdx_mlp_predict")
+    return (out, feat) if want_features else out
+
+
+def mlp_train_step(ctx: Context, params: Params, H, y, noise_var, ml_sym, ml_metric, lr=1e-3, update=True,
+                   want_grad=False, stream=None):
+    """One step; returns (loss tensor [2], grad tensor or None)."""
+    import torch
+
+    B = int(H.shape[0])
+    loss = torch.zeros(2, dtype=torch.float32, device=H.device)
+    grad = (torch.empty(mlp_param_count(params.n_tx, params.qam), dtype=torch.float32, device=H.device)
+            if want_grad else None)
+    st = lib().mdx_mlp_train_step(ctx.handle, ctypes.byref(params), B, _ptr(H), _ptr(y), _ptr(noise_var),
+                                  _ptr(ml_sym), _ptr(ml_metric), float(lr), int(update), _ptr(grad), _ptr(loss),
+                                  _stream(stream))
+    ctx.check(st, "mdx_mlp_train_step")
+    return loss, grad
+
+
+def mlp_error(ctx: Context) -> int:
+    e = ctypes.c_int()
+    ctx.check(lib().mdx_mlp_error(ctx.handle, ctypes.byref(e)), "mdx_mlp_error")
+    return e.value
