@@ -74,11 +74,16 @@ struct KbLayout {
   }
 };
 
+// Ascending bitonic sort of Cs (a power of two) keys by T threads.  Thread t
+// handles the pairs t, t + T, ...; for strides up to 32 a warp's pairs lie in
+// its own 64 consecutive keys (when T >= Cs / 2), so a stage followed by such a
+// stage needs only a warp barrier; every other transition takes the CTA barrier.
 __device__ __forceinline__ void bitonic_sort(uint64_t* keys, int Cs, int tid, int T) {
+  const bool warp_local = T >= (Cs >> 1);
   for (int size = 2; size <= Cs; size <<= 1) {
     for (int stride = size >> 1; stride > 0; stride >>= 1) {
       for (int p = tid; p < (Cs >> 1); p += T) {
-        const int lo = (p / stride) * 2 * stride + (p % stride);
+        const int lo = ((p & ~(stride - 1)) << 1) | (p & (stride - 1));
         const int hi = lo + stride;
         const bool asc = (lo & size) == 0;
         const uint64_t x = keys[lo], y = keys[hi];
@@ -87,9 +92,13 @@ __device__ __forceinline__ void bitonic_sort(uint64_t* keys, int Cs, int tid, in
           keys[hi] = x;
         }
       }
-      __syncthreads();
+      // the next stage's stride: half this one, or the next size's first
+      const int next = stride > 1 ? stride >> 1 : size;
+      if (warp_local && stride <= 32 && next <= 32) __syncwarp();
+      else __syncthreads();
     }
   }
+  __syncthreads();
 }
 
 struct KbCtx {

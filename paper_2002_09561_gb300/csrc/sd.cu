@@ -197,14 +197,18 @@ __global__ void __launch_bounds__(kWarpsMax * 32) sd_kernel(SdArgs g) {
   uint8_t* xs = reinterpret_cast<uint8_t*>(lv_lohi + n);  // current path
   const float alpha = a.alpha;
   const float uoff = 0.5f * (float)(P - 1);
-  int staged = -1;  // vector whose R is in shared memory
+  int staged = -1;   // vector whose R is in shared memory
+  int restart_v = -1;  // vector whose root this warp searches again (radius doubled)
 
   for (;;) {
     // ------------------------------------------------------------- get work
     int v = -1, top = n - 1;
     float top_ped = 0.0f;
     bool fresh = false;
-    {
+    if (restart_v >= 0) {
+      v = restart_v;
+      restart_v = -1;
+    } else {
       long long slot = -1;
       if (lane == 0) slot = queue_pop(g);
       slot = __shfl_sync(0xffffffffu, slot, 0);
@@ -493,9 +497,14 @@ __global__ void __launch_bounds__(kWarpsMax * 32) sd_kernel(SdArgs g) {
             break;
           }
         }
-        const int idle = ((a.flags & MDX_SEQUENTIAL_SEARCH) || task_nodes < kSplitMinNodes)
-                             ? 0
-                             : __shfl_sync(0xffffffffu, lane == 0 ? *(volatile int*)&g.sh->idle : 0, 0);
+        // split only while more warps wait than tasks are queued for them
+        int want = 0;
+        if (!(a.flags & MDX_SEQUENTIAL_SEARCH) && task_nodes >= kSplitMinNodes && lane == 0) {
+          const int idle_w = *(volatile int*)&g.sh->idle;
+          const int queued = (int)(*(volatile unsigned int*)&g.sh->q_tail - *(volatile unsigned int*)&g.sh->q_head);
+          want = idle_w > queued ? 1 : 0;
+        }
+        const int idle = __shfl_sync(0xffffffffu, want, 0);
         if (idle > 0) {
           if (lane == 0) atomicAdd(&g.sh->split_checks, 1u);
           // donate the in-sphere children of the top-most open level (at least
@@ -620,8 +629,9 @@ __global__ void __launch_bounds__(kWarpsMax * 32) sd_kernel(SdArgs g) {
       const float r2s = __shfl_sync(0xffffffffu, lane == 0 ? vv->r2_start : 0.0f, 0);
       const int rs = __shfl_sync(0xffffffffu, lane == 0 ? vv->restarts : 0, 0);
       if (nc == 0 && !bh && r2s < INFINITY && rs < 64) {
-        // empty sphere: double the radius (r^2 <- 4 r^2) and search again
-        int requeued = 0;
+        // empty sphere: double the radius (r^2 <- 4 r^2) and search the root
+        // again; this warp takes the new root itself (outstanding stays: the
+        // new root replaces this task)
         if (lane == 0) {
           const float nr2 = 4.0f * r2s;
           vs->r2_start = nr2;
@@ -629,28 +639,10 @@ __global__ void __launch_bounds__(kWarpsMax * 32) sd_kernel(SdArgs g) {
           vs->restarts += 1;
           vs->pending = 1;
           __threadfence();
-          // re-queue the root as a task of this vector
-          long long sl = queue_reserve(g, 1);
-          SdTask* t = sl >= 0 ? g.queue + ((unsigned)sl & (g.qcap - 1)) : nullptr;
-          if (t && !slot_writable(g, t, (unsigned long long)sl)) {
-            atomicExch(&g.sh->error, 3);
-            t = nullptr;
-          }
-          if (t) {
-            t->v = v;
-            t->level = n - 1;
-            t->ped = 0.0f;
-            __threadfence();
-            atomicExch(&t->seq, (g.epoch << 32) | ((unsigned long long)sl + 1ull));
-            requeued = 1;
-          } else {
-            vs->pending = 0;
-            atomicExch(&g.sh->error, 4);
-          }
         }
-        requeued = __shfl_sync(0xffffffffu, requeued, 0);
         __syncwarp();
-        if (requeued) continue;  // outstanding stays: the re-queued root replaces this task
+        restart_v = v;
+        continue;
       }
       // FP64 re-scoring of the candidates within FP32 error of the best
       float best = INFINITY;
