@@ -2,12 +2,16 @@
 """Throughput benchmark of the batched MIMO tree-search detectors.
 
 One step = one pass of the detection path over one batch of synthetic
-received vectors resident in device memory: FP64 QR, the tree search
-(FP32 partial distances), FP64 re-scoring of the final leaves, and the
-Gray-coded bit/symbol error count of the batch.  The default workload is
-16x16 MIMO, 16-QAM, exact sphere decoding with the paper's initial radius
-r^2 = N M sigma^2, 100,000 vectors per step with the SNR points 4, 6, ..., 20
-dB interleaved (vector b at point b mod 9).
+received vectors resident in device memory: FP64 QR, (for the learned
+workloads) the network's features and tensor-core forward pass giving each
+vector's initial radius, the tree search (FP32 partial distances), FP64
+re-scoring of the final leaves, and the Gray-coded bit/symbol error count of
+the batch.  The default workload is 16x16 MIMO, 16-QAM, exact sphere
+decoding from the learned radius (the trained model in
+paper_2002_09561_gb300/models), 100,000 vectors per step with the SNR points
+4, 6, ..., 20 dB interleaved (vector b at point b mod 9); the same batch is
+also timed with the paper's radius r^2 = N M sigma^2 ("plain"), and both
+arms' decisions (hence BER) must be identical.
 
 Prints one JSON line (rank 0).  Launch: python bench.py [--gpus N] [--steps K]
 [--warmup W] [--workload NAME] [--impl mdx|reference]; for N > 1 under
@@ -33,6 +37,8 @@ sys.path.insert(0, ROOT)
 
 SWEEP_16 = [4.0, 6.0, 8.0, 10.0, 12.0, 14.0, 16.0, 18.0, 20.0]
 WORKLOADS = {
+    "16x16-16qam-sd-learned": dict(n=16, qam=16, snr=SWEEP_16, vectors=100_000, detector="sd", radius="paper",
+                                   K=0, depth=0, learned=True),
     "16x16-16qam-sd": dict(n=16, qam=16, snr=SWEEP_16, vectors=100_000, detector="sd", radius="paper",
                            K=0, depth=0),
     "16x16-16qam-kbest64": dict(n=16, qam=16, snr=SWEEP_16, vectors=100_000, detector="kbest",
@@ -54,7 +60,8 @@ def parse():
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="mdx", choices=["mdx", "reference"])
-    ap.add_argument("--workload", default="16x16-16qam-sd", choices=sorted(WORKLOADS))
+    ap.add_argument("--workload", default="16x16-16qam-sd-learned", choices=sorted(WORKLOADS))
+    ap.add_argument("--no-plain", action="store_true", help="skip the plain-radius comparison arm")
     ap.add_argument("--vectors", type=int, default=0, help="override vectors per step (per GPU)")
     ap.add_argument("--snr", type=str, default="", help="comma-separated SNR points (override)")
     ap.add_argument("--seed", type=int, default=1)
@@ -245,44 +252,67 @@ def main():
     nv = torch.from_numpy(data["noise_var"]).to(dev)
     truth = torch.from_numpy(data["sym"]).to(dev)
     ctx = mdx.Context(local, max_batch=B, max_n_rx=n, max_n_tx=n)
-    params = mdx.make_params(n, n, qam, radius=w["radius"], K=max(w["K"], 1), depth=w["depth"])
+    learned = bool(w.get("learned"))
+    model_meta = None
+    if learned:
+        from paper_2002_09561_gb300 import train
+
+        model_meta = train.load_model(ctx, n, qam)
+    flags = mdx.MDX_LEARNED_RADIUS if learned else 0
+    params = mdx.make_params(n, n, qam, radius=w["radius"], K=max(w["K"], 1), depth=w["depth"], flags=flags)
     algo = w["detector"]
     out = mdx._outputs(B, n, dev, True)
     stream = torch.cuda.current_stream(dev)
 
-    def step():
-        mdx.detect(algo, ctx, params, H, y, nv, stream=stream, out=out)
-        return mdx.count_errors(ctx, out[0], truth, qam, stream=stream)
+    def timed(prm, outs, steps, warm):
+        def step():
+            mdx.detect(algo, ctx, prm, H, y, nv, stream=stream, out=outs)
+            return mdx.count_errors(ctx, outs[0], truth, qam, stream=stream)
 
-    for _ in range(args.warmup):
-        step()
-    torch.cuda.synchronize(dev)
-    if dist is not None:
-        dist.barrier()
-    torch.cuda.synchronize(dev)
+        for _ in range(warm):
+            step()
+        torch.cuda.synchronize(dev)
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize(dev)
+        sampler = ClockSampler(local)
+        sampler.start()
+        ctx.profile(True)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        errs = None
+        for _ in range(steps):
+            errs = step()
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize(dev)
+        sampler.stop()
+        el = e0.elapsed_time(e1)
+        prof = ctx.profile_read()
+        ctx.profile(False)
+        if dist is not None:
+            t = torch.tensor([el], device=dev, dtype=torch.float64)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            el = float(t.item())
+        return el, prof, errs, sampler
 
-    sampler = ClockSampler(local)
-    sampler.start()
-    ctx.profile(True)
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    for _ in range(args.steps):
-        errs = step()
-    e1.record(stream)
-    torch.cuda.synchronize(dev)
-    if dist is not None:
-        dist.barrier()
-    torch.cuda.synchronize(dev)
-    sampler.stop()
-    ms = e0.elapsed_time(e1)
-    qr_ms, search_ms, calls = ctx.profile_read()
-    ctx.profile(False)
-    if dist is not None:
-        t = torch.tensor([ms], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms, (qr_ms, search_ms, calls), errs, sampler = timed(params, out, args.steps, args.warmup)
     value = B * world * args.steps / (ms / 1e3)
+    plain = None
+    if learned and not args.no_plain:
+        pparams = mdx.make_params(n, n, qam, radius=w["radius"], K=max(w["K"], 1), depth=w["depth"])
+        pout = mdx._outputs(B, n, dev, True)
+        pms, _, perrs, _ = timed(pparams, pout, args.steps, 1)
+        same = bool(torch.equal(pout[0], out[0]))
+        pst = pout[3].cpu().numpy()
+        plain = {"value": B * world * args.steps / (pms / 1e3), "unit": "vectors/s", "ms_per_step": pms / args.steps,
+                 "initial_radius": "r^2 = N M sigma^2", "mean_nodes": float(pst[:, 0].mean()),
+                 "identical_decisions": same,
+                 "ber": int(perrs[0]) / (B * n * 2 * int(round(math.log2(int(round(qam ** 0.5)))))),
+                 "speedup_learned": (B * world * args.steps / (ms / 1e3)) / (B * world * args.steps / (pms / 1e3))}
 
     stats = out[3].cpu().numpy()
     vst = out[2].cpu().numpy()
@@ -333,12 +363,16 @@ def main():
         cpu = cpu_baseline(w, args.seed, args.cpu_seconds, 0)
 
     if rank == 0:
+        cfg = config_of(args, w, world)
+        if learned:
+            cfg["initial_radius"] = "learned (network of the models directory), doubled on an empty sphere"
+            cfg["model"] = {k: model_meta.get(k) for k in ("traces", "snr_db", "epochs", "seed")} if model_meta else None
         line = {"metric": METRIC, "value": value, "unit": "vectors/s", "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f32 search, f64 QR and re-scoring",
                 "data": "synthetic (seeded Rayleigh channels, uniform QAM symbols, AWGN)",
-                "config": config_of(args, w, world), "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
-                "gpu_launches": 3 * args.steps, "clocks": sampler.summary(),
+                "config": cfg, "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
+                "gpu_launches": (8 if learned else 3) * args.steps, "clocks": sampler.summary(), "plain": plain,
                 "quality": {"ber": bit_err / bits, "ser": sym_err / (B * n),
                             "budget_exceeded": int((vst == 2).sum()), "radius_doublings": int((vst == 1).sum()),
                             "mean_nodes": float(stats[:, 0].mean()), "max_nodes": int(stats[:, 0].max())}}
