@@ -175,9 +175,12 @@ mdx_status run_detect(int algo, mdx_ctx* c, const mdx_params* p, int batch, cons
     if (np > 4096) return fail(c, MDX_EUNSUPPORTED, "P^depth = %lld > 4096 prefixes", np);
     keys_cap += pow2ceil(np < 2 ? 2 : (int)np);
   }
-  if (algo != ALGO_SD && kbest_layout_bytes(n, p->K, P, keys_cap) > 227 * 1024)
+  if (algo == ALGO_KBEST && kbest_layout_bytes(n, p->K, P, keys_cap) > 227 * 1024)
     return fail(c, MDX_EUNSUPPORTED, "K=%d at n=%d, P=%d needs more than 227 KB of shared memory", p->K,
                 n, P);
+  if (algo == ALGO_HYBRID && hybrid_smem_bytes(n, p->K, P, p->hybrid_depth) == (size_t)-1)
+    return fail(c, MDX_EUNSUPPORTED, "hybrid K=%d at n=%d, P=%d, depth %d does not fit in shared memory", p->K, n,
+                P, p->hybrid_depth);
   const bool host = (p->flags & MDX_HOST_BUFFERS) != 0;
   if (!H || !y || !sym || !met || !vst) return fail(c, MDX_EINVAL, "NULL input or output pointer");
   if (radius_mode == RADIUS_PAPER && !nv) return fail(c, MDX_EINVAL, "noise_var needed for the paper radius");

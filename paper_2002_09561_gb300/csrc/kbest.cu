@@ -311,127 +311,438 @@ __global__ void kbest_kernel(SearchArgs a, KbLayout L) {
   }
 }
 
-__global__ void hybrid_kernel(SearchArgs a, KbLayout L, int nprefix) {
+// ---------------------------------------------------------------------------
+// Hybrid with warp workers.  Shared memory: R and ybar (FP32), the sorted list
+// of in-sphere prefixes (u16 indices), the vector's radius r2 (FP32 bits,
+// shrunk with atomicMin by any warp) and leaf-candidate list (guarded by a
+// shared-memory lock), and one K-best workspace per warp.  During the master
+// phase the warp workspaces double as the prefix sort buffer.
+struct HyLayout {
+  int n, K, P, W, pp, ts, Cw;  // Cw: key capacity per warp
+  size_t off_R, off_yb, off_idx, off_cx, off_cp, off_misc, off_warp, warp_bytes, bytes;
+};
+
+__host__ __device__ inline size_t hy_warp_bytes(int n, int K, int P) {
+  const size_t pp = path_stride(n);
+  (void)P;
+  const size_t b = 2 * sizeof(uint16_t) * round_up(K, 8) + 2 * pp * K + 2 * sizeof(float) * round_up(K, 4);
+  return (b + 15) / 16 * 16;
+}
+
+__host__ __device__ inline void hy_layout(HyLayout& L, int n, int K, int P, int W, size_t sort_bytes) {
+  L.n = n;
+  L.K = K;
+  L.P = P;
+  L.W = W;
+  L.pp = path_stride(n);
+  L.ts = tri_stride32(n);
+  L.Cw = round_up(K, 8);
+  size_t o = 0;
+  L.off_R = o;
+  o += sizeof(float) * L.ts;
+  L.off_yb = o;
+  o += sizeof(float) * round_up(n, 4);
+  L.off_idx = o;
+  o += sizeof(uint16_t) * 4096;
+  L.off_cp = o;
+  o += sizeof(float) * kCandMax;
+  L.off_misc = o;
+  o += 128;
+  L.off_cx = o;
+  o += (size_t)L.pp * kCandMax;
+  o = (o + 15) / 16 * 16;
+  L.off_warp = o;
+  L.warp_bytes = hy_warp_bytes(n, K, P);
+  // the warp workspaces double as the master's prefix sort buffer
+  const size_t need = ((sort_bytes + W - 1) / W + 15) / 16 * 16;
+  if (L.warp_bytes < need) L.warp_bytes = need;
+  o += L.warp_bytes * W;
+  L.bytes = o;
+}
+
+// One warp's K-best run over rows top..0 from the node (prefix path in
+// *xcur[0], partial distance in (*pcur)[0]).  Selection is a tournament: the
+// children of each survivor come out of its Schnorr-Euchner zig-zag in
+// increasing distance, so the K best children of the level are the first K
+// results of merging those sorted streams.  Lane l enumerates the children of
+// survivors l, l+32, ... (SPL slots); each round a warp-wide arg-min over the
+// lanes' current heads (ties to the lower parent rank) picks the next
+// survivor and its lane advances that stream by one child.  The merge stops
+// after K picks or when the smallest head leaves the sphere.  Returns the
+// number of final survivors, sorted by partial distance in (*xcur, *pcur).
+template <int SPL>
+__device__ int warp_kbest(const float* Rc, const float* yb, int n, int P, int K, int pp, float alpha, int top,
+                          const unsigned int* r2bits, float E, uint16_t* sel, uint8_t** xcur, uint8_t** xnxt,
+                          float** pcur, float** pnxt, int lane, long long* nodes, long long* flops) {
+  const float uoff = 0.5f * (float)(P - 1);
+  int S = 1;
+  for (int i = top; i >= 0 && S > 0; --i) {
+    float r2 = 0.0f;
+    if (lane == 0) r2 = __uint_as_float(*(volatile const unsigned int*)r2bits);
+    const float bnd = prune_bound(__shfl_sync(0xffffffffu, r2, 0), E, n);
+    const float rii = Rc[col_off(i) + i];
+    const float rinv = 0.5f / (alpha * rii);
+    float c[SPL], u[SPL], head[SPL], pp0[SPL];
+    int lo[SPL], hi[SPL], kh[SPL];
+#pragma unroll
+    for (int t = 0; t < SPL; ++t) {
+      const int sv = lane + 32 * t;
+      head[t] = INFINITY;
+      kh[t] = -1;
+      lo[t] = -1;
+      hi[t] = P;
+      c[t] = 0.f;
+      u[t] = 0.f;
+      pp0[t] = 0.f;
+      if (sv < S) {
+        const uint8_t* xp = *xcur + (size_t)sv * pp;
+        // interference of row i: four independent partial sums over j > i
+        float a0 = yb[i], a1 = 0.f, a2 = 0.f, a3 = 0.f;
+        int j = n - 1;
+        for (; j - 3 > i; j -= 4) {
+          a0 = fmaf(-Rc[col_off(j) + i], (float)(2 * (int)xp[j] - (P - 1)) * alpha, a0);
+          a1 = fmaf(-Rc[col_off(j - 1) + i], (float)(2 * (int)xp[j - 1] - (P - 1)) * alpha, a1);
+          a2 = fmaf(-Rc[col_off(j - 2) + i], (float)(2 * (int)xp[j - 2] - (P - 1)) * alpha, a2);
+          a3 = fmaf(-Rc[col_off(j - 3) + i], (float)(2 * (int)xp[j - 3] - (P - 1)) * alpha, a3);
+        }
+        for (; j > i; --j) a0 = fmaf(-Rc[col_off(j) + i], (float)(2 * (int)xp[j] - (P - 1)) * alpha, a0);
+        c[t] = (a0 + a1) + (a2 + a3);
+        pp0[t] = (*pcur)[sv];
+        u[t] = fmaf(c[t], rinv, uoff);
+        lo[t] = min(max((int)ceilf(u[t] - 0.5f), 0), P - 1);
+        hi[t] = lo[t] + 1;
+      }
+    }
+    // first child of every stream
+#pragma unroll
+    for (int t = 0; t < SPL; ++t) {
+      if (lo[t] >= 0 || hi[t] < P) {
+        const int k = (hi[t] >= P || (lo[t] >= 0 && fabsf(u[t] - (float)lo[t]) <= fabsf((float)hi[t] - u[t])))
+                          ? lo[t]--
+                          : hi[t]++;
+        const float d = fmaf(-rii, (float)(2 * k - (P - 1)) * alpha, c[t]);
+        const float pd = fmaf(d, d, pp0[t]);
+        if (pd < bnd) {
+          head[t] = pd;
+          kh[t] = k;
+        }
+      }
+    }
+    int kept = 0;
+    while (kept < K) {
+      // this lane's smallest head, then the warp's (ties to the lower parent rank)
+      uint64_t best = kInfKey;
+#pragma unroll
+      for (int t = 0; t < SPL; ++t) {
+        if (kh[t] >= 0) {
+          const uint64_t key = ((uint64_t)__float_as_uint(head[t]) << 32) | (unsigned)(lane + 32 * t);
+          if (key < best) best = key;
+        }
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        const uint64_t other = __shfl_xor_sync(0xffffffffu, best, o);
+        if (other < best) best = other;
+      }
+      if (best == kInfKey) break;
+      const int sv = (int)(best & 0xffffffffu);
+      if ((sv & 31) == lane) {
+        const int t = sv >> 5;
+#pragma unroll
+        for (int tt = 0; tt < SPL; ++tt) {
+          if (tt == t) {
+            sel[2 * kept] = (uint16_t)sv;
+            sel[2 * kept + 1] = (uint16_t)kh[tt];
+            (*pnxt)[kept] = head[tt];
+            // advance this stream by one child
+            kh[tt] = -1;
+            head[tt] = INFINITY;
+            if (lo[tt] >= 0 || hi[tt] < P) {
+              const int k = (hi[tt] >= P ||
+                             (lo[tt] >= 0 && fabsf(u[tt] - (float)lo[tt]) <= fabsf((float)hi[tt] - u[tt])))
+                                ? lo[tt]--
+                                : hi[tt]++;
+              const float d = fmaf(-rii, (float)(2 * k - (P - 1)) * alpha, c[tt]);
+              const float pd = fmaf(d, d, pp0[tt]);
+              if (pd < bnd) {
+                head[tt] = pd;
+                kh[tt] = k;
+              }
+            }
+          }
+        }
+      }
+      ++kept;
+    }
+    __syncwarp();
+    for (int t = lane; t < kept; t += 32) {
+      const int par = sel[2 * t], k = sel[2 * t + 1];
+      const uint32_t* src = reinterpret_cast<const uint32_t*>(*xcur + (size_t)par * pp);
+      uint32_t* dst = reinterpret_cast<uint32_t*>(*xnxt + (size_t)t * pp);
+      for (int w = 0; w < pp / 4; ++w) dst[w] = src[w];
+      (*xnxt)[(size_t)t * pp + i] = (uint8_t)k;
+    }
+    *nodes += S;
+    *flops += (long long)S * (2 * (n - 1 - i) + 4 * P);
+    __syncwarp();
+    uint8_t* tx = *xcur;
+    *xcur = *xnxt;
+    *xnxt = tx;
+    float* tp = *pcur;
+    *pcur = *pnxt;
+    *pnxt = tp;
+    S = kept;
+  }
+  return S;
+}
+
+__device__ int warp_kbest_any(const float* Rc, const float* yb, int n, int P, int K, int pp, float alpha, int top,
+                              const unsigned int* r2bits, float E, uint16_t* sel, uint8_t** xcur, uint8_t** xnxt,
+                              float** pcur, float** pnxt, int lane, long long* nodes, long long* flops) {
+  if (K <= 32)
+    return warp_kbest<1>(Rc, yb, n, P, K, pp, alpha, top, r2bits, E, sel, xcur, xnxt, pcur, pnxt, lane, nodes, flops);
+  if (K <= 64)
+    return warp_kbest<2>(Rc, yb, n, P, K, pp, alpha, top, r2bits, E, sel, xcur, xnxt, pcur, pnxt, lane, nodes, flops);
+  if (K <= 128)
+    return warp_kbest<4>(Rc, yb, n, P, K, pp, alpha, top, r2bits, E, sel, xcur, xnxt, pcur, pnxt, lane, nodes, flops);
+  return warp_kbest<8>(Rc, yb, n, P, K, pp, alpha, top, r2bits, E, sel, xcur, xnxt, pcur, pnxt, lane, nodes, flops);
+}
+
+__global__ void hybrid_kernel(SearchArgs a, HyLayout L) {
   extern __shared__ __align__(16) unsigned char smem[];
-  const int tid = threadIdx.x, T = blockDim.x;
-  const int n = a.n, P = a.P, d = a.depth;
-  uint64_t* keys = reinterpret_cast<uint64_t*>(smem + L.off_keys);
-  int* misc = reinterpret_cast<int*>(smem + L.off_misc);
-  float* misc_f = reinterpret_cast<float*>(misc + 4);
+  const int tid = threadIdx.x, T = blockDim.x, warp = tid >> 5, lane = tid & 31;
+  const int n = a.n, P = a.P, d = a.depth, K = a.K;
   float* Rc = reinterpret_cast<float*>(smem + L.off_R);
   float* yb = reinterpret_cast<float*>(smem + L.off_yb);
-  uint8_t* cx = smem + L.off_cx;
+  uint16_t* pidx = reinterpret_cast<uint16_t*>(smem + L.off_idx);
   float* cped = reinterpret_cast<float*>(smem + L.off_cp);
-  KbCtx c{n, P, a.K, L.pp, tid, T, a.alpha, Rc, yb, keys, misc};
-  // prefix keys live in the upper part of the key buffer (the levels use the lower part)
-  uint64_t* pkeys = keys + (L.keys_cap - nprefix);
+  uint8_t* cx = smem + L.off_cx;
+  int* misc = reinterpret_cast<int*>(smem + L.off_misc);
+  // misc: [0] vector, [1] valid prefixes, [2] next prefix, [3] ncand, [4] lock,
+  //       [5] r2 bits, [6] E bits, [7] stop, [8] budget hit, [9] error
+  unsigned int* r2bits = reinterpret_cast<unsigned int*>(&misc[5]);
+  unsigned char* wbase = smem + L.off_warp + (size_t)warp * L.warp_bytes;
+  uint16_t* wsel = reinterpret_cast<uint16_t*>(wbase);
+  uint8_t* wxa = wbase + 2 * sizeof(uint16_t) * L.Cw;
+  uint8_t* wxb = wxa + (size_t)L.pp * K;
+  float* wpa = reinterpret_cast<float*>(wxb + (size_t)L.pp * K);
+  float* wpb = wpa + round_up(K, 4);
+  uint64_t* sortbuf = reinterpret_cast<uint64_t*>(smem + L.off_warp);  // master phase only
+  int np = 1;
+  for (int l = 0; l < d; ++l) np *= P;
+  const int nprefix = pow2ceil(np < 2 ? 2 : np);
 
   for (;;) {
-    if (tid == 0) misc[1] = (int)atomicAdd(a.work_counter, 1u);
+    if (tid == 0) misc[0] = (int)atomicAdd(a.work_counter, 1u);
     __syncthreads();
-    const int v = misc[1];
+    const int v = misc[0];
     __syncthreads();
     if (v >= a.batch) break;
     if (singular_vector(a, v)) continue;
-    stage_vector(a, v, L, smem, misc_f);
-    const float E = misc_f[0];
+    {
+      KbLayout dummy;
+      dummy.off_R = L.off_R;
+      dummy.off_yb = L.off_yb;
+      dummy.ts = L.ts;
+      stage_vector(a, v, dummy, smem, reinterpret_cast<float*>(&misc[10]));
+    }
+    const float E = reinterpret_cast<float*>(&misc[10])[0];
+    unsigned long long* acc_budget = reinterpret_cast<unsigned long long*>(&misc[12]);  // nodes (budgeted)
+    unsigned long long* acc_nodes = reinterpret_cast<unsigned long long*>(&misc[14]);
+    unsigned long long* acc_flops = reinterpret_cast<unsigned long long*>(&misc[16]);
+    if (tid == 0) {
+      misc[5] = (int)__float_as_uint(reinterpret_cast<float*>(&misc[10])[1]);
+      misc[3] = 0;
+      misc[4] = 0;
+      misc[8] = 0;
+      *acc_budget = 0ull;
+      *acc_nodes = 0ull;
+      *acc_flops = 0ull;
+    }
+    __syncthreads();
     long long nodes = 0, peds = 0, restarts = 0, flops = 0;
-    bool budget_hit = false;
-    int ncand = 0;  // uniform copy of the candidate count
-    if (tid == 0) misc[2] = 0;
     for (;;) {
-      // master: all depth-d prefixes inside the current sphere, best first
-      const float bnd0 = prune_bound(misc_f[1], E, n);
-      int np = 1;
-      for (int l = 0; l < d; ++l) np *= P;
+      // ---- master: every depth-d prefix inside the sphere, sorted by partial distance
+      const float bnd0 = prune_bound(__uint_as_float((unsigned)misc[5]), E, n);
       for (int q = tid; q < nprefix; q += T) {
-        if (q >= np) {
-          pkeys[q] = kInfKey;
-          continue;
+        uint64_t key = kInfKey;
+        if (q < np) {
+          int rem = q;
+          float ped = 0.0f;
+          uint8_t xs[16];
+          for (int l = 0; l < d; ++l) {
+            const int i = n - 1 - l;
+            xs[l] = (uint8_t)(rem % P);
+            rem /= P;
+            float ci = yb[i];
+            for (int m = 0; m < l; ++m)
+              ci = fmaf(-Rc[col_off(n - 1 - m) + i], (float)(2 * (int)xs[m] - (P - 1)) * a.alpha, ci);
+            const float dd = fmaf(-Rc[col_off(i) + i], (float)(2 * (int)xs[l] - (P - 1)) * a.alpha, ci);
+            ped = fmaf(dd, dd, ped);
+          }
+          if (ped < bnd0) key = ((uint64_t)__float_as_uint(ped) << 32) | (unsigned)q;
         }
-        int rem = q;
-        float ped = 0.0f;
-        uint8_t xs[16];
-        for (int l = 0; l < d; ++l) {
-          const int i = n - 1 - l;
-          xs[l] = (uint8_t)(rem % P);
-          rem /= P;
-          float ci = yb[i];
-          for (int m = 0; m < l; ++m)
-            ci = fmaf(-Rc[col_off(n - 1 - m) + i], (float)(2 * (int)xs[m] - (P - 1)) * a.alpha, ci);
-          const float dd = fmaf(-Rc[col_off(i) + i], (float)(2 * (int)xs[l] - (P - 1)) * a.alpha, ci);
-          ped = fmaf(dd, dd, ped);
-        }
-        pkeys[q] = (ped < bnd0) ? (((uint64_t)__float_as_uint(ped) << 32) | (unsigned)q) : kInfKey;
+        sortbuf[q] = key;
       }
       __syncthreads();
-      bitonic_sort(pkeys, nprefix, tid, T);
-      for (int t = 0; t < nprefix; ++t) {
-        const uint64_t key = pkeys[t];
-        const float pped = __uint_as_float((unsigned)(key >> 32));
-        if (key == kInfKey || !(pped < prune_bound(misc_f[1], E, n))) break;
-        if (a.budget > 0 && nodes >= a.budget) {
-          budget_hit = true;
+      bitonic_sort(sortbuf, nprefix, tid, T);
+      if (tid == 0) misc[1] = 0;
+      __syncthreads();
+      for (int q = tid; q < nprefix; q += T) {
+        if (sortbuf[q] != kInfKey) {
+          pidx[q] = (uint16_t)(sortbuf[q] & 0xffffu);
+          if (q + 1 == nprefix || sortbuf[q + 1] == kInfKey) misc[1] = q + 1;
+        }
+      }
+      if (tid == 0) {
+        misc[2] = 0;
+        misc[7] = 0;
+      }
+      nodes += (tid == 0) ? 1 : 0;
+      __syncthreads();
+      const int nvalid = misc[1];
+      // ---- workers: the best prefix is finished first by warp 0 alone (its leaf
+      // sets the radius, as the paper's SD master explores best-first); then
+      // every warp takes the remaining prefixes in order
+      long long wnodes = 0, wflops = 0;
+      for (int phase = 0; phase < 2; ++phase) {
+       if (phase == 1) __syncthreads();
+       if (phase == 1 || warp == 0) {
+        for (;;) {
+        int t = 0;
+        if (lane == 0) t = atomicAdd(&misc[2], 1);
+        t = __shfl_sync(0xffffffffu, t, 0);
+        if (t >= nvalid) break;
+        int stopped = 0;
+        if (lane == 0) stopped = *(volatile int*)&misc[7] | *(volatile int*)&misc[8];
+        if (__shfl_sync(0xffffffffu, stopped, 0)) break;
+        const int q = pidx[t];
+        uint8_t* xcur = wxa;
+        uint8_t* xnxt = wxb;
+        float* pcur = wpa;
+        float* pnxt = wpb;
+        // the prefix's path and partial distance (recomputed, same FMA chain as the master)
+        float pped = 0.0f;
+        {
+          int rem = q;
+          for (int l = 0; l < d; ++l) {
+            const int i = n - 1 - l;
+            const int k = rem % P;
+            rem /= P;
+            if (lane == 0) xcur[i] = (uint8_t)k;
+            float ci = yb[i];
+            int rr = q;
+            for (int m = 0; m < l; ++m) {
+              const int km = rr % P;
+              rr /= P;
+              ci = fmaf(-Rc[col_off(n - 1 - m) + i], (float)(2 * km - (P - 1)) * a.alpha, ci);
+            }
+            const float dd = fmaf(-Rc[col_off(i) + i], (float)(2 * k - (P - 1)) * a.alpha, ci);
+            pped = fmaf(dd, dd, pped);
+          }
+        }
+        float r2 = 0.0f;
+        if (lane == 0) r2 = __uint_as_float(*(volatile unsigned int*)r2bits);
+        r2 = __shfl_sync(0xffffffffu, r2, 0);
+        if (!(pped < prune_bound(r2, E, n))) {
+          // sorted best-first: every later prefix is outside the sphere too
+          if (lane == 0) atomicExch(&misc[7], 1);
           break;
         }
-        ++nodes;  // the master's node at depth d, handed over
-        flops += 2 * (d > 0 ? d - 1 : 0) + 4 * P;
-        // hand the prefix to the K-best worker (the whole CTA)
-        uint8_t* xcur = smem + L.off_xa;
-        uint8_t* xnxt = smem + L.off_xb;
-        float* pcur = reinterpret_cast<float*>(smem + L.off_pa);
-        float* pnxt = reinterpret_cast<float*>(smem + L.off_pb);
-        if (tid == 0) {
-          int rem = (int)(key & 0xffffffffu);
-          for (int l = 0; l < d; ++l) {
-            xcur[n - 1 - l] = (uint8_t)(rem % P);
-            rem /= P;
-          }
-          pcur[0] = pped;
-        }
-        __syncthreads();
-        const int S = kbest_levels(c, n - 1 - d, 1, &xcur, &xnxt, &pcur, &pnxt, &misc_f[1], E,
-                                   &nodes, &peds, &flops);
+        if (lane == 0) pcur[0] = pped;
+        __syncwarp();
+        wnodes += 1;
+        wflops += 2 * (d > 0 ? d - 1 : 0) + 4 * P;
+        const int S = warp_kbest_any(Rc, yb, n, P, K, L.pp, a.alpha, n - 1 - d, r2bits, E, wsel, &xcur, &xnxt,
+                                     &pcur, &pnxt, lane, &wnodes, &wflops);
         if (S > 0) {
-          // keep this run's leaves within FP32 error of its best in the candidate list,
-          // then shrink the radius with its best leaf
-          const float lim = prune_bound(fminf(pcur[0], misc_f[1]), E, n);
-          for (int s = 0; s < S && s < kCandMax; ++s) {
-            const float ps = pcur[s];
+          // this run's leaves within FP32 error of its best join the candidate list
+          float cur = 0.0f;
+          if (lane == 0) cur = __uint_as_float(*(volatile unsigned int*)r2bits);
+          cur = __shfl_sync(0xffffffffu, cur, 0);
+          const float lim = prune_bound(fminf(pcur[0], cur), E, n);
+          for (int sidx = 0; sidx < S && sidx < kCandMax; ++sidx) {
+            const float ps = pcur[sidx];
             if (!(ps <= lim)) break;
             int slot = -1;
-            if (ncand < kCandMax) {
-              slot = ncand++;
-            } else {
-              float worst = -1.0f;
-              for (int q = 0; q < kCandMax; ++q)
-                if (cped[q] > worst) {
-                  worst = cped[q];
-                  slot = q;
+            if (lane == 0) {
+              bool got = false;
+              for (int it = 0; it < (1 << 20); ++it) {
+                if (atomicCAS(&misc[4], 0, 1) == 0) {
+                  got = true;
+                  break;
                 }
-              if (!(ps < worst)) slot = -1;
+                __nanosleep(32);
+              }
+              if (got) {
+                const int nc = *(volatile int*)&misc[3];
+                if (nc < kCandMax) {
+                  slot = nc;
+                  misc[3] = nc + 1;
+                } else {
+                  float worst = -1.0f;
+                  int w = -1;
+                  for (int c2 = 0; c2 < kCandMax; ++c2)
+                    if (((volatile float*)cped)[c2] > worst) {
+                      worst = ((volatile float*)cped)[c2];
+                      w = c2;
+                    }
+                  if (ps < worst) slot = w;
+                }
+                if (slot < 0) {
+                  __threadfence_block();
+                  atomicExch(&misc[4], 0);
+                }
+              } else {
+                atomicExch(&misc[9], 1);
+              }
             }
+            slot = __shfl_sync(0xffffffffu, slot, 0);
             if (slot >= 0) {
-              const uint32_t* src = reinterpret_cast<const uint32_t*>(xcur + (size_t)s * L.pp);
+              const uint32_t* src = reinterpret_cast<const uint32_t*>(xcur + (size_t)sidx * L.pp);
               uint32_t* dst = reinterpret_cast<uint32_t*>(cx + (size_t)slot * L.pp);
-              for (int w = tid; w < L.pp / 4; w += T) dst[w] = src[w];
-              if (tid == 0) cped[slot] = ps;
+              for (int w2 = lane; w2 < L.pp / 4; w2 += 32) dst[w2] = src[w2];
+              __syncwarp();
+              if (lane == 0) {
+                cped[slot] = ps;
+                __threadfence_block();
+                atomicExch(&misc[4], 0);
+              }
             }
-            __syncthreads();
           }
-          if (tid == 0 && pcur[0] < misc_f[1]) misc_f[1] = pcur[0];
+          if (lane == 0) atomicMin(r2bits, __float_as_uint(pcur[0]));
         }
-        __syncthreads();
+        if (a.budget > 0) {
+          // commit this warp's nodes; the vector stops once the budget is spent
+          if (lane == 0) {
+            const unsigned long long tot = atomicAdd(acc_budget, (unsigned long long)wnodes) + wnodes;
+            if ((long long)tot >= a.budget) atomicExch(&misc[8], 1);
+          }
+          wnodes = 0;
+        }
+        __syncwarp();
+        if (phase == 0) break;  // warp 0 hands over after the best prefix
+        }
+       }
       }
-      if (ncand > 0 || budget_hit || !(misc_f[1] < INFINITY) || restarts >= 64) break;
+      if (lane == 0) {
+        atomicAdd(acc_nodes, (unsigned long long)wnodes);
+        atomicAdd(acc_flops, (unsigned long long)wflops);
+      }
       __syncthreads();
-      if (tid == 0) misc_f[1] *= 4.0f;
+      const int nc = misc[3];
+      const float r2now = __uint_as_float((unsigned)misc[5]);
+      if (nc > 0 || misc[8] || !(r2now < INFINITY) || restarts >= 64) break;
+      // empty sphere: double the radius and run master and workers again
+      if (tid == 0) misc[5] = (int)__float_as_uint(4.0f * r2now);
       ++restarts;
       __syncthreads();
     }
-    finish_vector(a, v, cx, cped, ncand, L.pp, E,
-                  budget_hit ? MDX_V_BUDGET_EXCEEDED : (restarts > 0 ? MDX_V_EMPTY_RETRIED : MDX_V_OK),
-                  nodes, peds, restarts, flops);
+    nodes += (long long)*acc_nodes + (long long)*acc_budget;
+    flops = (long long)*acc_flops;
+    peds = nodes * P;
+    const int status = misc[8] ? MDX_V_BUDGET_EXCEEDED : (restarts > 0 ? MDX_V_EMPTY_RETRIED : MDX_V_OK);
+    finish_vector(a, v, cx, cped, misc[3], L.pp, E, status, nodes, peds, restarts, flops);
     __syncthreads();
   }
 }
@@ -444,8 +755,8 @@ int kb_threads(int K, int P) {
   return T;
 }
 
-cudaError_t launch_generic(const void* fn, const SearchArgs& a, const KbLayout& L, int T, int extra,
-                           bool hybrid, int num_sms, cudaStream_t s) {
+cudaError_t launch_generic(const void* fn, const SearchArgs& a, const KbLayout& L, int T, int num_sms,
+                           cudaStream_t s) {
   cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.bytes);
   if (e != cudaSuccess) return e;
   int per_sm = 0;
@@ -454,8 +765,7 @@ cudaError_t launch_generic(const void* fn, const SearchArgs& a, const KbLayout& 
   if (per_sm < 1) return cudaErrorInvalidConfiguration;
   int grid = per_sm * num_sms;
   if (grid > a.batch) grid = a.batch;
-  if (hybrid) hybrid_kernel<<<grid, T, L.bytes, s>>>(a, L, extra);
-  else kbest_kernel<<<grid, T, L.bytes, s>>>(a, L);
+  kbest_kernel<<<grid, T, L.bytes, s>>>(a, L);
   return cudaGetLastError();
 }
 
@@ -467,20 +777,44 @@ cudaError_t launch_kbest(const SearchArgs& a, int num_sms, cudaStream_t s) {
   KbLayout L;
   L.init(a.n, a.K, a.P, C < 2 ? 2 : C);
   if (L.bytes > 227 * 1024) return cudaErrorInvalidConfiguration;
-  return launch_generic((const void*)kbest_kernel, a, L, kb_threads(a.K, a.P), 0, false, num_sms, s);
+  return launch_generic((const void*)kbest_kernel, a, L, kb_threads(a.K, a.P), num_sms, s);
 }
 
 cudaError_t launch_hybrid(const SearchArgs& a, int num_sms, cudaStream_t s) {
   if (a.batch <= 0) return cudaSuccess;
   int np = 1;
   for (int l = 0; l < a.depth; ++l) np *= a.P;
-  const int nprefix = pow2ceil(np < 2 ? 2 : np);
-  const int C = pow2ceil(a.K * a.P);
-  KbLayout L;
-  L.init(a.n, a.K, a.P, (C < 2 ? 2 : C) + nprefix);
-  if (L.bytes > 227 * 1024) return cudaErrorInvalidConfiguration;
-  return launch_generic((const void*)hybrid_kernel, a, L, kb_threads(a.K, a.P), nprefix, true, num_sms,
-                        s);
+  const size_t sort_bytes = sizeof(uint64_t) * pow2ceil(np < 2 ? 2 : np);
+  HyLayout L;
+  int W = 8;
+  for (; W >= 1; --W) {
+    hy_layout(L, a.n, a.K, a.P, W, sort_bytes);
+    if (L.bytes <= 227 * 1024) break;
+  }
+  if (W < 1) return cudaErrorInvalidConfiguration;
+  const void* fn = (const void*)hybrid_kernel;
+  cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.bytes);
+  if (e != cudaSuccess) return e;
+  int per_sm = 0;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, W * 32, L.bytes);
+  if (e != cudaSuccess) return e;
+  if (per_sm < 1) return cudaErrorInvalidConfiguration;
+  int grid = per_sm * num_sms;
+  if (grid > a.batch) grid = a.batch;
+  hybrid_kernel<<<grid, W * 32, L.bytes, s>>>(a, L);
+  return cudaGetLastError();
+}
+
+size_t hybrid_smem_bytes(int n, int K, int P, int depth) {
+  int np = 1;
+  for (int l = 0; l < depth; ++l) np *= P;
+  const size_t sort_bytes = sizeof(uint64_t) * pow2ceil(np < 2 ? 2 : np);
+  HyLayout L;
+  for (int W = 8; W >= 1; --W) {
+    hy_layout(L, n, K, P, W, sort_bytes);
+    if (L.bytes <= 227 * 1024) return L.bytes;
+  }
+  return (size_t)-1;
 }
 
 }  // namespace mdx

@@ -85,6 +85,8 @@ size_t sd_vec_state_bytes(int n);
 cudaError_t launch_sd(const SearchArgs& a, const SdWorkspace& w, int num_sms, cudaStream_t s);
 cudaError_t launch_kbest(const SearchArgs& a, int num_sms, cudaStream_t s);
 cudaError_t launch_hybrid(const SearchArgs& a, int num_sms, cudaStream_t s);
+// Shared memory the hybrid needs for (n, K, P, depth), or (size_t)-1 if it does not fit.
+size_t hybrid_smem_bytes(int n, int K, int P, int depth);
 // Learned radius model (mlp.cu).
 struct MlpState;
 void mlp_dims(int n_tx, int qam, int* D0, int* DO);
