@@ -165,6 +165,50 @@ mdx_status detect_hybrid(mdx_ctx* ctx, const mdx_params* p, int batch, const dou
                          const double* y, const double* noise_var, uint8_t* sym_out,
                          double* metric_out, int32_t* vstatus, int64_t* stats, void* stream);
 
+/* ---------------------------------------------------------------------------
+ * Uneven batches: one call detects many requests that differ in antennas,
+ * modulation, detector and K.  (The paper detects one system at a time; this
+ * is the batching layer around its detectors.)  Request r reads H at
+ * H + reqs[r].h_offset (double [n_rx][n_tx][2]), y at y + reqs[r].y_offset
+ * (double [n_rx][2]) and noise_var[r], and writes sym_out + reqs[r].sym_offset
+ * (uint8 [n_tx]), metric_out[r], vstatus[r], stats[r][5].  `reqs` is a HOST
+ * array; every other pointer is device memory.  The QR runs per (n_rx, n_tx)
+ * class; the search is one persistent kernel whose warps take requests from a
+ * global counter, heaviest classes first: exact SD (Algorithm 1, one warp per
+ * request, node_budget honoured) or K-best (Sec. VI, tournament selection),
+ * with R and the search state in a per-warp shared-memory slice, or in a
+ * per-warp global-memory slot for requests too large for the slice.  The slice
+ * size and warps per CTA come from the context's tuning table
+ * (mdx_autotune_mixed) or a default.  With MDX_GRAPH in flags the launch
+ * sequence is captured into a CUDA graph on the first call and replayed by
+ * later calls with the same request table and pointers (the table must not
+ * change between such calls).
+ * Limits: n_tx <= MDX_MAX_TX, K <= MDX_MAX_K, nreq <= the context's max_batch
+ * and the sum of per-request QR outputs within the workspace. */
+enum { MDX_ALGO_SD = 0, MDX_ALGO_KBEST = 1 };
+enum { MDX_GRAPH = 1 << 4 };
+typedef struct {
+  int n_rx, n_tx, qam;
+  int algo;               /* MDX_ALGO_SD or MDX_ALGO_KBEST */
+  int K;                  /* K-best survivors */
+  int pad;
+  double init_radius_sq;  /* as in mdx_params */
+  long long node_budget;  /* exact SD: cap on branched nodes, 0 = none */
+  long long h_offset;     /* in doubles */
+  long long y_offset;     /* in doubles */
+  long long sym_offset;   /* in symbols */
+} mdx_request;
+mdx_status detect_mixed(mdx_ctx* ctx, int nreq, const mdx_request* reqs, const double* H, const double* y,
+                        const double* noise_var, uint8_t* sym_out, double* metric_out, int32_t* vstatus,
+                        int64_t* stats, int flags, void* stream);
+/* Tune the persistent kernel for a request table: times detect_mixed on the
+ * given (device) inputs for each candidate (warps per CTA, shared-memory
+ * slice) and keeps the fastest in the context; results[0..2] = chosen warps,
+ * slice bytes, milliseconds.  Outputs are overwritten during tuning. */
+mdx_status mdx_autotune_mixed(mdx_ctx* ctx, int nreq, const mdx_request* reqs, const double* H, const double* y,
+                              const double* noise_var, uint8_t* sym_out, double* metric_out, int32_t* vstatus,
+                              double* results, void* stream);
+
 /* Bit and symbol errors of detected against transmitted indices (the error
  * rates plotted in Sec. VII), with a Gray code per PAM dimension of
  * q = k_re*P + k_im.  counts_out int64[2] = {bit errors, symbol errors},

@@ -223,3 +223,38 @@ def count_errors(sym_hat, sym_true, qam):
     out = np.zeros(2, dtype=np.int64)
     lib().orc_count_errors(a.shape[0], a.shape[1], int(qam), _p(a), _p(b), _p(out))
     return int(out[0]), int(out[1])
+
+
+def detect_mixed(reqs, H, y, noise_var, want_gap=True, nthreads=0):
+    """An uneven batch (request table with the fields of mdx_request: n_rx,
+    n_tx, qam, algo (0 = exact SD, 1 = K-best), K, init_radius_sq (negative =
+    the paper's N M sigma^2), node_budget and the offsets of each request's H,
+    y and symbols in the flat arrays) detected request by request with
+    detect_batch, grouping requests of equal parameters.  Returns flat symbols
+    and per-request metric, status and gap."""
+    H, y, nv = _f64(H).ravel(), _f64(y).ravel(), _f64(noise_var).ravel()
+    nreq = len(reqs)
+    nsym = int(max((int(r["sym_offset"]) + int(r["n_tx"]) for r in reqs), default=0))
+    sym = np.zeros(nsym, dtype=np.uint8)
+    met, gap = np.zeros(nreq), np.ones(nreq)
+    status = np.zeros(nreq, dtype=np.int32)
+    groups = {}
+    for i, r in enumerate(reqs):
+        key = (int(r["n_rx"]), int(r["n_tx"]), int(r["qam"]), int(r["algo"]),
+               int(r["K"]) if int(r["algo"]) == 1 else 0, float(r["init_radius_sq"]),
+               int(r["node_budget"]) if int(r["algo"]) == 0 else 0)
+        groups.setdefault(key, []).append(i)
+    for (N, M, qam, algo, K, r0, budget), idx in groups.items():
+        Hb = np.stack([H[int(reqs[i]["h_offset"]):int(reqs[i]["h_offset"]) + 2 * N * M] for i in idx])
+        yb = np.stack([y[int(reqs[i]["y_offset"]):int(reqs[i]["y_offset"]) + 2 * N] for i in idx])
+        radius = "paper" if r0 < 0 else r0
+        out = detect_batch("sd" if algo == 0 else "kbest", Hb.reshape(len(idx), N, M, 2), yb.reshape(len(idx), N, 2),
+                           nv[idx], qam, radius=radius, K=max(K, 1), budget=budget,
+                           want_gap=want_gap and algo == 0, nthreads=nthreads)
+        for j, i in enumerate(idx):
+            s0 = int(reqs[i]["sym_offset"])
+            sym[s0:s0 + M] = out["sym"][j]
+        met[idx] = out["metric"]
+        status[idx] = out["status"]
+        gap[idx] = out["gap"]
+    return {"sym": sym, "metric": met, "status": status, "gap": gap}

@@ -6,6 +6,10 @@
 #include <stdio.h>
 #include <string.h>
 
+#include <algorithm>
+#include <utility>
+#include <vector>
+
 #include "mdx_internal.cuh"
 
 struct mdx_ctx {
@@ -37,6 +41,26 @@ struct mdx_ctx {
   double* smet = nullptr;
   int32_t* svst = nullptr;
   int64_t* sstats = nullptr;
+  // uneven batches (detect_mixed): the uploaded request table and its device
+  // descriptors [MixedReq x n | order x n | QR ids x n], the QR class runs
+  // (n_rx, n_tx, first id, count), per-warp global state slots, the tuning
+  // (warps per CTA, shared-memory slice per warp, placement per request
+  // class) and the captured graph with the arguments it was captured for
+  std::vector<mdx_request> mx_table;
+  unsigned long long mx_gen = 0;  // bumped whenever descriptors or tuning change
+  unsigned char* mx_dev = nullptr;
+  size_t mx_dev_bytes = 0;
+  unsigned char* mx_pinned = nullptr;
+  size_t mx_pinned_bytes = 0;
+  std::vector<int> mx_qr;  // 4 ints per class run
+  int mx_maxK = 0;
+  size_t mx_gslot = 16;
+  unsigned char* mx_scratch = nullptr;
+  size_t mx_scratch_bytes = 0;
+  int mx_W = 8, mx_slice = 12288;
+  std::vector<std::pair<unsigned long long, int>> mx_modes;  // class key -> MIX_* bits
+  cudaGraphExec_t mx_graph = nullptr;
+  std::vector<const void*> mx_graph_key;
   // optional kernel timing (mdx_profile)
   static constexpr int kProfSlots = 1024;
   bool prof = false;
@@ -118,6 +142,10 @@ void free_all(mdx_ctx* c) {
                   c->sstats, c->sd_shared, c->sd_queue, c->sd_vstate};
   for (void* p : ptrs)
     if (p) cudaFree(p);
+  if (c->mx_graph) cudaGraphExecDestroy(c->mx_graph);
+  if (c->mx_dev) cudaFree(c->mx_dev);
+  if (c->mx_scratch) cudaFree(c->mx_scratch);
+  if (c->mx_pinned) cudaFreeHost(c->mx_pinned);
 }
 
 enum Algo { ALGO_SD = 0, ALGO_KBEST = 1, ALGO_HYBRID = 2 };
@@ -292,6 +320,439 @@ mdx_status run_detect(int algo, mdx_ctx* c, const mdx_params* p, int batch, cons
   return MDX_OK;
 }
 
+// ---------------------------------------------------------------------------
+// Uneven batches.
+
+unsigned long long class_key(const mdx_request& q) {
+  return (unsigned long long)q.n_rx | ((unsigned long long)q.n_tx << 8) | ((unsigned long long)q.qam << 16) |
+         ((unsigned long long)q.algo << 24) | ((unsigned long long)(q.algo == MDX_ALGO_KBEST ? q.K : 0) << 32);
+}
+
+bool mode_fits(int mode, int algo, int n, int K, int slice) {
+  size_t need = 0;
+  if (mode & MIX_STAGE_R) need += mixed_stage_bytes(n);
+  if (mode & MIX_STATE_SMEM) need += mixed_state_bytes(algo, n, K);
+  return need <= (size_t)slice;
+}
+
+// Most shared-memory use that fits: everything, else the state, else R.
+int greedy_mode(int algo, int n, int K, int slice) {
+  const int order[3] = {MIX_STAGE_R | MIX_STATE_SMEM, MIX_STATE_SMEM, MIX_STAGE_R};
+  for (int m : order)
+    if (mode_fits(m, algo, n, K, slice)) return m;
+  return 0;
+}
+
+int mode_for(const mdx_ctx* c, const mdx_request& q) {
+  const int n = 2 * q.n_tx;
+  const unsigned long long k = class_key(q);
+  for (const auto& e : c->mx_modes)
+    if (e.first == k && mode_fits(e.second, q.algo, n, q.K, c->mx_slice)) return e.second;
+  return greedy_mode(q.algo, n, q.K, c->mx_slice);
+}
+
+mdx_status check_request(mdx_ctx* c, int r, const mdx_request& q) {
+  if (q.n_tx < 1 || q.n_rx < q.n_tx)
+    return fail(c, MDX_EINVAL, "request %d: need n_rx >= n_tx >= 1 (got %d, %d)", r, q.n_rx, q.n_tx);
+  if (q.n_tx > c->max_tx || q.n_rx > c->max_rx)
+    return fail(c, MDX_EUNSUPPORTED, "request %d: %dx%d exceeds the context's %dx%d", r, q.n_rx, q.n_tx, c->max_rx,
+                c->max_tx);
+  if (pam_of(q.qam) < 0) return fail(c, MDX_EINVAL, "request %d: qam %d not in {4, 16, 64}", r, q.qam);
+  if (q.algo != MDX_ALGO_SD && q.algo != MDX_ALGO_KBEST)
+    return fail(c, MDX_EINVAL, "request %d: algo %d is neither MDX_ALGO_SD nor MDX_ALGO_KBEST", r, q.algo);
+  if (q.algo == MDX_ALGO_KBEST && (q.K < 1 || q.K > MDX_MAX_K))
+    return fail(c, MDX_EINVAL, "request %d: K %d not in 1..%d", r, q.K, MDX_MAX_K);
+  if (isnan(q.init_radius_sq) || q.init_radius_sq == 0.0)
+    return fail(c, MDX_EINVAL, "request %d: init_radius_sq must be > 0, < 0 or INFINITY", r);
+  if (q.node_budget < 0) return fail(c, MDX_EINVAL, "request %d: node_budget < 0", r);
+  if (q.h_offset < 0 || q.y_offset < 0 || q.sym_offset < 0 || (q.h_offset & 1) || (q.y_offset & 1))
+    return fail(c, MDX_EINVAL, "request %d: offsets must be >= 0, h_offset and y_offset even", r);
+  return MDX_OK;
+}
+
+bool same_table(const mdx_ctx* c, int nreq, const mdx_request* reqs) {
+  return (int)c->mx_table.size() == nreq && nreq > 0 &&
+         memcmp(c->mx_table.data(), reqs, sizeof(mdx_request) * (size_t)nreq) == 0;
+}
+
+// Builds the device descriptors of a request table (placement from the
+// current tuning), the heaviest-first order and the QR class runs, uploads
+// them, and sizes the per-warp global state slots.  Skipped when the table
+// and the tuning are those of the last upload.
+mdx_status mixed_upload(mdx_ctx* c, int nreq, const mdx_request* reqs, cudaStream_t s) {
+  if (same_table(c, nreq, reqs)) return MDX_OK;
+  std::vector<MixedReq> d((size_t)nreq);
+  long long roff = 0, yoff = 0;
+  int maxK = 0;
+  size_t gslot = 16;
+  std::vector<std::pair<double, int>> cost((size_t)nreq);
+  for (int r = 0; r < nreq; ++r) {
+    const mdx_request& q = reqs[r];
+    MixedReq& m = d[r];
+    memset(&m, 0, sizeof(m));
+    m.n_rx = q.n_rx;
+    m.n_tx = q.n_tx;
+    m.n = 2 * q.n_tx;
+    m.P = pam_of(q.qam);
+    m.algo = q.algo;
+    m.K = q.algo == MDX_ALGO_KBEST ? q.K : 0;
+    m.mode = mode_for(c, q);
+    const double r0 = q.init_radius_sq;
+    m.radius_mode = isinf(r0) ? (r0 > 0 ? RADIUS_NONE : RADIUS_PAPER) : (r0 < 0 ? RADIUS_PAPER : RADIUS_VALUE);
+    m.radius_value = r0;
+    m.alpha64 = sqrt(3.0 / (2.0 * (q.qam - 1)));
+    m.alpha = (float)m.alpha64;
+    m.budget = q.algo == MDX_ALGO_SD ? q.node_budget : 0;
+    m.h_off = q.h_offset;
+    m.yin_off = q.y_offset;
+    m.sym_off = q.sym_offset;
+    m.r_off = roff;
+    m.y_off = yoff;
+    roff += tri_stride32(m.n);
+    yoff += vec_stride32(m.n);
+    if (m.K > maxK) maxK = m.K;
+    if (!(m.mode & MIX_STATE_SMEM)) gslot = std::max(gslot, mixed_state_bytes(m.algo, m.n, m.K));
+    // a cost proxy for the order: the exact SD's tree grows fastest with n
+    const double n = m.n;
+    cost[r].first = (m.algo == MDX_ALGO_SD) ? n * n * n * m.P : n * m.K * (n + 8.0 * m.P);
+    cost[r].second = r;
+  }
+  std::stable_sort(cost.begin(), cost.end(),
+                   [](const std::pair<double, int>& a, const std::pair<double, int>& b) { return a.first > b.first; });
+  // QR runs: requests grouped by (n_rx, n_tx)
+  std::vector<int> ids((size_t)nreq);
+  for (int r = 0; r < nreq; ++r) ids[r] = r;
+  std::stable_sort(ids.begin(), ids.end(), [&](int a, int b) {
+    return std::make_pair(reqs[a].n_rx, reqs[a].n_tx) < std::make_pair(reqs[b].n_rx, reqs[b].n_tx);
+  });
+  std::vector<int> runs;
+  for (int t = 0; t < nreq; ++t) {
+    const mdx_request& q = reqs[ids[t]];
+    if (runs.empty() || runs[runs.size() - 4] != q.n_rx || runs[runs.size() - 3] != q.n_tx) {
+      runs.push_back(q.n_rx);
+      runs.push_back(q.n_tx);
+      runs.push_back(t);
+      runs.push_back(0);
+    }
+    runs.back() += 1;
+  }
+  const size_t bytes = sizeof(MixedReq) * (size_t)nreq + 2 * sizeof(int) * (size_t)nreq;
+  cudaError_t e = cudaSuccess;
+  if (c->mx_pinned_bytes < bytes) {
+    if (c->mx_pinned) cudaFreeHost(c->mx_pinned);
+    c->mx_pinned = nullptr;
+    c->mx_pinned_bytes = 0;
+    e = cudaMallocHost(reinterpret_cast<void**>(&c->mx_pinned), bytes);
+    if (e != cudaSuccess) return cuda_fail(c, e, "pinned descriptor buffer");
+    c->mx_pinned_bytes = bytes;
+  }
+  if (c->mx_dev_bytes < bytes) {
+    if (c->mx_graph) {
+      cudaGraphExecDestroy(c->mx_graph);
+      c->mx_graph = nullptr;
+    }
+    if (c->mx_dev) cudaFree(c->mx_dev);
+    c->mx_dev = nullptr;
+    c->mx_dev_bytes = 0;
+    e = cudaMalloc(reinterpret_cast<void**>(&c->mx_dev), bytes);
+    if (e != cudaSuccess) return cuda_fail(c, e, "descriptor buffer");
+    c->mx_dev_bytes = bytes;
+  }
+  memcpy(c->mx_pinned, d.data(), sizeof(MixedReq) * (size_t)nreq);
+  int* ord = reinterpret_cast<int*>(c->mx_pinned + sizeof(MixedReq) * (size_t)nreq);
+  for (int t = 0; t < nreq; ++t) ord[t] = cost[t].second;
+  memcpy(ord + nreq, ids.data(), sizeof(int) * (size_t)nreq);
+  // the stream may still be reading the previous descriptors: upload in order on it
+  e = cudaMemcpyAsync(c->mx_dev, c->mx_pinned, bytes, cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return cuda_fail(c, e, "descriptor upload");
+  // per-warp global state slots for the requests whose state is not in shared memory
+  const int warps = mixed_resident_warps(c->mx_W, c->mx_slice, maxK, c->num_sms);
+  if (warps < 1) return fail(c, MDX_EUNSUPPORTED, "no launch of %d warps x %d bytes fits", c->mx_W, c->mx_slice);
+  const size_t sbytes = (size_t)warps * gslot;
+  if (c->mx_scratch_bytes < sbytes) {
+    if (c->mx_graph) {
+      cudaGraphExecDestroy(c->mx_graph);
+      c->mx_graph = nullptr;
+    }
+    if (c->mx_scratch) cudaFree(c->mx_scratch);
+    c->mx_scratch = nullptr;
+    c->mx_scratch_bytes = 0;
+    e = cudaMalloc(reinterpret_cast<void**>(&c->mx_scratch), sbytes);
+    if (e != cudaSuccess) return fail(c, MDX_ENOMEM, "%zu bytes of per-warp search state", sbytes);
+    c->mx_scratch_bytes = sbytes;
+  }
+  c->mx_table.assign(reqs, reqs + nreq);
+  c->mx_qr = runs;
+  c->mx_maxK = maxK;
+  c->mx_gslot = gslot;
+  ++c->mx_gen;
+  return MDX_OK;
+}
+
+// The launch sequence of one uneven batch: counter reset, QR per class, search.
+cudaError_t mixed_launches(mdx_ctx* c, int nreq, const double* dH, const double* dy, const double* dnv,
+                           uint8_t* dsym, double* dmet, int32_t* dvst, int64_t* dstats, int flags, cudaStream_t s,
+                           cudaEvent_t* ev) {
+  const MixedReq* dreqs = reinterpret_cast<const MixedReq*>(c->mx_dev);
+  const int* dorder = reinterpret_cast<const int*>(c->mx_dev + sizeof(MixedReq) * (size_t)nreq);
+  const int* dids = dorder + nreq;
+  if (ev) cudaEventRecord(ev[0], s);
+  QrOut q{c->R64, c->yb64, c->R32, c->yb32, nullptr, nullptr, c->singular};
+  for (size_t k = 0; k + 3 < c->mx_qr.size(); k += 4) {
+    const cudaError_t e = launch_qr_gather(c->mx_qr[k + 3], c->mx_qr[k], c->mx_qr[k + 1], dids + c->mx_qr[k + 2],
+                                           dreqs, dH, dy, q, s);
+    if (e != cudaSuccess) return e;
+  }
+  cudaError_t e = cudaMemsetAsync(c->counter, 0, sizeof(unsigned int), s);
+  if (e != cudaSuccess) return e;
+  if (ev) cudaEventRecord(ev[1], s);
+  MixedArgs a{};
+  a.nreq = nreq;
+  a.reqs = dreqs;
+  a.order = dorder;
+  a.R32 = c->R32;
+  a.yb32 = c->yb32;
+  a.R64 = c->R64;
+  a.yb64 = c->yb64;
+  a.singular = c->singular;
+  a.noise_var = dnv;
+  a.counter = c->counter;
+  a.gscratch = c->mx_scratch;
+  a.gslot_bytes = c->mx_gslot;
+  a.slice_bytes = c->mx_slice;
+  a.flags = flags;
+  a.sym_out = dsym;
+  a.metric_out = dmet;
+  a.vstatus = dvst;
+  a.stats = dstats;
+  e = launch_mixed(a, c->mx_W, c->mx_maxK, c->num_sms, s);
+  if (ev && e == cudaSuccess) cudaEventRecord(ev[2], s);
+  return e;
+}
+
+mdx_status run_mixed(mdx_ctx* c, int nreq, const mdx_request* reqs, const double* H, const double* y,
+                     const double* nv, uint8_t* sym, double* met, int32_t* vst, int64_t* stats, int flags,
+                     void* stream) {
+  if (!c) return MDX_EINVAL;
+  if (nreq < 0) return fail(c, MDX_EINVAL, "nreq %d < 0", nreq);
+  if (nreq == 0) return MDX_OK;
+  if (!reqs) return fail(c, MDX_EINVAL, "request table is NULL");
+  if (nreq > c->max_batch)
+    return fail(c, MDX_EUNSUPPORTED, "nreq %d > context max_batch %d", nreq, c->max_batch);
+  if (!H || !y || !sym || !met || !vst) return fail(c, MDX_EINVAL, "NULL input or output pointer");
+  const bool host = (flags & MDX_HOST_BUFFERS) != 0;
+  long long h_end = 0, y_end = 0, s_end = 0;
+  bool need_nv = false;
+  if (!same_table(c, nreq, reqs)) {
+    for (int r = 0; r < nreq; ++r) {
+      const mdx_status st = check_request(c, r, reqs[r]);
+      if (st != MDX_OK) return st;
+    }
+  }
+  for (int r = 0; r < nreq; ++r) {
+    const mdx_request& q = reqs[r];
+    h_end = std::max(h_end, q.h_offset + 2LL * q.n_rx * q.n_tx);
+    y_end = std::max(y_end, q.y_offset + 2LL * q.n_rx);
+    s_end = std::max(s_end, q.sym_offset + (long long)q.n_tx);
+    need_nv |= (q.init_radius_sq < 0.0);
+  }
+  if (need_nv && !nv) return fail(c, MDX_EINVAL, "noise_var needed for the paper radius");
+  if (host) {
+    if (h_end > 2LL * c->max_batch * c->max_rx * c->max_tx || y_end > 2LL * c->max_batch * c->max_rx ||
+        s_end > (long long)c->max_batch * c->max_tx)
+      return fail(c, MDX_EUNSUPPORTED, "host buffers larger than the context's staging");
+  } else {
+    if (!aligned16(H) || !aligned16(y)) return fail(c, MDX_EINVAL, "H and y must be 16-byte aligned");
+    const void* ptrs[] = {H, y, sym, met, vst};
+    for (const void* q : ptrs)
+      if (!is_device_ptr(q, c->device))
+        return fail(c, MDX_EINVAL, "pointer %p is not device memory of device %d", q, c->device);
+    if (nv && !is_device_ptr(nv, c->device)) return fail(c, MDX_EINVAL, "noise_var is not device memory");
+    if (stats && !is_device_ptr(stats, c->device)) return fail(c, MDX_EINVAL, "stats is not device memory");
+  }
+  DeviceGuard g(c->device);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail(c, e, "earlier asynchronous error");
+  mdx_status st = mixed_upload(c, nreq, reqs, s);
+  if (st != MDX_OK) return st;
+
+  const double* dH = H;
+  const double* dy = y;
+  const double* dnv = nv;
+  uint8_t* dsym = sym;
+  double* dmet = met;
+  int32_t* dvst = vst;
+  int64_t* dstats = stats;
+  if (host) {
+    e = cudaMemcpyAsync(c->sH, H, sizeof(double) * (size_t)h_end, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(c->sy, y, sizeof(double) * (size_t)y_end, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess && nv) e = cudaMemcpyAsync(c->snv, nv, sizeof(double) * nreq, cudaMemcpyHostToDevice, s);
+    if (e != cudaSuccess) return cuda_fail(c, e, "host-to-device staging");
+    dH = c->sH;
+    dy = c->sy;
+    dnv = nv ? c->snv : nullptr;
+    dsym = c->ssym;
+    dmet = c->smet;
+    dvst = c->svst;
+    dstats = stats ? c->sstats : nullptr;
+  }
+  if (flags & MDX_GRAPH) {
+    const std::vector<const void*> key = {reinterpret_cast<const void*>(c->mx_gen), dH, dy, dnv, dsym, dmet, dvst,
+                                          dstats, reinterpret_cast<const void*>((uintptr_t)(flags & ~MDX_HOST_BUFFERS))};
+    if (!c->mx_graph || c->mx_graph_key != key) {
+      if (c->mx_graph) cudaGraphExecDestroy(c->mx_graph);
+      c->mx_graph = nullptr;
+      cudaGraph_t graph = nullptr;
+      e = cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal);
+      if (e != cudaSuccess) return cuda_fail(c, e, "graph capture (use a non-default stream)");
+      const cudaError_t le = mixed_launches(c, nreq, dH, dy, dnv, dsym, dmet, dvst, dstats, flags, s, nullptr);
+      e = cudaStreamEndCapture(s, &graph);
+      if (le != cudaSuccess) {
+        if (graph) cudaGraphDestroy(graph);
+        cudaGetLastError();
+        if (le == cudaErrorInvalidConfiguration)
+          return fail(c, MDX_EUNSUPPORTED, "no launch configuration fits this size");
+        return cuda_fail(c, le, "captured launches");
+      }
+      if (e != cudaSuccess) return cuda_fail(c, e, "graph capture");
+      e = cudaGraphInstantiate(&c->mx_graph, graph, 0);
+      cudaGraphDestroy(graph);
+      if (e != cudaSuccess) {
+        c->mx_graph = nullptr;
+        return cuda_fail(c, e, "graph instantiation");
+      }
+      c->mx_graph_key = key;
+    }
+    e = cudaGraphLaunch(c->mx_graph, s);
+    if (e != cudaSuccess) return cuda_fail(c, e, "graph launch");
+  } else {
+    cudaEvent_t* ev = nullptr;
+    if (c->prof && c->prof_n < mdx_ctx::kProfSlots) ev = c->prof_ev[c->prof_n++];
+    e = mixed_launches(c, nreq, dH, dy, dnv, dsym, dmet, dvst, dstats, flags, s, ev);
+    if (e == cudaErrorInvalidConfiguration) return fail(c, MDX_EUNSUPPORTED, "no launch configuration fits this size");
+    if (e != cudaSuccess) return cuda_fail(c, e, "uneven-batch launches");
+  }
+  if (host) {
+    e = cudaMemcpyAsync(sym, c->ssym, (size_t)s_end, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(met, c->smet, sizeof(double) * nreq, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(vst, c->svst, sizeof(int32_t) * nreq, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess && stats)
+      e = cudaMemcpyAsync(stats, c->sstats, sizeof(int64_t) * kStats * (size_t)nreq, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_fail(c, e, "device-to-host results");
+  }
+  return MDX_OK;
+}
+
+// Milliseconds of one detect_mixed call (after one untimed call).
+mdx_status time_mixed(mdx_ctx* c, int nreq, const mdx_request* reqs, const double* H, const double* y,
+                      const double* nv, uint8_t* sym, double* met, int32_t* vst, cudaStream_t s, float* ms) {
+  cudaEvent_t e0, e1;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)
+    return fail(c, MDX_ECUDA, "event creation");
+  mdx_status st = run_mixed(c, nreq, reqs, H, y, nv, sym, met, vst, nullptr, 0, s);
+  if (st == MDX_OK) {
+    cudaEventRecord(e0, s);
+    st = run_mixed(c, nreq, reqs, H, y, nv, sym, met, vst, nullptr, 0, s);
+    cudaEventRecord(e1, s);
+  }
+  if (st == MDX_OK) {
+    const cudaError_t e = cudaEventSynchronize(e1);
+    if (e != cudaSuccess) st = cuda_fail(c, e, "tuning run");
+    else cudaEventElapsedTime(ms, e0, e1);
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  return st;
+}
+
+void set_tuning(mdx_ctx* c, int W, int slice, const std::vector<std::pair<unsigned long long, int>>& modes) {
+  c->mx_W = W;
+  c->mx_slice = slice;
+  c->mx_modes = modes;
+  c->mx_table.clear();  // descriptors are rebuilt with the new placement
+}
+
+mdx_status run_autotune(mdx_ctx* c, int nreq, const mdx_request* reqs, const double* H, const double* y,
+                        const double* nv, uint8_t* sym, double* met, int32_t* vst, double* results, void* stream) {
+  if (!c) return MDX_EINVAL;
+  if (nreq < 1 || !reqs) return fail(c, MDX_EINVAL, "autotuning needs a non-empty request table");
+  for (int r = 0; r < nreq; ++r) {
+    const mdx_status st = check_request(c, r, reqs[r]);
+    if (st != MDX_OK) return st;
+  }
+  DeviceGuard g(c->device);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  // 1. warps per CTA and slice size, every class on its greedy placement
+  struct Shape {
+    int W, S;
+  };
+  const Shape shapes[] = {{4, 0},     {4, 16384},  {4, 49152}, {8, 0},    {8, 6144},  {8, 12288},
+                          {8, 24576}, {16, 0},     {16, 3072}, {16, 6144}, {16, 12288}};
+  int bestW = c->mx_W, bestS = c->mx_slice;
+  float best = INFINITY;
+  for (const Shape& sh : shapes) {
+    set_tuning(c, sh.W, sh.S, {});
+    if (mixed_resident_warps(sh.W, sh.S, MDX_MAX_K, c->num_sms) < 1) continue;
+    float ms = INFINITY;
+    const mdx_status st = time_mixed(c, nreq, reqs, H, y, nv, sym, met, vst, s, &ms);
+    if (st != MDX_OK) return st;
+    if (ms < best) {
+      best = ms;
+      bestW = sh.W;
+      bestS = sh.S;
+    }
+  }
+  // 2. placement per request class, each class timed alone
+  std::vector<unsigned long long> keys;
+  for (int r = 0; r < nreq; ++r)
+    if (std::find(keys.begin(), keys.end(), class_key(reqs[r])) == keys.end()) keys.push_back(class_key(reqs[r]));
+  std::vector<std::pair<unsigned long long, int>> modes;
+  for (unsigned long long k : keys) {
+    std::vector<mdx_request> sub;
+    for (int r = 0; r < nreq; ++r)
+      if (class_key(reqs[r]) == k) sub.push_back(reqs[r]);
+    const mdx_request& q0 = sub[0];
+    const int n = 2 * q0.n_tx;
+    const int greedy = greedy_mode(q0.algo, n, q0.K, bestS);
+    int win = greedy;
+    float win_ms = INFINITY;
+    for (int m : {greedy, 0, (int)MIX_STAGE_R, (int)MIX_STATE_SMEM, (int)(MIX_STAGE_R | MIX_STATE_SMEM)}) {
+      if (!mode_fits(m, q0.algo, n, q0.K, bestS) || (m == greedy && win_ms < INFINITY)) continue;
+      std::vector<std::pair<unsigned long long, int>> trial = modes;
+      trial.push_back({k, m});
+      set_tuning(c, bestW, bestS, trial);
+      float ms = INFINITY;
+      const mdx_status st = time_mixed(c, (int)sub.size(), sub.data(), H, y, nv, sym, met, vst, s, &ms);
+      if (st != MDX_OK) return st;
+      // keep the greedy placement unless another is clearly faster
+      if (m == greedy) win_ms = ms;
+      else if (ms < 0.97f * win_ms) {
+        win = m;
+        win_ms = ms;
+      }
+    }
+    modes.push_back({k, win});
+  }
+  // 3. the whole table with the chosen placements; keep them only if not slower
+  set_tuning(c, bestW, bestS, modes);
+  float ms = INFINITY;
+  mdx_status st = time_mixed(c, nreq, reqs, H, y, nv, sym, met, vst, s, &ms);
+  if (st != MDX_OK) return st;
+  if (!(ms <= best)) {
+    set_tuning(c, bestW, bestS, {});
+    ms = best;
+  }
+  if (results) {
+    results[0] = bestW;
+    results[1] = bestS;
+    results[2] = ms;
+  }
+  return MDX_OK;
+}
+
 // Gray-coded bit errors and symbol errors, one thread per symbol.
 __global__ void count_errors_kernel(long long total, int P, const uint8_t* __restrict__ a,
                                     const uint8_t* __restrict__ b, unsigned long long* counts) {
@@ -369,8 +830,10 @@ mdx_status mdx_create(mdx_ctx** out, int device, int max_batch, int max_n_rx, in
   auto chk = [&](cudaError_t r) {
     if (e == cudaSuccess) e = r;
   };
-  chk(alloc(c, &c->R64, B * tri_stride64(n)));
-  chk(alloc(c, &c->yb64, B * vec_stride64(n)));
+  // FP64 buffers sized with the FP32 strides (multiples of 4 elements), so that
+  // an uneven batch of up to max_batch requests also fits
+  chk(alloc(c, &c->R64, B * tri_stride32(n)));
+  chk(alloc(c, &c->yb64, B * vec_stride32(n)));
   chk(alloc(c, &c->R32, B * tri_stride32(n)));
   chk(alloc(c, &c->yb32, B * vec_stride32(n)));
   chk(alloc(c, &c->singular, B));
@@ -453,6 +916,18 @@ mdx_status detect_hybrid(mdx_ctx* ctx, const mdx_params* p, int batch, const dou
                          double* metric_out, int32_t* vstatus, int64_t* stats, void* stream) {
   return run_detect(ALGO_HYBRID, ctx, p, batch, H, y, noise_var, sym_out, metric_out, vstatus, stats,
                     stream);
+}
+
+mdx_status detect_mixed(mdx_ctx* ctx, int nreq, const mdx_request* reqs, const double* H, const double* y,
+                        const double* noise_var, uint8_t* sym_out, double* metric_out, int32_t* vstatus,
+                        int64_t* stats, int flags, void* stream) {
+  return run_mixed(ctx, nreq, reqs, H, y, noise_var, sym_out, metric_out, vstatus, stats, flags, stream);
+}
+
+mdx_status mdx_autotune_mixed(mdx_ctx* ctx, int nreq, const mdx_request* reqs, const double* H, const double* y,
+                              const double* noise_var, uint8_t* sym_out, double* metric_out, int32_t* vstatus,
+                              double* results, void* stream) {
+  return run_autotune(ctx, nreq, reqs, H, y, noise_var, sym_out, metric_out, vstatus, results, stream);
 }
 
 mdx_status mdx_count_errors(mdx_ctx* c, int batch, int n_tx, int qam, const uint8_t* sym_hat,

@@ -69,6 +69,58 @@ struct SearchArgs {
 
 cudaError_t launch_qr(int batch, int n_rx, int n_tx, const double* H, const double* y, QrOut out,
                       cudaStream_t s);
+
+// One request of an uneven batch as the device sees it (built by the host
+// from mdx_request).  R and ybar of request r live at r_off / y_off (elements)
+// in the R32/R64 and yb32/yb64 workspaces; both offsets are multiples of 4.
+struct MixedReq {
+  int n_rx, n_tx, n, P;
+  int algo, K;
+  int mode;         // MIX_* placement bits chosen by the tuner
+  int radius_mode;  // RADIUS_NONE / RADIUS_PAPER / RADIUS_VALUE
+  float alpha;
+  float pad0;
+  double alpha64;
+  double radius_value;
+  long long budget;
+  long long h_off, yin_off;  // H and y of the request (doubles)
+  long long sym_off;
+  long long r_off, y_off;
+};
+// placement of a request's data: R and ybar staged in the warp's shared-memory
+// slice, and the search state (SD stacks / K-best survivors) in the slice;
+// otherwise each is read from / kept in global memory
+enum { MIX_STAGE_R = 1, MIX_STATE_SMEM = 2 };
+
+cudaError_t launch_qr_gather(int count, int n_rx, int n_tx, const int* ids, const MixedReq* reqs,
+                             const double* H, const double* y, QrOut out, cudaStream_t s);
+
+struct MixedArgs {
+  int nreq;
+  const MixedReq* reqs;
+  const int* order;  // requests in the order warps take them
+  const float* R32;
+  const float* yb32;
+  const double* R64;
+  const double* yb64;
+  const int* singular;
+  const double* noise_var;
+  unsigned int* counter;
+  unsigned char* gscratch;  // per-warp global state slots
+  size_t gslot_bytes;
+  int slice_bytes;          // shared memory per warp
+  int flags;
+  uint8_t* sym_out;
+  double* metric_out;
+  int32_t* vstatus;
+  int64_t* stats;
+};
+// Bytes of a request's staged R + ybar and of its search state.
+size_t mixed_stage_bytes(int n);
+size_t mixed_state_bytes(int algo, int n, int K);
+// Warps a launch with this shape keeps resident (for sizing gscratch).
+int mixed_resident_warps(int warps_per_cta, int slice_bytes, int max_K, int num_sms);
+cudaError_t launch_mixed(const MixedArgs& a, int warps_per_cta, int max_K, int num_sms, cudaStream_t s);
 // Global workspace of the sphere decoder's task queue (see sd.cu).
 struct SdWorkspace {
   void* shared;          // sd_shared_bytes()

@@ -1,0 +1,409 @@
+// Uneven batches: one persistent search kernel over requests that differ in
+// antennas, modulation, detector and K (the batching layer around the
+// paper's detectors; the paper runs one system at a time).
+//
+// Every warp of the grid takes requests from a global counter, in the order
+// the host chose (heaviest classes first), and searches each one alone:
+//   exact SD   Algorithm 1 with Schnorr-Euchner child order (Sec. IV-A) and
+//              incremental partial distances (Eq. inc), one warp walking the
+//              whole tree: lanes own rows, the residual of every row below the
+//              current level sits in a stack zs[level][row], so a descent
+//              costs one FMA per lower row and the next interference is the
+//              owner lane's value broadcast by a shuffle (the same node step as
+//              the split-task decoder, without the task queue);
+//   K-best     Sec. VI, selection of the K best children per level by a
+//              warp tournament over the survivors' Schnorr-Euchner child
+//              streams (warp_kbest.cuh).
+// Each warp owns a slice of the CTA's shared memory and a slot of global
+// memory.  Per request class the tuner decides whether R and ybar are copied
+// into the slice (MIX_STAGE_R) and whether the search state (SD stacks and
+// leaf candidates, or K-best survivor paths) lives in the slice
+// (MIX_STATE_SMEM) or in the global slot; the kernel uses generic pointers,
+// so one code path serves every placement.  Leaves within the FP32 error
+// bound of the best are re-scored in FP64 against the FP64 R and ybar.
+#include "mdx_internal.cuh"
+#include "warp_kbest.cuh"
+
+namespace mdx {
+namespace {
+
+constexpr int kMixCand = 8;  // SD leaf candidates kept per request
+
+__host__ __device__ inline size_t stage_bytes(int n) {
+  return sizeof(float) * ((size_t)tri_stride32(n) + round_up(n, 4));
+}
+
+__host__ __device__ inline int mix_path_pad(int n) { return round_up(n, 16); }
+
+__host__ __device__ inline size_t sd_state_bytes(int n) {
+  const size_t n4 = (size_t)round_up(n, 4);
+  const size_t b = sizeof(float) * (round_up(tri(n), 4) + 5 * n4) + sizeof(int) * n4 + sizeof(float) * kMixCand +
+                   (size_t)mix_path_pad(n) * (1 + kMixCand);
+  return (b + 15) / 16 * 16;
+}
+
+__host__ __device__ inline size_t kb_state_bytes(int n, int K) {
+  const size_t b = 16 + 2 * sizeof(float) * round_up(K, 4) + 2 * sizeof(uint16_t) * round_up(K, 8) +
+                   2 * (size_t)path_stride(n) * K;
+  return (b + 15) / 16 * 16;
+}
+
+__device__ float initial_r2(const MixedArgs& g, const MixedReq& q, int r) {
+  float r2;
+  if (q.radius_mode == RADIUS_NONE) r2 = INFINITY;
+  else if (q.radius_mode == RADIUS_PAPER) r2 = (float)((double)q.n_rx * q.n_tx * g.noise_var[r]);
+  else r2 = (float)q.radius_value;
+  return (r2 > 0.0f) ? r2 : INFINITY;
+}
+
+// Picks, among nc candidate paths (stride cs bytes) with FP32 distances cped,
+// the one of least FP64 metric (ties: smaller index vector, top row first)
+// among those within the FP32 error bound of the best; writes the request's
+// outputs.  All lanes call it.
+__device__ void finish_request(const MixedArgs& g, const MixedReq& q, int r, const uint8_t* cx, int cs,
+                               const float* cped, int nc, float E, int status, long long nodes, long long peds,
+                               long long restarts, long long flops, int lane) {
+  const int n = q.n, P = q.P;
+  float best = INFINITY;
+  for (int k = 0; k < nc; ++k) best = fminf(best, cped[k]);
+  const float keep = prune_bound(best, E, n);
+  const double* R64 = g.R64 + q.r_off;
+  const double* y64 = g.yb64 + q.y_off;
+  int win = -1;
+  double win_m = INFINITY;
+  long long rescored = 0;
+  for (int k = 0; k < nc; ++k) {
+    if (!(cped[k] <= keep)) continue;
+    double m;
+    if (g.flags & MDX_NO_RESCORE) {
+      m = (double)cped[k];
+    } else {
+      m = rescore_fp64_warp(n, P, q.alpha64, R64, y64, cx + (size_t)k * cs, lane);
+      ++rescored;
+    }
+    bool better = m < win_m;
+    if (!better && m == win_m && win >= 0) {
+      for (int j = n - 1; j >= 0; --j) {
+        const int x1 = cx[(size_t)k * cs + j], x2 = cx[(size_t)win * cs + j];
+        if (x1 != x2) {
+          better = x1 < x2;
+          break;
+        }
+      }
+    }
+    if (better) {
+      win = k;
+      win_m = m;
+    }
+  }
+  uint8_t* so = g.sym_out + q.sym_off;
+  for (int j = lane; j < q.n_tx; j += 32)
+    so[j] = (win >= 0) ? (uint8_t)(cx[(size_t)win * cs + 2 * j] * P + cx[(size_t)win * cs + 2 * j + 1]) : 0;
+  if (lane == 0) {
+    g.metric_out[r] = (win >= 0) ? win_m : (double)INFINITY;
+    g.vstatus[r] = status;
+    if (g.stats) {
+      int64_t* s = g.stats + (size_t)r * kStats;
+      s[0] = nodes;
+      s[1] = peds;
+      s[2] = restarts;
+      s[3] = rescored;
+      s[4] = flops;
+    }
+  }
+}
+
+// Exact SD of one request by one warp (ROWS = rows per lane, n <= 32 ROWS).
+template <int ROWS>
+__device__ void sd_request(const MixedArgs& g, const MixedReq& q, int r, const float* Rc, const float* yb,
+                           unsigned char* st, float E, int lane) {
+  const int n = q.n, P = q.P, n4 = round_up(n, 4);
+  const float alpha = q.alpha, uoff = 0.5f * (float)(P - 1);
+  float* zs = reinterpret_cast<float*>(st);
+  float* lv_ped = zs + round_up(tri(n), 4);
+  float* lv_c = lv_ped + n4;
+  float* lv_u = lv_c + n4;
+  float* lv_rii = lv_u + n4;
+  float* lv_rinv = lv_rii + n4;
+  int* lv_lohi = reinterpret_cast<int*>(lv_rinv + n4);
+  float* cped = reinterpret_cast<float*>(lv_lohi + n4);
+  uint8_t* xs = reinterpret_cast<uint8_t*>(cped + kMixCand);
+  uint8_t* cx = xs + mix_path_pad(n);
+  const int cs = mix_path_pad(n);
+
+  for (int rr = lane; rr < n; rr += 32) {
+    const float d = Rc[col_off(rr) + rr];
+    lv_rii[rr] = d;
+    lv_rinv[rr] = 0.5f / (alpha * d);
+  }
+  float r2_start = initial_r2(g, q, r);
+  float r2 = r2_start;
+  long long nodes = 0, peds = 0, flops = 0;
+  int restarts = 0, ncand = 0;
+  bool bh = false;
+  for (;;) {
+    // the root: z_r = ybar_r for every row
+#pragma unroll
+    for (int t = 0; t < ROWS; ++t) {
+      const int rr = lane + 32 * t;
+      if (rr < n) zs[col_off(n - 1) + rr] = yb[rr];
+    }
+    __syncwarp();
+    float bnd = prune_bound(r2, E, n);
+    int i = n - 1;
+    float ped_par = 0.0f;
+    float c = zs[col_off(i) + i];
+    float rii = lv_rii[i];
+    float u = fmaf(c, lv_rinv[i], uoff);
+    int lo = min(max((int)ceilf(u - 0.5f), 0), P - 1);
+    int hi = lo + 1;
+    ++nodes;
+    flops += 4 * P;
+    for (;;) {
+      int k = -1;
+      if (lo >= 0 || hi < P) {
+        if (hi >= P || (lo >= 0 && fabsf(u - (float)lo) <= fabsf((float)hi - u))) k = lo--;
+        else k = hi++;
+      }
+      float ped = INFINITY;
+      if (k >= 0) {
+        const float d = fmaf(-rii, (float)(2 * k - (P - 1)) * alpha, c);
+        ped = fmaf(d, d, ped_par);
+        ++peds;
+      }
+      if (k < 0 || !(ped < bnd)) {
+        if (i == n - 1) break;  // the root is exhausted
+        ++i;                    // backtrack
+        ped_par = lv_ped[i];
+        c = lv_c[i];
+        u = lv_u[i];
+        rii = lv_rii[i];
+        const int lh = lv_lohi[i];
+        lo = (lh & 0xffff) - 1;
+        hi = lh >> 16;
+        continue;
+      }
+      if (i == 0) {
+        // leaf inside the sphere: keep it among the kMixCand best, shrink the radius
+        int slot = -1;
+        if (lane == 0) {
+          xs[0] = (uint8_t)k;
+          if (ncand < kMixCand) {
+            slot = ncand;
+          } else {
+            float worst = -1.0f;
+            for (int t = 0; t < kMixCand; ++t)
+              if (cped[t] > worst) {
+                worst = cped[t];
+                slot = t;
+              }
+            if (!(ped < worst)) slot = -1;
+          }
+        }
+        slot = __shfl_sync(0xffffffffu, slot, 0);
+        __syncwarp();
+        if (slot >= 0) {
+          for (int rr = lane; rr < n; rr += 32) cx[(size_t)slot * cs + rr] = xs[rr];
+          if (lane == 0) cped[slot] = ped;
+          if (slot == ncand) ++ncand;
+        }
+        __syncwarp();
+        if (ped < r2) {
+          r2 = ped;
+          bnd = prune_bound(r2, E, n);
+        }
+        continue;
+      }
+      if (q.budget > 0 && nodes >= q.budget) {
+        bh = true;
+        break;
+      }
+      // descend into child k: push level i, update the residuals of the rows below
+      const float av = (float)(2 * k - (P - 1)) * alpha;
+      if (lane == 0) {
+        lv_ped[i] = ped_par;
+        lv_c[i] = c;
+        lv_u[i] = u;
+        lv_lohi[i] = (lo + 1) | (hi << 16);
+        xs[i] = (uint8_t)k;
+      }
+      const float* zin = zs + col_off(i);
+      float* zout = zs + col_off(i - 1);
+      const float* rc = Rc + col_off(i);
+      float cnext = 0.0f;
+#pragma unroll
+      for (int t = 0; t < ROWS; ++t) {
+        const int rr = lane + 32 * t;
+        if (rr < i) {
+          const float z = fmaf(-rc[rr], av, zin[rr]);
+          zout[rr] = z;
+          if (rr == i - 1) cnext = z;
+        }
+      }
+      --i;
+      c = __shfl_sync(0xffffffffu, cnext, i & 31);
+      __syncwarp();
+      ped_par = ped;
+      rii = lv_rii[i];
+      u = fmaf(c, lv_rinv[i], uoff);
+      lo = min(max((int)ceilf(u - 0.5f), 0), P - 1);
+      hi = lo + 1;
+      ++nodes;
+      flops += 2 * (n - 1 - i) + 4 * P;
+    }
+    if (ncand == 0 && !bh && r2_start < INFINITY && restarts < 64) {
+      // empty sphere: r^2 <- 4 r^2 and search again
+      r2_start *= 4.0f;
+      r2 = r2_start;
+      ++restarts;
+      continue;
+    }
+    break;
+  }
+  __syncwarp();
+  const int status = bh ? MDX_V_BUDGET_EXCEEDED : (restarts > 0 ? MDX_V_EMPTY_RETRIED : MDX_V_OK);
+  finish_request(g, q, r, cx, cs, cped, ncand, E, status, nodes, peds, restarts, flops, lane);
+}
+
+// K-best of one request by one warp (SPL survivor slots per lane, K <= 32 SPL).
+template <int SPL>
+__device__ void kb_request(const MixedArgs& g, const MixedReq& q, int r, const float* Rc, const float* yb,
+                           unsigned char* st, float E, int lane) {
+  const int n = q.n, P = q.P, K = q.K, pp = path_stride(n);
+  unsigned int* r2w = reinterpret_cast<unsigned int*>(st);
+  float* pa = reinterpret_cast<float*>(st + 16);
+  float* pb = pa + round_up(K, 4);
+  uint16_t* sel = reinterpret_cast<uint16_t*>(pb + round_up(K, 4));
+  uint8_t* xa = reinterpret_cast<uint8_t*>(sel + 2 * round_up(K, 8));
+  uint8_t* xb = xa + (size_t)pp * K;
+  float r2 = initial_r2(g, q, r);
+  long long nodes = 0, flops = 0;
+  int restarts = 0, S = 0;
+  uint8_t *xcur = xa, *xnxt = xb;
+  float *pcur = pa, *pnxt = pb;
+  for (;;) {
+    xcur = xa;
+    xnxt = xb;
+    pcur = pa;
+    pnxt = pb;
+    if (lane == 0) {
+      *r2w = __float_as_uint(r2);
+      pa[0] = 0.0f;
+    }
+    __syncwarp();
+    S = warp_kbest<SPL>(Rc, yb, n, P, K, pp, q.alpha, n - 1, r2w, E, sel, &xcur, &xnxt, &pcur, &pnxt, lane, &nodes,
+                        &flops);
+    __syncwarp();
+    if (S > 0 || !(r2 < INFINITY) || restarts >= 64) break;
+    r2 *= 4.0f;  // every survivor left the sphere: r^2 <- 4 r^2
+    ++restarts;
+  }
+  const int nc = S < kCandMax ? S : kCandMax;
+  finish_request(g, q, r, xcur, pp, pcur, nc, E, restarts > 0 ? MDX_V_EMPTY_RETRIED : MDX_V_OK, nodes,
+                 nodes * P, restarts, flops, lane);
+}
+
+template <int KSPL>
+__global__ void mixed_kernel(MixedArgs g) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, W = blockDim.x >> 5;
+  unsigned char* slice = smem + (size_t)warp * g.slice_bytes;
+  unsigned char* gslot = g.gscratch + ((size_t)blockIdx.x * W + warp) * g.gslot_bytes;
+  for (;;) {
+    unsigned int t = 0;
+    if (lane == 0) t = atomicAdd(g.counter, 1u);
+    t = __shfl_sync(0xffffffffu, t, 0);
+    if (t >= (unsigned int)g.nreq) break;
+    const int r = g.order[t];
+    const MixedReq q = g.reqs[r];
+    if (g.singular[r]) {
+      for (int j = lane; j < q.n_tx; j += 32) g.sym_out[q.sym_off + j] = 0;
+      if (lane == 0) {
+        g.metric_out[r] = 0.0;
+        g.vstatus[r] = MDX_V_SINGULAR;
+        if (g.stats)
+          for (int k = 0; k < kStats; ++k) g.stats[(size_t)r * kStats + k] = 0;
+      }
+      continue;
+    }
+    const float* Rc = g.R32 + q.r_off;
+    const float* yb = g.yb32 + q.y_off;
+    unsigned char* st = gslot;
+    if (q.mode & MIX_STAGE_R) {
+      const int ts = tri_stride32(q.n);
+      float* sR = reinterpret_cast<float*>(slice);
+      float* sy = sR + ts;
+      const float4* src = reinterpret_cast<const float4*>(Rc);
+      for (int k = lane; k < ts / 4; k += 32) reinterpret_cast<float4*>(sR)[k] = src[k];
+      for (int k = lane; k < q.n; k += 32) sy[k] = yb[k];
+      Rc = sR;
+      yb = sy;
+      if (q.mode & MIX_STATE_SMEM) st = slice + stage_bytes(q.n);
+    } else if (q.mode & MIX_STATE_SMEM) {
+      st = slice;
+    }
+    __syncwarp();
+    const float E = error_scale_warp(q.n, q.P, q.alpha, Rc, yb, lane);
+    if (q.algo == MDX_ALGO_SD) {
+      if (q.n <= 32) sd_request<1>(g, q, r, Rc, yb, st, E, lane);
+      else if (q.n <= 64) sd_request<2>(g, q, r, Rc, yb, st, E, lane);
+      else if (q.n <= 128) sd_request<4>(g, q, r, Rc, yb, st, E, lane);
+      else sd_request<7>(g, q, r, Rc, yb, st, E, lane);
+    } else {
+      if (q.K <= 32) kb_request<1>(g, q, r, Rc, yb, st, E, lane);
+      else if (KSPL <= 2 || q.K <= 64) kb_request<2>(g, q, r, Rc, yb, st, E, lane);
+      else if constexpr (KSPL > 2) {
+        if (q.K <= 128) kb_request<4>(g, q, r, Rc, yb, st, E, lane);
+        else kb_request<8>(g, q, r, Rc, yb, st, E, lane);
+      }
+    }
+    __syncwarp();
+  }
+}
+
+template <int KSPL>
+cudaError_t prepare(int W, int slice_bytes, int num_sms, int* grid) {
+  const int smem = W * slice_bytes;
+  cudaError_t e = cudaFuncSetAttribute(mixed_kernel<KSPL>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (e != cudaSuccess) return e;
+  int per_sm = 0;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, mixed_kernel<KSPL>, W * 32, (size_t)smem);
+  if (e != cudaSuccess) return e;
+  if (per_sm < 1) return cudaErrorInvalidConfiguration;
+  *grid = per_sm * num_sms;
+  return cudaSuccess;
+}
+
+}  // namespace
+
+size_t mixed_stage_bytes(int n) { return stage_bytes(n); }
+
+size_t mixed_state_bytes(int algo, int n, int K) {
+  return algo == MDX_ALGO_SD ? sd_state_bytes(n) : kb_state_bytes(n, K);
+}
+
+int mixed_resident_warps(int W, int slice_bytes, int max_K, int num_sms) {
+  int grid = 0;
+  const cudaError_t e = (max_K > 64) ? prepare<8>(W, slice_bytes, num_sms, &grid)
+                                     : prepare<2>(W, slice_bytes, num_sms, &grid);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  return grid * W;
+}
+
+cudaError_t launch_mixed(const MixedArgs& a, int W, int max_K, int num_sms, cudaStream_t s) {
+  if (a.nreq <= 0) return cudaSuccess;
+  if (W < 1 || W > 32 || a.slice_bytes < 0 || (a.slice_bytes & 15)) return cudaErrorInvalidConfiguration;
+  int grid = 0;
+  cudaError_t e = (max_K > 64) ? prepare<8>(W, a.slice_bytes, num_sms, &grid)
+                               : prepare<2>(W, a.slice_bytes, num_sms, &grid);
+  if (e != cudaSuccess) return e;
+  const size_t smem = (size_t)W * a.slice_bytes;
+  if (max_K > 64) mixed_kernel<8><<<grid, W * 32, smem, s>>>(a);
+  else mixed_kernel<2><<<grid, W * 32, smem, s>>>(a);
+  return cudaGetLastError();
+}
+
+}  // namespace mdx

@@ -18,17 +18,27 @@ __device__ __forceinline__ double group_sum(double v) {
   return v;
 }
 
+// Output bases of one matrix (any pointer may be null).
+struct QrDst {
+  double* R64;
+  double* yb64;
+  float* R32;
+  float* yb32;
+  double* Rdense;
+  double* ybdense;
+  int* singular;
+};
+
+// Factorises one [H | y] (N x M complex, row-major; y of N) with the calling CTA.
 template <int LPC>
-__global__ void qr_kernel(int batch, int N, int M, const double* __restrict__ H,
-                          const double* __restrict__ y, QrOut out) {
+__device__ void qr_one(int N, int M, const double2* __restrict__ Hb, const double2* __restrict__ yb,
+                       const QrDst& out) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   double2* A = reinterpret_cast<double2*>(smem_raw);  // column-major, (M+1) columns of N
   double2* alpha = A + (size_t)(M + 1) * N;           // R_kk before the phase fix
   double* tau = reinterpret_cast<double*>(alpha + M);
   int* sing = reinterpret_cast<int*>(tau + M);
 
-  const int b = blockIdx.x;
-  if (b >= batch) return;
   const int tid = threadIdx.x;
   const int nthr = blockDim.x;
   const int lane_g = tid % LPC;  // lane within the column worker
@@ -36,8 +46,6 @@ __global__ void qr_kernel(int batch, int N, int M, const double* __restrict__ H,
   const int nworkers = nthr / LPC;
 
   // load [H | y] (global row-major complex) into column-major smem
-  const double2* Hb = reinterpret_cast<const double2*>(H) + (size_t)b * N * M;
-  const double2* yb = reinterpret_cast<const double2*>(y) + (size_t)b * N;
   for (int t = tid; t < N * M; t += nthr) {
     const int r = t / M, c = t % M;
     A[(size_t)c * N + r] = Hb[t];
@@ -138,16 +146,16 @@ __global__ void qr_kernel(int batch, int N, int M, const double* __restrict__ H,
       const int rr = rows[e], cc = cols[e];
       if (rr > cc) continue;  // below the diagonal (only in diagonal blocks)
       const double v = vals[e];
-      if (out.R64) out.R64[(size_t)b * tri_stride64(n) + col_off(cc) + rr] = v;
-      if (out.R32) out.R32[(size_t)b * tri_stride32(n) + col_off(cc) + rr] = (float)v;
-      if (out.Rdense) out.Rdense[(size_t)b * n * n + (size_t)rr * n + cc] = v;
+      if (out.R64) out.R64[col_off(cc) + rr] = v;
+      if (out.R32) out.R32[col_off(cc) + rr] = (float)v;
+      if (out.Rdense) out.Rdense[(size_t)rr * n + cc] = v;
     }
   }
   if (out.Rdense) {
     // zero the rest of the lower triangle
     for (int t = tid; t < n * n; t += nthr) {
       const int rr = t / n, cc = t % n;
-      if (rr > cc) out.Rdense[(size_t)b * n * n + t] = 0.0;
+      if (rr > cc) out.Rdense[t] = 0.0;
     }
   }
   for (int a = tid; a < M; a += nthr) {
@@ -157,28 +165,78 @@ __global__ void qr_kernel(int batch, int N, int M, const double* __restrict__ H,
     const double2 r = A[(size_t)M * N + a];
     const double re = r.x * ph.x + r.y * ph.y, im = r.y * ph.x - r.x * ph.y;
     if (out.yb64) {
-      out.yb64[(size_t)b * vec_stride64(n) + 2 * a] = re;
-      out.yb64[(size_t)b * vec_stride64(n) + 2 * a + 1] = im;
+      out.yb64[2 * a] = re;
+      out.yb64[2 * a + 1] = im;
     }
     if (out.yb32) {
-      out.yb32[(size_t)b * vec_stride32(n) + 2 * a] = (float)re;
-      out.yb32[(size_t)b * vec_stride32(n) + 2 * a + 1] = (float)im;
+      out.yb32[2 * a] = (float)re;
+      out.yb32[2 * a + 1] = (float)im;
     }
     if (out.ybdense) {
-      out.ybdense[(size_t)b * n + 2 * a] = re;
-      out.ybdense[(size_t)b * n + 2 * a + 1] = im;
+      out.ybdense[2 * a] = re;
+      out.ybdense[2 * a + 1] = im;
     }
   }
-  if (out.singular && tid == 0) out.singular[b] = *sing;
+  if (out.singular && tid == 0) *out.singular = *sing;
+}
+
+template <int LPC>
+__global__ void qr_kernel(int batch, int N, int M, const double* __restrict__ H,
+                          const double* __restrict__ y, QrOut out) {
+  const int b = blockIdx.x;
+  if (b >= batch) return;
+  const int n = 2 * M;
+  QrDst d;
+  d.R64 = out.R64 ? out.R64 + (size_t)b * tri_stride64(n) : nullptr;
+  d.yb64 = out.yb64 ? out.yb64 + (size_t)b * vec_stride64(n) : nullptr;
+  d.R32 = out.R32 ? out.R32 + (size_t)b * tri_stride32(n) : nullptr;
+  d.yb32 = out.yb32 ? out.yb32 + (size_t)b * vec_stride32(n) : nullptr;
+  d.Rdense = out.Rdense ? out.Rdense + (size_t)b * n * n : nullptr;
+  d.ybdense = out.ybdense ? out.ybdense + (size_t)b * n : nullptr;
+  d.singular = out.singular ? out.singular + b : nullptr;
+  qr_one<LPC>(N, M, reinterpret_cast<const double2*>(H) + (size_t)b * N * M,
+              reinterpret_cast<const double2*>(y) + (size_t)b * N, d);
+}
+
+// One CTA per listed request of an uneven batch (all of one n_rx x n_tx);
+// inputs and outputs at the request's own offsets.
+template <int LPC>
+__global__ void qr_gather_kernel(int count, const int* __restrict__ ids, const MixedReq* __restrict__ reqs,
+                                 const double* __restrict__ H, const double* __restrict__ y, QrOut out) {
+  if ((int)blockIdx.x >= count) return;
+  const int r = ids[blockIdx.x];
+  const MixedReq q = reqs[r];
+  QrDst d{out.R64 + q.r_off, out.yb64 + q.y_off, out.R32 + q.r_off, out.yb32 + q.y_off, nullptr, nullptr,
+          out.singular + r};
+  qr_one<LPC>(q.n_rx, q.n_tx, reinterpret_cast<const double2*>(H + q.h_off),
+              reinterpret_cast<const double2*>(y + q.yin_off), d);
+}
+
+size_t qr_smem(int n_rx, int n_tx) {
+  return sizeof(double2) * ((size_t)(n_tx + 1) * n_rx + n_tx) + sizeof(double) * n_tx + sizeof(int) * 4;
 }
 
 }  // namespace
 
+cudaError_t launch_qr_gather(int count, int n_rx, int n_tx, const int* ids, const MixedReq* reqs,
+                             const double* H, const double* y, QrOut out, cudaStream_t s) {
+  if (count <= 0) return cudaSuccess;
+  const size_t smem = qr_smem(n_rx, n_tx);
+  if (n_rx <= 16) {
+    cudaFuncSetAttribute(qr_gather_kernel<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    qr_gather_kernel<16><<<count, 32, smem, s>>>(count, ids, reqs, H, y, out);
+  } else {
+    const int threads = n_tx <= 32 ? 128 : 256;
+    cudaFuncSetAttribute(qr_gather_kernel<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    qr_gather_kernel<32><<<count, threads, smem, s>>>(count, ids, reqs, H, y, out);
+  }
+  return cudaGetLastError();
+}
+
 cudaError_t launch_qr(int batch, int n_rx, int n_tx, const double* H, const double* y, QrOut out,
                       cudaStream_t s) {
   if (batch <= 0) return cudaSuccess;
-  const size_t smem = sizeof(double2) * ((size_t)(n_tx + 1) * n_rx + n_tx) + sizeof(double) * n_tx +
-                      sizeof(int) * 4;
+  const size_t smem = qr_smem(n_rx, n_tx);
   if (n_rx <= 16) {
     // two 16-lane workers per warp
     cudaFuncSetAttribute(qr_kernel<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);

@@ -21,13 +21,15 @@ MDX_OK, MDX_EINVAL, MDX_EUNSUPPORTED, MDX_ENOMEM, MDX_ECUDA = 0, -1, -2, -3, -4
 MDX_V_OK, MDX_V_EMPTY_RETRIED, MDX_V_BUDGET_EXCEEDED, MDX_V_SINGULAR = 0, 1, 2, 3
 MDX_HOST_BUFFERS, MDX_NO_RESCORE, MDX_LEARNED_RADIUS, MDX_SEQUENTIAL_SEARCH = 1, 2, 4, 8
 MDX_MAX_TX, MDX_MAX_RX, MDX_MAX_K = 100, 128, 256
+MDX_ALGO_SD, MDX_ALGO_KBEST = 0, 1
+MDX_GRAPH = 1 << 4
 
 # Every symbol the header declares; the library must export all of them.
 EXPORTS = ["mdx_create", "mdx_destroy", "mdx_strerror", "mdx_last_error", "mdx_workspace_bytes",
            "mdx_qr", "detect_sd", "detect_kbest", "detect_hybrid", "mdx_count_errors",
            "mdx_profile", "mdx_profile_read", "detect_kbest_noalloc", "mdx_mlp_param_count",
            "mdx_mlp_dims", "mdx_mlp_init", "mdx_mlp_set_params", "mdx_mlp_get_params", "mdx_mlp_predict",
-           "mdx_mlp_train_step", "mdx_mlp_error"]
+           "mdx_mlp_train_step", "mdx_mlp_error", "detect_mixed", "mdx_autotune_mixed"]
 NOALLOC_SCRATCH_BYTES = 16 << 20
 STATS = 5  # per-vector stats: nodes, peds, restarts, rescored, algorithmic FP32 flops
 
@@ -49,6 +51,15 @@ def make_params(n_rx, n_tx, qam, radius=math.inf, K=16, depth=4, budget=0, flags
     """radius: float r^2 (inf = none) or 'paper' for r^2 = N M sigma^2."""
     r = -1.0 if isinstance(radius, str) else float(radius)
     return Params(int(n_rx), int(n_tx), int(qam), r, int(K), int(depth), int(budget), int(flags))
+
+
+# mdx_request as a numpy structured type (64 bytes, the C layout)
+def request_dtype():
+    import numpy as np
+
+    return np.dtype([("n_rx", "<i4"), ("n_tx", "<i4"), ("qam", "<i4"), ("algo", "<i4"), ("K", "<i4"),
+                     ("pad", "<i4"), ("init_radius_sq", "<f8"), ("node_budget", "<i8"), ("h_offset", "<i8"),
+                     ("y_offset", "<i8"), ("sym_offset", "<i8")])
 
 
 _lock = threading.Lock()
@@ -101,6 +112,10 @@ def lib():
             L.mdx_mlp_train_step.restype = i
             L.mdx_mlp_error.argtypes = [vp, vp]
             L.mdx_mlp_error.restype = i
+            L.detect_mixed.argtypes = [vp, i, vp, vp, vp, vp, vp, vp, vp, vp, i, vp]
+            L.detect_mixed.restype = i
+            L.mdx_autotune_mixed.argtypes = [vp, i, vp, vp, vp, vp, vp, vp, vp, vp, vp]
+            L.mdx_autotune_mixed.restype = i
             L.mdx_profile.argtypes = [vp, i]
             L.mdx_profile.restype = i
             L.mdx_profile_read.argtypes = [vp, vp]
@@ -253,6 +268,95 @@ def count_errors(ctx: Context, sym_hat, sym_true, qam: int, stream=None):
                                 _stream(stream))
     ctx.check(st, "mdx_count_errors")
     return out
+
+
+# ----------------------------------------------------------------------------- uneven batches
+
+
+def make_requests(n_rx, n_tx, qam, algo, K=64, radius=None, budget=0, h_offset=None, y_offset=None,
+                  sym_offset=None):
+    """A request table (numpy, request_dtype) from per-request arrays.
+    radius: per-request r^2 (inf = none, negative = the paper's N M sigma^2);
+    default: the paper's radius for exact SD, none for K-best.  Offsets
+    default to the requests packed back to back in table order."""
+    import numpy as np
+
+    n_rx = np.asarray(n_rx, dtype=np.int64)
+    cnt = n_rx.size
+    t = np.zeros(cnt, dtype=request_dtype())
+    t["n_rx"] = n_rx
+    t["n_tx"] = np.broadcast_to(np.asarray(n_tx), (cnt,))
+    t["qam"] = np.broadcast_to(np.asarray(qam), (cnt,))
+    t["algo"] = np.broadcast_to(np.asarray(algo), (cnt,))
+    t["K"] = np.broadcast_to(np.asarray(K), (cnt,))
+    if radius is None:
+        radius = np.where(t["algo"] == MDX_ALGO_SD, -1.0, math.inf)
+    t["init_radius_sq"] = np.broadcast_to(np.asarray(radius, dtype=np.float64), (cnt,))
+    t["node_budget"] = np.broadcast_to(np.asarray(budget), (cnt,))
+    hsz = 2 * t["n_rx"].astype(np.int64) * t["n_tx"]
+    ysz = 2 * t["n_rx"].astype(np.int64)
+    t["h_offset"] = np.concatenate([[0], np.cumsum(hsz)[:-1]]) if h_offset is None else h_offset
+    t["y_offset"] = np.concatenate([[0], np.cumsum(ysz)[:-1]]) if y_offset is None else y_offset
+    t["sym_offset"] = (np.concatenate([[0], np.cumsum(t["n_tx"].astype(np.int64))[:-1]])
+                       if sym_offset is None else sym_offset)
+    return t
+
+
+def _table(reqs):
+    import numpy as np
+
+    reqs = np.ascontiguousarray(reqs, dtype=request_dtype())
+    return reqs, ctypes.c_void_p(reqs.ctypes.data) if reqs.size else None
+
+
+def detect_mixed(ctx: Context, reqs, H, y, noise_var, flags=0, stream=None, want_stats=True, out=None):
+    """detect_mixed over a request table (see make_requests) and flat float64
+    CUDA tensors H, y, noise_var [nreq].  Returns (sym (flat uint8, indexed by
+    sym_offset), metric [nreq], vstatus [nreq], stats [nreq][STATS])."""
+    import torch
+
+    reqs, tp = _table(reqs)
+    nreq = int(reqs.size)
+    if out is None:
+        nsym = int((reqs["sym_offset"] + reqs["n_tx"]).max()) if nreq else 0
+        dev = H.device
+        out = (torch.zeros(max(nsym, 1), dtype=torch.uint8, device=dev),
+               torch.empty(max(nreq, 1), dtype=torch.float64, device=dev),
+               torch.empty(max(nreq, 1), dtype=torch.int32, device=dev),
+               torch.empty((max(nreq, 1), STATS), dtype=torch.int64, device=dev) if want_stats else None)
+    sym, met, vst, stats = out
+    st = lib().detect_mixed(ctx.handle, nreq, tp, _ptr(H), _ptr(y), _ptr(noise_var), _ptr(sym), _ptr(met),
+                            _ptr(vst), _ptr(stats), int(flags), _stream(stream))
+    ctx.check(st, "detect_mixed")
+    return sym, met, vst, stats
+
+
+def detect_mixed_host(ctx: Context, reqs, H, y, noise_var, sym, metric, vstatus, stats=None, flags=0,
+                      stream=None):
+    """detect_mixed on numpy host arrays (outputs preallocated), staged through
+    the context's device buffers (MDX_HOST_BUFFERS); returns when the results
+    are in host memory."""
+    reqs, tp = _table(reqs)
+    st = lib().detect_mixed(ctx.handle, int(reqs.size), tp, _ptr(H), _ptr(y), _ptr(noise_var), _ptr(sym),
+                            _ptr(metric), _ptr(vstatus), _ptr(stats), int(flags) | MDX_HOST_BUFFERS,
+                            _stream(stream))
+    ctx.check(st, "detect_mixed")
+
+
+def autotune_mixed(ctx: Context, reqs, H, y, noise_var, stream=None):
+    """Tune the uneven-batch kernel for this table (outputs are scratch);
+    returns {"warps_per_cta", "slice_bytes", "ms"}."""
+    import numpy as np
+    import torch
+
+    reqs, tp = _table(reqs)
+    sym, met, vst, _ = detect_mixed(ctx, reqs, H, y, noise_var, stream=stream, want_stats=False)
+    res = np.zeros(3)
+    st = lib().mdx_autotune_mixed(ctx.handle, int(reqs.size), tp, _ptr(H), _ptr(y), _ptr(noise_var), _ptr(sym),
+                                  _ptr(met), _ptr(vst), ctypes.c_void_p(res.ctypes.data), _stream(stream))
+    ctx.check(st, "mdx_autotune_mixed")
+    torch.cuda.synchronize()
+    return {"warps_per_cta": int(res[0]), "slice_bytes": int(res[1]), "ms": float(res[2])}
 
 
 # ----------------------------------------------------------------------------- learned radius

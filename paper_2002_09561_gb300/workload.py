@@ -128,3 +128,38 @@ def generate_mixed(seed: int, count: int, antennas=(8, 16, 32, 64, 100), qams=(4
     snr = snr_range[0] + (snr_range[1] - snr_range[0]) * u[:, 2]
     algo = (u[:, 3] >= sd_fraction).astype(np.int32)
     return {"n": ant.astype(np.int32), "qam": qm.astype(np.int32), "snr_db": snr, "algo": algo}
+
+
+def generate_mixed_inputs(seed: int, count: int, antennas=(8, 16, 32, 64, 100), qams=(4, 16, 64),
+                          snr_range=(6.0, 30.0), sd_fraction=0.5):
+    """The mix of generate_mixed together with its inputs.  Each (n, qam)
+    class is one generate() workload under the seed
+    seed * 1000003 + 1000 n + qam, whose rows go to the class's requests in
+    table order.  Returns the descriptor arrays of generate_mixed plus
+    H and y (float64, the requests' [N][M][2] and [N][2] blocks back to back
+    in table order), noise_var, sym (uint8, [n_tx] per request, back to back)
+    and the offsets h_offset, y_offset, sym_offset of every request."""
+    d = generate_mixed(seed, count, antennas, qams, snr_range, sd_fraction)
+    n = d["n"].astype(np.int64)
+    hsz, ysz = 2 * n * n, 2 * n
+    h_off = np.concatenate([[0], np.cumsum(hsz)[:-1]]).astype(np.int64)
+    y_off = np.concatenate([[0], np.cumsum(ysz)[:-1]]).astype(np.int64)
+    s_off = np.concatenate([[0], np.cumsum(n)[:-1]]).astype(np.int64)
+    H = np.empty(int(hsz.sum()))
+    y = np.empty(int(ysz.sum()))
+    sym = np.empty(int(n.sum()), dtype=np.uint8)
+    for a in np.unique(n):
+        for q in np.unique(d["qam"]):
+            idx = np.flatnonzero((n == a) & (d["qam"] == q))
+            if idx.size == 0:
+                continue
+            w = generate(int(seed) * 1000003 + 1000 * int(a) + int(q), idx.size, int(a), int(a), int(q),
+                         d["snr_db"][idx])
+            Hw, yw = w["H"].reshape(idx.size, -1), w["y"].reshape(idx.size, -1)
+            for j, r in enumerate(idx):
+                H[h_off[r]:h_off[r] + hsz[r]] = Hw[j]
+                y[y_off[r]:y_off[r] + ysz[r]] = yw[j]
+                sym[s_off[r]:s_off[r] + a] = w["sym"][j]
+    d.update({"H": H, "y": y, "noise_var": noise_var_from_snr(d["snr_db"]), "sym": sym, "h_offset": h_off,
+              "y_offset": y_off, "sym_offset": s_off})
+    return d
