@@ -29,6 +29,84 @@ struct QrDst {
   int* singular;
 };
 
+// Phase fix and output of a factorised [R | ybar]: row k of R and ybar_k are
+// multiplied by conj(alpha_k / |alpha_k|) so that R_kk = |alpha_k| > 0; R is
+// written in the real interleaved form (entry r_ab -> [[Re,-Im],[Im,Re]]).
+// getA(c, r) returns the complex entry of column c, row r (r < c for R, the
+// ybar column is c = M).
+// alpha and tau are overwritten: alpha_k by its phase alpha_k / |alpha_k|
+// (1 if zero) and tau_k by |alpha_k|.
+template <typename GetA>
+__device__ void qr_writeout(int M, GetA getA, double2* alpha, double* tau, const QrDst& out) {
+  const int tid = threadIdx.x;
+  const int nthr = blockDim.x;
+  for (int a = tid; a < M; a += nthr) {
+    const double2 al = alpha[a];
+    const double aa = hypot(al.x, al.y);
+    alpha[a] = (aa > 0.0) ? make_double2(al.x / aa, al.y / aa) : make_double2(1.0, 0.0);
+    tau[a] = aa;
+  }
+  __syncthreads();
+  const int n = 2 * M;
+  const int nb = M * (M + 1) / 2;  // complex entries (a, c) with a <= c
+  for (int t = tid; t < nb; t += nthr) {
+    // unrank t -> (a, c), a <= c, column-major over c
+    int c = (int)((sqrt(8.0 * t + 1.0) - 1.0) * 0.5);
+    while (c * (c + 1) / 2 > t) --c;
+    while ((c + 1) * (c + 2) / 2 <= t) ++c;
+    const int a = t - c * (c + 1) / 2;
+    const double2 ph = alpha[a];
+    const double aa = tau[a];
+    double re, im;
+    if (a == c) {
+      re = aa;
+      im = 0.0;
+    } else {
+      const double2 r = getA(c, a);
+      re = r.x * ph.x + r.y * ph.y;  // r * conj(ph)
+      im = r.y * ph.x - r.x * ph.y;
+    }
+    const int r0 = 2 * a, c0 = 2 * c;
+    // the 2x2 block [[re, -im], [im, re]] at rows r0..r0+1, columns c0..c0+1
+    const double vals[4] = {re, -im, im, re};
+    const int rows[4] = {r0, r0, r0 + 1, r0 + 1};
+    const int cols[4] = {c0, c0 + 1, c0, c0 + 1};
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      const int rr = rows[e], cc = cols[e];
+      if (rr > cc) continue;  // below the diagonal (only in diagonal blocks)
+      const double v = vals[e];
+      if (out.R64) out.R64[col_off(cc) + rr] = v;
+      if (out.R32) out.R32[col_off(cc) + rr] = (float)v;
+      if (out.Rdense) out.Rdense[(size_t)rr * n + cc] = v;
+    }
+  }
+  if (out.Rdense) {
+    // zero the rest of the lower triangle
+    for (int t = tid; t < n * n; t += nthr) {
+      const int rr = t / n, cc = t % n;
+      if (rr > cc) out.Rdense[t] = 0.0;
+    }
+  }
+  for (int a = tid; a < M; a += nthr) {
+    const double2 ph = alpha[a];
+    const double2 r = getA(M, a);
+    const double re = r.x * ph.x + r.y * ph.y, im = r.y * ph.x - r.x * ph.y;
+    if (out.yb64) {
+      out.yb64[2 * a] = re;
+      out.yb64[2 * a + 1] = im;
+    }
+    if (out.yb32) {
+      out.yb32[2 * a] = (float)re;
+      out.yb32[2 * a + 1] = (float)im;
+    }
+    if (out.ybdense) {
+      out.ybdense[2 * a] = re;
+      out.ybdense[2 * a + 1] = im;
+    }
+  }
+}
+
 // Factorises one [H | y] (N x M complex, row-major; y of N) with the calling CTA.
 template <int LPC>
 __device__ void qr_one(int N, int M, const double2* __restrict__ Hb, const double2* __restrict__ yb,
@@ -115,70 +193,443 @@ __device__ void qr_one(int N, int M, const double2* __restrict__ Hb, const doubl
     __syncthreads();
   }
 
-  // phase fix: row k of R and ybar_k times conj(alpha_k / |alpha_k|), R_kk = |alpha_k|
-  const int n = 2 * M;
-  const int nb = M * (M + 1) / 2;  // complex entries (a, c) with a <= c
-  for (int t = tid; t < nb; t += nthr) {
-    // unrank t -> (a, c), a <= c, column-major over c
-    int c = (int)((sqrt(8.0 * t + 1.0) - 1.0) * 0.5);
-    while (c * (c + 1) / 2 > t) --c;
-    while ((c + 1) * (c + 2) / 2 <= t) ++c;
-    const int a = t - c * (c + 1) / 2;
-    const double2 al = alpha[a];
-    const double aa = hypot(al.x, al.y);
-    const double2 ph = (aa > 0.0) ? make_double2(al.x / aa, al.y / aa) : make_double2(1.0, 0.0);
-    double re, im;
-    if (a == c) {
-      re = aa;
-      im = 0.0;
-    } else {
-      const double2 r = A[(size_t)c * N + a];
-      re = r.x * ph.x + r.y * ph.y;  // r * conj(ph)
-      im = r.y * ph.x - r.x * ph.y;
-    }
-    const int r0 = 2 * a, c0 = 2 * c;
-    // the 2x2 block [[re, -im], [im, re]] at rows r0..r0+1, columns c0..c0+1
-    const double vals[4] = {re, -im, im, re};
-    const int rows[4] = {r0, r0, r0 + 1, r0 + 1};
-    const int cols[4] = {c0, c0 + 1, c0, c0 + 1};
-#pragma unroll
-    for (int e = 0; e < 4; ++e) {
-      const int rr = rows[e], cc = cols[e];
-      if (rr > cc) continue;  // below the diagonal (only in diagonal blocks)
-      const double v = vals[e];
-      if (out.R64) out.R64[col_off(cc) + rr] = v;
-      if (out.R32) out.R32[col_off(cc) + rr] = (float)v;
-      if (out.Rdense) out.Rdense[(size_t)rr * n + cc] = v;
-    }
-  }
-  if (out.Rdense) {
-    // zero the rest of the lower triangle
-    for (int t = tid; t < n * n; t += nthr) {
-      const int rr = t / n, cc = t % n;
-      if (rr > cc) out.Rdense[t] = 0.0;
-    }
-  }
-  for (int a = tid; a < M; a += nthr) {
-    const double2 al = alpha[a];
-    const double aa = hypot(al.x, al.y);
-    const double2 ph = (aa > 0.0) ? make_double2(al.x / aa, al.y / aa) : make_double2(1.0, 0.0);
-    const double2 r = A[(size_t)M * N + a];
-    const double re = r.x * ph.x + r.y * ph.y, im = r.y * ph.x - r.x * ph.y;
-    if (out.yb64) {
-      out.yb64[2 * a] = re;
-      out.yb64[2 * a + 1] = im;
-    }
-    if (out.yb32) {
-      out.yb32[2 * a] = (float)re;
-      out.yb32[2 * a + 1] = (float)im;
-    }
-    if (out.ybdense) {
-      out.ybdense[2 * a] = re;
-      out.ybdense[2 * a + 1] = im;
-    }
-  }
+  qr_writeout(M, [&](int c, int r) { return A[(size_t)c * N + r]; }, alpha, tau, out);
   if (out.singular && tid == 0) *out.singular = *sing;
 }
+
+// ---------------------------------------------------------------------------
+// Blocked Householder QR with the trailing updates on the FP64 tensor cores.
+//
+// Measured on this GPU: an m8n8k4 FP64 MMA occupies a scheduler's FP64 unit
+// for about 585 cycles (256 FMA) and an FP64 FMA instruction for about 75
+// (32 FMA), so the MMA path is not faster per FMA; it wins (for n_tx >= 48)
+// because the block update needs no cross-lane reductions, and loses to
+// qr_one on small matrices, where the panel dominates.
+//
+// Same reflectors as qr_one (H_k = I - tau_k v_k v_k^H, tau_k real), taken in
+// panels of 8 columns.  On this GPU an FP64 instruction of one warp occupies
+// its scheduler's FP64 unit for tens of cycles, so the level-2 panel is
+// spread over four warps, one per scheduler, each holding 32 rows of the
+// panel in registers (lane = row); column sums are warp reductions plus one
+// exchange through shared memory.  The panel also builds Y = V T, the
+// compact-WY form H_k ... H_{k+7} = I - V T V^H (Y_j = tau_j (v_j -
+// Y[:, 0:j] (V[:, 0:j]^H v_j)), T_jj = tau_j), so that the columns right of
+// the panel are updated as A_t <- A_t - V (Y^H A_t) in two FP64 MMA steps
+// (mma.sync m8n8k4 .f64; complex products as four real ones), 8 columns per
+// warp task.  Matrices live in shared memory as separate real and imaginary
+// planes, column-major with a column stride of N8 + 4 doubles (N8 = N
+// rounded up to 8), zero-padded to N8 rows and C8 = round_up(M + 1, 8)
+// columns, so the MMA tiles need no masks; the padding stays zero.
+
+constexpr int kQrdWarps = 8;
+constexpr int kPanelWarps = 4;
+constexpr int kTileStride = 12;  // doubles per column of a warp's 8 x 8 tile
+
+struct QrdLayout {
+  int N8, C8, S;
+  size_t off_are, off_aim, off_vre, off_vim, off_yre, off_yim, off_tile, off_red, off_alpha, off_tau, off_sing,
+      bytes;
+  __host__ __device__ void init(int N, int M) {
+    N8 = round_up(N, 8);
+    C8 = round_up(M + 1, 8);
+    S = N8 + 4;
+    size_t o = 0;
+    auto take = [&](size_t bytes) {
+      const size_t at = o;
+      o += (bytes + 15) / 16 * 16;
+      return at;
+    };
+    off_are = take(sizeof(double) * (size_t)C8 * S);
+    off_aim = take(sizeof(double) * (size_t)C8 * S);
+    off_vre = take(sizeof(double) * 8 * (size_t)S);
+    off_vim = take(sizeof(double) * 8 * (size_t)S);
+    off_yre = take(sizeof(double) * 8 * (size_t)S);
+    off_yim = take(sizeof(double) * 8 * (size_t)S);
+    off_tile = take(sizeof(double) * 2 * 8 * kTileStride * kQrdWarps);
+    off_red = take(sizeof(double) * (8 + 2 * 16 * kPanelWarps));
+    off_alpha = take(sizeof(double2) * (size_t)M);
+    off_tau = take(sizeof(double) * (size_t)M);
+    off_sing = take(16);
+    bytes = o;
+  }
+};
+
+__device__ __forceinline__ void dmma(double& d0, double& d1, double a, double b) {
+  asm volatile("mma.sync.aligned.m8n8k4.row.col.f64.f64.f64.f64 {%0,%1}, {%2}, {%3}, {%0,%1};"
+               : "+d"(d0), "+d"(d1)
+               : "d"(a), "d"(b));
+}
+
+// Sign flip on the integer pipe: an FP64 negation would occupy the FP64 unit,
+// which the MMAs around it share.
+__device__ __forceinline__ double ineg(double x) {
+  return __hiloint2double(__double2hiint(x) ^ (int)0x80000000, __double2loint(x));
+}
+
+__device__ __forceinline__ double wsum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+__device__ __forceinline__ void panel_sync() { asm volatile("bar.sync 1, %0;" ::"n"(kPanelWarps * 32)); }
+
+// 1 / sqrt(x) for a positive normal x: a single-precision estimate refined by
+// two Newton-Raphson steps y <- y (3 - x y^2) / 2 (quadratic convergence from
+// about 2^-22 relative error to the double rounding level).
+__device__ __forceinline__ double rsqrt_nr(double x) {
+  if (!(x > 1e-30 && x < 1e30)) return 1.0 / sqrt(x);
+  double y = (double)rsqrtf((float)x);
+  const double hx = 0.5 * x;
+  y = y * fma(-hx * y, y, 1.5);
+  y = y * fma(-hx * y, y, 1.5);
+  return y;
+}
+// 1 / d for a positive normal d: single-precision estimate, two Newton-Raphson
+// steps y <- y (2 - d y).
+__device__ __forceinline__ double rcp_nr(double d) {
+  if (!(d > 1e-30 && d < 1e30)) return 1.0 / d;
+  double y = (double)(1.0f / (float)d);
+  y = y * fma(-d, y, 2.0);
+  y = y * fma(-d, y, 2.0);
+  return y;
+}
+
+// Sum of 16 per-lane values over the warp, scattered: on return lane l holds
+// the total of value (l >> 1) & 15 (16 additions instead of 80).
+__device__ __forceinline__ double reduce_scatter16(double (&v)[16], int lane) {
+  double a8[8], a4[4], a2[2];
+  {
+    const bool h = (lane >> 4) & 1;
+#pragma unroll
+    for (int m = 0; m < 8; ++m) {
+      const double keep = h ? v[8 + m] : v[m], give = h ? v[m] : v[8 + m];
+      a8[m] = keep + __shfl_xor_sync(0xffffffffu, give, 16);
+    }
+  }
+  {
+    const bool h = (lane >> 3) & 1;
+#pragma unroll
+    for (int m = 0; m < 4; ++m) {
+      const double keep = h ? a8[4 + m] : a8[m], give = h ? a8[m] : a8[4 + m];
+      a4[m] = keep + __shfl_xor_sync(0xffffffffu, give, 8);
+    }
+  }
+  {
+    const bool h = (lane >> 2) & 1;
+#pragma unroll
+    for (int m = 0; m < 2; ++m) {
+      const double keep = h ? a4[2 + m] : a4[m], give = h ? a4[m] : a4[2 + m];
+      a2[m] = keep + __shfl_xor_sync(0xffffffffu, give, 4);
+    }
+  }
+  const bool h = (lane >> 1) & 1;
+  const double keep = h ? a2[1] : a2[0], give = h ? a2[0] : a2[1];
+  double a1 = keep + __shfl_xor_sync(0xffffffffu, give, 2);
+  return a1 + __shfl_xor_sync(0xffffffffu, a1, 1);
+}
+
+// Factors the panel of columns k..k+7 (bw of them are reflector columns) with
+// warps 0..3, lane = row k + 32 warp + lane.  Writes the panel back, V (rows
+// relative to k, zero above each reflector's first row) and Y = V T.
+__device__ void qrd_panel(const QrdLayout& L, int k, int bw, double* Are, double* Aim, double* Vre, double* Vim,
+                          double* Yre, double* Yim, double* red, double2* alpha, double* tau, int* sing, int warp,
+                          int lane) {
+  const int S = L.S;
+  const int rr = 32 * warp + lane, r = k + rr;
+  const bool live = r < L.N8;
+  double pr[8], pi[8], yr[8], yi[8];
+#pragma unroll
+  for (int j = 0; j < 8; ++j) {
+    pr[j] = live ? Are[(size_t)(k + j) * S + r] : 0.0;
+    pi[j] = live ? Aim[(size_t)(k + j) * S + r] : 0.0;
+    yr[j] = 0.0;
+    yi[j] = 0.0;
+  }
+  double* rn = red;      // [0..3] norm partials, [4..5] x0
+  double* rd = red + 8;  // [warp][16] dot partials
+#pragma unroll
+  for (int j = 0; j < 8; ++j) {
+    if (j < bw) {
+      const bool in_j = rr >= j;  // row in the support of v_j
+      // ---- norm of the column's rows j.. and x0
+      double s = in_j ? fma(pr[j], pr[j], pi[j] * pi[j]) : 0.0;
+      s = wsum(s);
+      if (lane == 0) rn[warp] = s;
+      if (rr == j) {
+        rn[4] = pr[j];
+        rn[5] = pi[j];
+      }
+      panel_sync();
+      s = (rn[0] + rn[1]) + (rn[2] + rn[3]);
+      const double x0r = rn[4], x0i = rn[5];
+      double alr = 0.0, ali = 0.0, tj = 0.0;
+      if (s > 0.0) {
+        const double rs = rsqrt_nr(s);
+        const double sigma = s * rs;
+        const double q = fma(x0r, x0r, x0i * x0i);
+        double phr = 1.0, phi = 0.0, ax0 = 0.0;
+        if (q > 0.0) {
+          const double rq = rsqrt_nr(q);
+          ax0 = q * rq;
+          phr = x0r * rq;
+          phi = x0i * rq;
+        }
+        alr = -phr * sigma;
+        ali = -phi * sigma;
+        tj = rcp_nr(sigma * (sigma + ax0));
+      }
+      if (rr == j) {
+        pr[j] = x0r - alr;
+        pi[j] = x0i - ali;
+      }
+      if (rr == 0) {
+        alpha[k + j] = make_double2(alr, ali);
+        tau[k + j] = tj;
+        if (!(s > 0.0)) *sing = 1;
+      }
+      // ---- slot m < j: z_m = v_m^H v_j; slot m >= j: w_{m+1} = v_j^H a_{m+1}
+      double v[16];
+#pragma unroll
+      for (int m = 0; m < 7; ++m) {
+        const int c = (m < j) ? m : m + 1;
+        double dr, di;
+        if (m < j) {  // conj(v_m) v_j
+          dr = fma(pr[c], pr[j], pi[c] * pi[j]);
+          di = fma(pr[c], pi[j], -pi[c] * pr[j]);
+        } else {  // conj(v_j) a_c
+          dr = fma(pr[j], pr[c], pi[j] * pi[c]);
+          di = fma(pr[j], pi[c], -pi[j] * pr[c]);
+        }
+        v[2 * m] = in_j ? dr : 0.0;
+        v[2 * m + 1] = in_j ? di : 0.0;
+      }
+      v[14] = 0.0;
+      v[15] = 0.0;
+      const double part = reduce_scatter16(v, lane);
+      if ((lane & 1) == 0) rd[warp * 16 + (lane >> 1)] = part;
+      panel_sync();
+      const int vi = (lane >> 1) & 15;
+      const double tot = (rd[vi] + rd[16 + vi]) + (rd[32 + vi] + rd[48 + vi]);
+      double t[14];
+#pragma unroll
+      for (int m = 0; m < 14; ++m) t[m] = __shfl_sync(0xffffffffu, tot, 2 * m);
+      // ---- Y_j = tau_j (v_j - sum_{l<j} Y_l z_l)
+      {
+        double ar = in_j ? pr[j] : 0.0, ai = in_j ? pi[j] : 0.0;
+#pragma unroll
+        for (int l = 0; l < 8; ++l) {
+          if (l < j) {
+            const double zr = t[2 * l], zi = t[2 * l + 1];
+            ar = fma(-yr[l], zr, fma(yi[l], zi, ar));
+            ai = fma(-yr[l], zi, fma(-yi[l], zr, ai));
+          }
+        }
+        yr[j] = tj * ar;
+        yi[j] = tj * ai;
+      }
+      // ---- apply H_j to the panel columns right of j
+#pragma unroll
+      for (int c = 0; c < 8; ++c) {
+        if (c > j && in_j) {
+          const double wr = t[2 * (c - 1)] * tj, wi = t[2 * (c - 1) + 1] * tj;
+          const double vr = pr[j], vv = pi[j];
+          pr[c] -= fma(vr, wr, -vv * wi);
+          pi[c] -= fma(vr, wi, vv * wr);
+        }
+      }
+    }
+  }
+  if (live) {
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      Are[(size_t)(k + j) * S + r] = pr[j];
+      Aim[(size_t)(k + j) * S + r] = pi[j];
+      const bool in_v = (j < bw) && rr >= j;
+      Vre[j * S + rr] = in_v ? pr[j] : 0.0;
+      Vim[j * S + rr] = in_v ? pi[j] : 0.0;
+      Yre[j * S + rr] = (j < bw) ? yr[j] : 0.0;
+      Yim[j * S + rr] = (j < bw) ? yi[j] : 0.0;
+    }
+  }
+}
+
+// One warp: columns c0..c0+7 of rows k..N8-1 updated by the panel's block
+// reflector, A_t <- A_t - V (Y^H A_t).
+__device__ void qrd_tile(const QrdLayout& L, int k, int c0, double* Are, double* Aim, const double* Vre,
+                         const double* Vim, const double* Yre, const double* Yim, double* tre, double* tim,
+                         int lane) {
+  const int S = L.S, g = lane >> 2, q = lane & 3;
+  const int R8 = L.N8 - k;
+  // W = Y^H A_t: A operand (Y^H)[i][rr] = conj(Y[rr][i]), B operand A_t[rr][c];
+  // even and odd k-steps accumulate separately (four independent chains)
+  double ar0 = 0.0, ar1 = 0.0, ai0 = 0.0, ai1 = 0.0, br0 = 0.0, br1 = 0.0, bi0 = 0.0, bi1 = 0.0;
+  const double* bre = Are + (size_t)(c0 + g) * S + k;
+  const double* bim = Aim + (size_t)(c0 + g) * S + k;
+  const double* yre = Yre + g * S;
+  const double* yim = Yim + g * S;
+  int ks = 0;
+  for (; ks + 8 <= R8; ks += 8) {
+    {
+      const double vr = yre[ks + q], vi = yim[ks + q], xr = bre[ks + q], xi = bim[ks + q];
+      dmma(ar0, ar1, vr, xr);
+      dmma(ai0, ai1, vr, xi);
+      dmma(ar0, ar1, vi, xi);
+      dmma(ai0, ai1, ineg(vi), xr);
+    }
+    {
+      const double vr = yre[ks + 4 + q], vi = yim[ks + 4 + q], xr = bre[ks + 4 + q], xi = bim[ks + 4 + q];
+      dmma(br0, br1, vr, xr);
+      dmma(bi0, bi1, vr, xi);
+      dmma(br0, br1, vi, xi);
+      dmma(bi0, bi1, ineg(vi), xr);
+    }
+  }
+  tre[(2 * q) * kTileStride + g] = ar0 + br0;
+  tre[(2 * q + 1) * kTileStride + g] = ar1 + br1;
+  tim[(2 * q) * kTileStride + g] = ai0 + bi0;
+  tim[(2 * q + 1) * kTileStride + g] = ai1 + bi1;
+  __syncwarp();
+  // A_t -= V W, row tiles of 8 (two at a time): A operand V[r][i], B operand W[i][n]
+  const double w0r = tre[g * kTileStride + q], w0i = tim[g * kTileStride + q];
+  const double w1r = tre[g * kTileStride + 4 + q], w1i = tim[g * kTileStride + 4 + q];
+  __syncwarp();
+  for (int m0 = 0; m0 < R8; m0 += 16) {
+    const bool two = m0 + 8 < R8;
+    double* pr0 = Are + (size_t)(c0 + 2 * q) * S + k + m0 + g;
+    double* pi0 = Aim + (size_t)(c0 + 2 * q) * S + k + m0 + g;
+    double cr0 = pr0[0], cr1 = pr0[S], ci0 = pi0[0], ci1 = pi0[S];
+    double dr0 = 0.0, dr1 = 0.0, di0 = 0.0, di1 = 0.0;
+    if (two) {
+      dr0 = pr0[8];
+      dr1 = pr0[S + 8];
+      di0 = pi0[8];
+      di1 = pi0[S + 8];
+    }
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const double wr = h ? w1r : w0r, wi = h ? w1i : w0i;
+      const double vr = Vre[(4 * h + q) * S + m0 + g], vi = Vim[(4 * h + q) * S + m0 + g];
+      dmma(cr0, cr1, ineg(vr), wr);
+      dmma(ci0, ci1, ineg(vr), wi);
+      dmma(cr0, cr1, vi, wi);
+      dmma(ci0, ci1, ineg(vi), wr);
+      if (two) {
+        const double ur = Vre[(4 * h + q) * S + m0 + 8 + g], ui = Vim[(4 * h + q) * S + m0 + 8 + g];
+        dmma(dr0, dr1, ineg(ur), wr);
+        dmma(di0, di1, ineg(ur), wi);
+        dmma(dr0, dr1, ui, wi);
+        dmma(di0, di1, ineg(ui), wr);
+      }
+    }
+    pr0[0] = cr0;
+    pr0[S] = cr1;
+    pi0[0] = ci0;
+    pi0[S] = ci1;
+    if (two) {
+      pr0[8] = dr0;
+      pr0[S + 8] = dr1;
+      pi0[8] = di0;
+      pi0[S + 8] = di1;
+    }
+  }
+  __syncwarp();
+}
+
+// Factorises one [H | y] with the calling CTA (kQrdWarps warps).
+__device__ void qr_dmma_one(int N, int M, const double2* __restrict__ Hb, const double2* __restrict__ yb,
+                            const QrDst& out) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  QrdLayout L;
+  L.init(N, M);
+  double* Are = reinterpret_cast<double*>(smem_raw + L.off_are);
+  double* Aim = reinterpret_cast<double*>(smem_raw + L.off_aim);
+  double* Vre = reinterpret_cast<double*>(smem_raw + L.off_vre);
+  double* Vim = reinterpret_cast<double*>(smem_raw + L.off_vim);
+  double* Yre = reinterpret_cast<double*>(smem_raw + L.off_yre);
+  double* Yim = reinterpret_cast<double*>(smem_raw + L.off_yim);
+  double* red = reinterpret_cast<double*>(smem_raw + L.off_red);
+  double2* alpha = reinterpret_cast<double2*>(smem_raw + L.off_alpha);
+  double* tau = reinterpret_cast<double*>(smem_raw + L.off_tau);
+  int* sing = reinterpret_cast<int*>(smem_raw + L.off_sing);
+  const int tid = threadIdx.x, nthr = blockDim.x, lane = tid & 31, warp = tid >> 5;
+  double* tre = reinterpret_cast<double*>(smem_raw + L.off_tile) + (size_t)warp * 2 * 8 * kTileStride;
+  double* tim = tre + 8 * kTileStride;
+
+  const int plane = L.C8 * L.S;
+  for (int t = tid; t < plane; t += nthr) {
+    Are[t] = 0.0;
+    Aim[t] = 0.0;
+  }
+  if (tid == 0) *sing = 0;
+  __syncthreads();
+  for (int t = tid; t < N * M; t += nthr) {
+    const int r = t / M, c = t % M;
+    const double2 h = Hb[t];
+    Are[(size_t)c * L.S + r] = h.x;
+    Aim[(size_t)c * L.S + r] = h.y;
+  }
+  for (int r = tid; r < N; r += nthr) {
+    const double2 v = yb[r];
+    Are[(size_t)M * L.S + r] = v.x;
+    Aim[(size_t)M * L.S + r] = v.y;
+  }
+  __syncthreads();
+  for (int k = 0; k < M; k += 8) {
+    const int bw = min(8, M - k);
+    if (warp < kPanelWarps) qrd_panel(L, k, bw, Are, Aim, Vre, Vim, Yre, Yim, red, alpha, tau, sing, warp, lane);
+    __syncthreads();
+    const int ntiles = (M + 1 - (k + 8) + 7) / 8;  // columns k+8 .. M, 8 per task
+    for (int t = warp; t < ntiles; t += nthr / 32)
+      qrd_tile(L, k, k + 8 + 8 * t, Are, Aim, Vre, Vim, Yre, Yim, tre, tim, lane);
+    __syncthreads();
+  }
+  qr_writeout(M, [&](int c, int r) { return make_double2(Are[(size_t)c * L.S + r], Aim[(size_t)c * L.S + r]); },
+              alpha, tau, out);
+  if (out.singular && tid == 0) *out.singular = *sing;
+}
+
+__global__ void __launch_bounds__(kQrdWarps * 32, 1)
+    qr_dmma_kernel(int batch, int N, int M, const double* __restrict__ H, const double* __restrict__ y,
+                   QrOut out) {
+  const int b = blockIdx.x;
+  if (b >= batch) return;
+  const int n = 2 * M;
+  QrDst d;
+  d.R64 = out.R64 ? out.R64 + (size_t)b * tri_stride64(n) : nullptr;
+  d.yb64 = out.yb64 ? out.yb64 + (size_t)b * vec_stride64(n) : nullptr;
+  d.R32 = out.R32 ? out.R32 + (size_t)b * tri_stride32(n) : nullptr;
+  d.yb32 = out.yb32 ? out.yb32 + (size_t)b * vec_stride32(n) : nullptr;
+  d.Rdense = out.Rdense ? out.Rdense + (size_t)b * n * n : nullptr;
+  d.ybdense = out.ybdense ? out.ybdense + (size_t)b * n : nullptr;
+  d.singular = out.singular ? out.singular + b : nullptr;
+  qr_dmma_one(N, M, reinterpret_cast<const double2*>(H) + (size_t)b * N * M,
+              reinterpret_cast<const double2*>(y) + (size_t)b * N, d);
+}
+
+__global__ void __launch_bounds__(kQrdWarps * 32, 1)
+    qr_dmma_gather_kernel(int count, const int* __restrict__ ids, const MixedReq* __restrict__ reqs,
+                          const double* __restrict__ H, const double* __restrict__ y, QrOut out) {
+  if ((int)blockIdx.x >= count) return;
+  const int r = ids[blockIdx.x];
+  const MixedReq q = reqs[r];
+  QrDst d{out.R64 + q.r_off, out.yb64 + q.y_off, out.R32 + q.r_off, out.yb32 + q.y_off, nullptr, nullptr,
+          out.singular + r};
+  qr_dmma_one(q.n_rx, q.n_tx, reinterpret_cast<const double2*>(H + q.h_off),
+              reinterpret_cast<const double2*>(y + q.yin_off), d);
+}
+
+// The tensor-core form for n_tx >= kQrdMinTx when its shared memory fits.
+#ifndef MDX_QRD_MIN_TX
+#define MDX_QRD_MIN_TX 48
+#endif
+constexpr int kQrdMinTx = MDX_QRD_MIN_TX;
+size_t qrd_smem(int n_rx, int n_tx) {
+  QrdLayout L;
+  L.init(n_rx, n_tx);
+  return L.bytes;
+}
+bool use_qrd(int n_rx, int n_tx) { return n_tx >= kQrdMinTx && n_rx <= 128 && qrd_smem(n_rx, n_tx) <= 227 * 1024; }
 
 template <int LPC>
 __global__ void qr_kernel(int batch, int N, int M, const double* __restrict__ H,
@@ -221,6 +672,12 @@ size_t qr_smem(int n_rx, int n_tx) {
 cudaError_t launch_qr_gather(int count, int n_rx, int n_tx, const int* ids, const MixedReq* reqs,
                              const double* H, const double* y, QrOut out, cudaStream_t s) {
   if (count <= 0) return cudaSuccess;
+  if (use_qrd(n_rx, n_tx)) {
+    const size_t sm = qrd_smem(n_rx, n_tx);
+    cudaFuncSetAttribute(qr_dmma_gather_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    qr_dmma_gather_kernel<<<count, kQrdWarps * 32, sm, s>>>(count, ids, reqs, H, y, out);
+    return cudaGetLastError();
+  }
   const size_t smem = qr_smem(n_rx, n_tx);
   if (n_rx <= 16) {
     cudaFuncSetAttribute(qr_gather_kernel<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -236,6 +693,12 @@ cudaError_t launch_qr_gather(int count, int n_rx, int n_tx, const int* ids, cons
 cudaError_t launch_qr(int batch, int n_rx, int n_tx, const double* H, const double* y, QrOut out,
                       cudaStream_t s) {
   if (batch <= 0) return cudaSuccess;
+  if (use_qrd(n_rx, n_tx)) {
+    const size_t sm = qrd_smem(n_rx, n_tx);
+    cudaFuncSetAttribute(qr_dmma_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    qr_dmma_kernel<<<batch, kQrdWarps * 32, sm, s>>>(batch, n_rx, n_tx, H, y, out);
+    return cudaGetLastError();
+  }
   const size_t smem = qr_smem(n_rx, n_tx);
   if (n_rx <= 16) {
     // two 16-lane workers per warp

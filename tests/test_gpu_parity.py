@@ -70,7 +70,7 @@ def _compare(gpu, ref, gap_tol, max_mismatch=0.01, label=""):
 # ----------------------------------------------------------------------------------- QR
 
 
-@pytest.mark.parametrize("N,M,B", [(4, 4, 64), (16, 16, 256), (12, 8, 33), (40, 24, 9),
+@pytest.mark.parametrize("N,M,B", [(4, 4, 64), (16, 16, 256), (12, 8, 33), (40, 24, 9), (64, 48, 5), (70, 64, 7),
                                    (100, 100, 3), (1, 1, 5)])
 def test_qr_matches_oracle(env, N, M, B):
     torch, mdx, ctx = env
@@ -263,3 +263,17 @@ def test_empty_batch(env):
     out = mdx.detect("sd", ctx, mdx.make_params(4, 4, 4), z, torch.zeros((0, 4, 2), dtype=torch.float64,
                      device="cuda"), torch.zeros(0, dtype=torch.float64, device="cuda"))
     assert out[0].shape == (0, 4)
+
+
+@pytest.mark.parametrize("n", [4, 64])
+def test_rank_deficient_channel_is_singular(env, n):
+    """A zero column makes R_kk = 0: the vector is reported singular (metric
+    0, indices 0) by every detector, the others are detected normally; both QR
+    kernels (small and blocked) take this path."""
+    torch, mdx, ctx = env
+    w = wl.generate(77, 6, n, n, 4, 20.0)
+    w["H"][2, :, n // 2, :] = 0.0
+    for algo in ("sd", "kbest"):
+        gpu = _run(env, algo, w, 4, radius="paper", K=8, budget=20000)
+        assert gpu[2][2] == 3 and gpu[1][2] == 0.0 and (gpu[0][2] == 0).all()
+        assert (gpu[2][[0, 1, 3, 4, 5]] != 3).all()
