@@ -7,7 +7,7 @@ workloads) the network's features and tensor-core forward pass giving each
 vector's initial radius, the tree search (FP32 partial distances), FP64
 re-scoring of the final leaves, and the Gray-coded bit/symbol error count of
 the batch.  The default workload is 16x16 MIMO, 16-QAM, exact sphere
-decoding from the learned radius (the trained model in
+decoding from the learned radius and first leaf (the trained model in
 paper_2002_09561_gb300/models), 100,000 vectors per step with the SNR points
 4, 6, ..., 20 dB interleaved (vector b at point b mod 9); the same batch is
 also timed with the paper's radius r^2 = N M sigma^2 ("plain"), and both
@@ -321,7 +321,7 @@ def main():
         from paper_2002_09561_gb300 import train
 
         model_meta = train.load_model(ctx, n, qam)
-    flags = mdx.MDX_LEARNED_RADIUS if learned else 0
+    flags = (mdx.MDX_LEARNED_RADIUS | mdx.MDX_LEARNED_ORDER) if learned else 0
     params = mdx.make_params(n, n, qam, radius=w["radius"], K=max(w["K"], 1), depth=w["depth"], flags=flags)
     algo = w["detector"]
     out = mdx._outputs(B, n, dev, True)
@@ -428,7 +428,8 @@ def main():
     if rank == 0:
         cfg = config_of(args, w, world)
         if learned:
-            cfg["initial_radius"] = "learned (network of the models directory), doubled on an empty sphere"
+            cfg["initial_radius"] = ("learned (network of the models directory), capped by the distance of the "
+                                     "network's top-ranked leaf, doubled on an empty sphere")
             cfg["model"] = {k: model_meta.get(k) for k in ("traces", "snr_db", "epochs", "seed")} if model_meta else None
         line = {"metric": METRIC, "value": value, "unit": "vectors/s", "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,

@@ -87,9 +87,16 @@ enum {
   MDX_NO_RESCORE = 1 << 1,   /* skip the FP64 re-scoring of the final leaf candidates;
                                 metric_out is then the FP32 partial distance */
   MDX_LEARNED_RADIUS = 1 << 2, /* initial radius from the context's MLP (mdx_mlp_load) */
-  MDX_SEQUENTIAL_SEARCH = 1 << 3 /* detect_sd: one warp searches each vector's whole tree
-                                    (no subtree splitting between warps), so visited-node
-                                    counts are those of the sequential search */
+  MDX_SEQUENTIAL_SEARCH = 1 << 3, /* detect_sd: one warp searches each vector's whole tree
+                                     (no subtree splitting between warps), so visited-node
+                                     counts are those of the sequential search */
+  MDX_LEARNED_ORDER = 1 << 5      /* detect_sd: the MLP's per-row child ranking (mdx_mlp_load)
+                                     proposes the first leaf x^ (the top-ranked PAM index
+                                     of every real row, ties to the lower index); the
+                                     search treats x^ as its first descent, i.e. the
+                                     initial r^2 is capped at ||ybar - R x^||^2 (FP32)
+                                     x (1 + 2^-16).  Exactness is unchanged: x^ is a
+                                     lattice point, so the cap is at least d_ML. */
 };
 
 /* Largest sizes the kernels support. */
@@ -230,7 +237,8 @@ mdx_status mdx_count_errors(mdx_ctx* ctx, int batch, int n_tx, int qam, const ui
  * (cross-entropy, weight 0.2).  Weights are BF16, accumulation FP32, on the
  * tensor cores (tcgen05); FP32 master weights and Adam moments are kept on
  * the device.  detect_sd with MDX_LEARNED_RADIUS starts from the predicted
- * radius and doubles it on an empty sphere, so its answer is unchanged.
+ * radius and doubles it on an empty sphere, so its answer is unchanged;
+ * with MDX_LEARNED_ORDER the logits' top-ranked leaf caps that radius.
  * Parameter vector (FP32, this order): W1 [256][d_in], b1 [256],
  * W2 [256][256], b2 [256], W3 [d_out][256], b3 [d_out].
  * Models exist for square systems n_rx = n_tx <= 32. */

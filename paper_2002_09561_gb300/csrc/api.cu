@@ -183,12 +183,13 @@ mdx_status run_detect(int algo, mdx_ctx* c, const mdx_params* p, int batch, cons
   if (isnan(r0) || r0 == 0.0) return fail(c, MDX_EINVAL, "init_radius_sq must be > 0, < 0 or INFINITY");
   int radius_mode = isinf(r0) ? (r0 > 0 ? RADIUS_NONE : RADIUS_PAPER) : (r0 < 0 ? RADIUS_PAPER : RADIUS_VALUE);
   const bool learned = (p->flags & MDX_LEARNED_RADIUS) != 0;
-  if (learned) {
-    if (algo != ALGO_SD) return fail(c, MDX_EUNSUPPORTED, "MDX_LEARNED_RADIUS applies to detect_sd");
+  const bool order = (p->flags & MDX_LEARNED_ORDER) != 0;
+  if (learned || order) {
+    if (algo != ALGO_SD) return fail(c, MDX_EUNSUPPORTED, "MDX_LEARNED_RADIUS / MDX_LEARNED_ORDER apply to detect_sd");
     if (!c->mlp || mlp_ntx(c->mlp) != M || mlp_qam(c->mlp) != p->qam || N != M)
-      return fail(c, MDX_EUNSUPPORTED, "MDX_LEARNED_RADIUS needs a model for this %dx%d %d-QAM (mdx_mlp_init)", N, M,
-                  p->qam);
-    if (!nv) return fail(c, MDX_EINVAL, "noise_var needed for the learned radius");
+      return fail(c, MDX_EUNSUPPORTED, "the learned radius / order needs a model for this %dx%d %d-QAM (mdx_mlp_init)",
+                  N, M, p->qam);
+    if (!nv) return fail(c, MDX_EINVAL, "noise_var needed for the learned radius / order (network input)");
   }
   if (p->node_budget < 0) return fail(c, MDX_EINVAL, "node_budget < 0");
   if (algo != ALGO_SD) {
@@ -259,12 +260,14 @@ mdx_status run_detect(int algo, mdx_ctx* c, const mdx_params* p, int batch, cons
   e = launch_qr(batch, N, M, dH, dy, q, s);
   if (e != cudaSuccess) return cuda_fail(c, e, "QR launch");
 
-  if (learned) {
-    // radius proposed by the network: r^2 = sigma^2 exp(o_0)
+  if (learned || order) {
+    // radius proposed by the network (r^2 = sigma^2 exp(o_0)) and/or capped by
+    // the distance of its top-ranked leaf
     const int rows = round_up(batch, 128);
     e = mlp_features(c->mlp, batch, rows, c->R32, c->yb32, dnv, false, nullptr, s);
     if (e == cudaSuccess) e = mlp_forward(c->mlp, rows, false, s);
-    if (e == cudaSuccess) e = mlp_radius(c->mlp, batch, dnv, s);
+    if (e == cudaSuccess)
+      e = mlp_radius(c->mlp, batch, dnv, learned, order, radius_mode, r0, N, c->R32, c->yb32, s);
     if (e != cudaSuccess) return cuda_fail(c, e, "learned radius");
     radius_mode = RADIUS_PER_VECTOR;
   }
@@ -282,7 +285,7 @@ mdx_status run_detect(int algo, mdx_ctx* c, const mdx_params* p, int batch, cons
   a.yb64 = c->yb64;
   a.singular = c->singular;
   a.noise_var = dnv;
-  a.r2_vec = learned ? mlp_r2(c->mlp) : nullptr;
+  a.r2_vec = (learned || order) ? mlp_r2(c->mlp) : nullptr;
   a.radius_mode = radius_mode;
   a.radius_value = r0;
   a.K = p->K;

@@ -152,7 +152,10 @@ cudaError_t mlp_forward(MlpState* s, int rows, bool train, cudaStream_t st);
 cudaError_t mlp_backward(MlpState* s, int batch, int rows, const double* ml_metric, const double* nv,
                          const uint8_t* ml_sym, cudaStream_t st);
 cudaError_t mlp_adam(MlpState* s, float lr, cudaStream_t st);
-cudaError_t mlp_radius(MlpState* s, int batch, const double* nv, cudaStream_t st);
+// Per-vector initial r^2 into mlp_r2(): learned (sigma^2 exp(o_0)) or the base
+// radius (RADIUS_* mode), capped by the top-ranked leaf's distance if order.
+cudaError_t mlp_radius(MlpState* s, int batch, const double* nv, bool learned, bool order, int base_mode,
+                       double base_value, int n_rx, const float* R32, const float* yb32, cudaStream_t st);
 // accessors (the struct is private to mlp.cu)
 float* mlp_params(MlpState* s);
 float* mlp_grads(MlpState* s);

@@ -460,10 +460,58 @@ __global__ void pack_kernel(int rows, int cols, const float* __restrict__ w, __n
   }
 }
 
-__global__ void radius_kernel(int batch, int DO, const float* __restrict__ O, const double* __restrict__ nv,
-                              float* __restrict__ r2) {
+struct RadiusArgs {
+  int batch, DO, n, P, n_rx, n_tx;
+  bool learned, order;
+  int base_mode;
+  double base_value;
+  float alpha;
+  const float* O;
+  const double* nv;
+  const float* R32;
+  const float* yb32;
+  float* r2;
+};
+
+// Initial r^2 per vector: sigma^2 exp(o_0) (learned) or the given base
+// radius, capped (order) by the FP32 distance of the leaf x^ whose row r
+// takes the PAM index of largest logit o[1 + r P + k] (ties to the lower k),
+// scaled by 1 + 2^-16 so that x^ stays inside the sphere under the search's
+// own FP32 evaluation.
+__global__ void radius_kernel(RadiusArgs a) {
   const int v = blockIdx.x * blockDim.x + threadIdx.x;
-  if (v < batch) r2[v] = (float)(nv[v] * exp((double)O[(size_t)v * DO]));
+  if (v >= a.batch) return;
+  const float* o = a.O + (size_t)v * a.DO;
+  double r2;
+  if (a.learned) r2 = a.nv[v] * exp((double)o[0]);
+  else if (a.base_mode == RADIUS_PAPER) r2 = (double)a.n_rx * a.n_tx * a.nv[v];
+  else if (a.base_mode == RADIUS_VALUE) r2 = a.base_value;
+  else r2 = INFINITY;
+  if (a.order) {
+    const int n = a.n, P = a.P;
+    uint8_t xh[64];
+    for (int r = 0; r < n; ++r) {
+      int best = 0;
+      float bl = o[1 + r * P];
+      for (int k = 1; k < P; ++k)
+        if (o[1 + r * P + k] > bl) {
+          bl = o[1 + r * P + k];
+          best = k;
+        }
+      xh[r] = (uint8_t)best;
+    }
+    const float* R = a.R32 + (size_t)v * tri_stride32(n);
+    const float* yb = a.yb32 + (size_t)v * vec_stride32(n);
+    float d = 0.0f;
+    for (int r = 0; r < n; ++r) {
+      float e = yb[r];
+      for (int c = r; c < n; ++c) e = fmaf(-R[col_off(c) + r], (float)(2 * (int)xh[c] - (P - 1)) * a.alpha, e);
+      d = fmaf(e, e, d);
+    }
+    const double cap = (double)d * (1.0 + 1.0 / 65536.0);
+    if (cap > 0.0 && cap < r2) r2 = cap;
+  }
+  a.r2[v] = (float)r2;
 }
 
 int grid_for(long long total, int threads) {
@@ -670,8 +718,26 @@ cudaError_t mlp_adam(MlpState* s, float lr, cudaStream_t st) {
   return mlp_pack(s, st);
 }
 
-cudaError_t mlp_radius(MlpState* s, int batch, const double* nv, cudaStream_t st) {
-  radius_kernel<<<(batch + 255) / 256, 256, 0, st>>>(batch, s->DO, s->O, nv, s->r2);
+cudaError_t mlp_radius(MlpState* s, int batch, const double* nv, bool learned, bool order, int base_mode,
+                       double base_value, int n_rx, const float* R32, const float* yb32, cudaStream_t st) {
+  RadiusArgs a{};
+  a.batch = batch;
+  a.DO = s->DO;
+  a.n = s->n;
+  a.P = s->P;
+  a.n_rx = n_rx;
+  a.n_tx = s->n_tx;
+  a.learned = learned;
+  a.order = order;
+  a.base_mode = base_mode;
+  a.base_value = base_value;
+  a.alpha = (float)sqrt(3.0 / (2.0 * (s->qam - 1)));
+  a.O = s->O;
+  a.nv = nv;
+  a.R32 = R32;
+  a.yb32 = yb32;
+  a.r2 = s->r2;
+  radius_kernel<<<(batch + 127) / 128, 128, 0, st>>>(a);
   return cudaGetLastError();
 }
 

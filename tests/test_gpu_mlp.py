@@ -111,6 +111,37 @@ def test_learned_radius_keeps_the_ml_point(env):
     assert rel < 1e-12
 
 
+def test_learned_order_keeps_the_ml_point(env):
+    """The top-ranked leaf of the ordering head caps the radius; with or
+    without the learned radius, and from no radius at all, the decisions and
+    metrics are those of the plain search."""
+    torch, mdx, ctx = env
+    w = wl.generate(14, 2000, N_TX, N_TX, QAM, 10.0)
+    H, y, nv = _dev(torch, w)
+    plain = mdx.detect("sd", ctx, mdx.make_params(N_TX, N_TX, QAM, radius="paper"), H, y, nv)
+    for radius, f in (("paper", mdx.MDX_LEARNED_ORDER), ("paper", mdx.MDX_LEARNED_ORDER | mdx.MDX_LEARNED_RADIUS),
+                      (math.inf, mdx.MDX_LEARNED_ORDER)):
+        got = mdx.detect("sd", ctx, mdx.make_params(N_TX, N_TX, QAM, radius=radius, flags=f), H, y, nv)
+        torch.cuda.synchronize()
+        assert torch.equal(plain[0], got[0]), (radius, f)
+        assert ((plain[1] - got[1]).abs() / plain[1]).max().item() < 1e-12
+        # the capped radius always contains the ML point: no radius doubling from no radius
+        if radius == math.inf:
+            assert (got[2] != 1).all()
+
+
+def test_learned_order_needs_a_matching_model(env):
+    torch, mdx, ctx = env
+    w = wl.generate(15, 8, 8, 8, QAM, 10.0)
+    H, y, nv = _dev(torch, w)
+    with pytest.raises(mdx.MdxError):
+        mdx.detect("sd", ctx, mdx.make_params(8, 8, QAM, radius="paper", flags=mdx.MDX_LEARNED_ORDER), H, y, nv)
+    w = wl.generate(15, 8, N_TX, N_TX, QAM, 10.0)
+    H, y, nv = _dev(torch, w)
+    with pytest.raises(mdx.MdxError):
+        mdx.detect("kbest", ctx, mdx.make_params(N_TX, N_TX, QAM, K=16, flags=mdx.MDX_LEARNED_ORDER), H, y, nv)
+
+
 def test_training_reduces_nodes(env):
     """A short training on exact-SD traces (SNR uniform in 8..20 dB): the loss
     falls, and on held-out vectors the learned radius visits fewer nodes than
@@ -145,9 +176,16 @@ def test_training_reduces_nodes(env):
                                                     flags=seq | mdx.MDX_LEARNED_RADIUS), Ht, yt, nvt)
     torch.cuda.synchronize()
     assert torch.equal(plain[0], learned[0])
+    both = mdx.detect("sd", ctx, mdx.make_params(N_TX, N_TX, QAM, radius="paper",
+                                                 flags=seq | mdx.MDX_LEARNED_RADIUS | mdx.MDX_LEARNED_ORDER),
+                      Ht, yt, nvt)
+    torch.cuda.synchronize()
+    assert torch.equal(plain[0], both[0])
     n_plain = plain[3][:, 0].double().sum().item()
     n_learned = learned[3][:, 0].double().sum().item()
+    n_both = both[3][:, 0].double().sum().item()
     fallback = (learned[2] == 1).double().mean().item()
     print(f"GAIN nodes plain {n_plain:.0f} learned {n_learned:.0f} ratio {n_learned / n_plain:.3f} "
-          f"fallback {fallback:.3f}")
+          f"fallback {fallback:.3f}; learned radius + order {n_both:.0f}")
     assert n_learned < n_plain
+    assert n_both <= n_learned * 1.02
