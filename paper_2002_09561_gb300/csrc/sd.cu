@@ -178,8 +178,15 @@ __device__ __forceinline__ void lock_release(int* lk) {
   atomicExch(lk, 0);
 }
 
+// Blocks per SM the register allocation is made for: for n <= 32 the shared
+// memory allows up to eight 4-warp blocks; six (80 registers, no spills)
+// measured fastest for the learned-radius search, larger n allows fewer.
+#ifndef MDX_SD_MIN_BLOCKS_N32
+#define MDX_SD_MIN_BLOCKS_N32 6
+#endif
 template <int ROWS>
-__global__ void __launch_bounds__(kWarpsMax * 32) sd_kernel(SdArgs g) {
+__global__ void __launch_bounds__(kWarpsMax * 32, ROWS == 1 ? MDX_SD_MIN_BLOCKS_N32 : (ROWS == 2 ? 3 : 1))
+    sd_kernel(SdArgs g) {
   extern __shared__ __align__(16) unsigned char smem[];
   const SearchArgs& a = g.a;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -188,13 +195,11 @@ __global__ void __launch_bounds__(kWarpsMax * 32) sd_kernel(SdArgs g) {
   unsigned char* base = smem + warp * sd_warp_bytes(n);
   float* Rc = reinterpret_cast<float*>(base);  // column-packed R (FP32)
   float* zs = Rc + ts;                          // residual stack, level i at col_off(i)
-  float* lv_ped = zs + ts;                      // per level: parent partial distance
-  float* lv_c = lv_ped + n;                     // c_i
-  float* lv_u = lv_c + n;                       // u_i
-  float* lv_rinv = lv_u + n;                    // 1 / (2 alpha R_ii)
-  float* lv_rii = lv_rinv + n;                  // R_ii
-  int* lv_lohi = reinterpret_cast<int*>(lv_rii + n);
-  uint8_t* xs = reinterpret_cast<uint8_t*>(lv_lohi + n);  // current path
+  // per level: {parent partial distance, c_i, u_i, zig-zag cursors (lo + 1) | hi << 16
+  // as bits}, pushed and popped as one 16-byte access
+  float4* lv_st = reinterpret_cast<float4*>(zs + ts);
+  float2* lv_r = reinterpret_cast<float2*>(lv_st + n);     // per level: {R_ii, 1 / (2 alpha R_ii)}
+  uint8_t* xs = reinterpret_cast<uint8_t*>(lv_r + n);      // current path
   const float alpha = a.alpha;
   const float uoff = 0.5f * (float)(P - 1);
   int staged = -1;   // vector whose R is in shared memory
@@ -282,8 +287,7 @@ __global__ void __launch_bounds__(kWarpsMax * 32) sd_kernel(SdArgs g) {
       __syncwarp();
       for (int r = lane; r < n; r += 32) {
         const float rr = Rc[col_off(r) + r];
-        lv_rii[r] = rr;
-        lv_rinv[r] = 0.5f / (alpha * rr);
+        lv_r[r] = make_float2(rr, 0.5f / (alpha * rr));
       }
       staged = v;
     }
@@ -344,8 +348,20 @@ __global__ void __launch_bounds__(kWarpsMax * 32) sd_kernel(SdArgs g) {
     __syncwarp();
 
     // -------------------------------------------------- depth-first search
-    long long nodes = 0, peds = 0, flops = 0, since = 0;
+    // task totals (64-bit) and the 32-bit counts since the last fold; the
+    // algorithmic flops of a branched node at level l are 2 (n - 1 - l) + 4P,
+    // kept as a node count and a sum of levels
+    long long nodes = 0, peds = 0, flops = 0;
+    int n32 = 0, p32 = 0, lsum = 0, since = 0;
     int task_nodes = 0;
+    const int node_flops0 = 2 * (n - 1) + 4 * P;
+#define SD_FOLD()                                            \
+  do {                                                       \
+    nodes += n32;                                            \
+    peds += p32;                                             \
+    flops += (long long)n32 * node_flops0 - 2ll * lsum;      \
+    n32 = p32 = lsum = 0;                                    \
+  } while (0)
     // nodes of this vector already counted by finished or committed tasks
     long long committed = 0;
     if (a.budget > 0) {
@@ -358,12 +374,19 @@ __global__ void __launch_bounds__(kWarpsMax * 32) sd_kernel(SdArgs g) {
     int i = top;
     float ped_par = top_ped;
     float c = zs[col_off(top) + top];
-    float rii = lv_rii[top];
-    float u = fmaf(c, lv_rinv[top], uoff);
+    const float2 rtop = lv_r[top];
+    float rii = rtop.x;
+    float u = fmaf(c, rtop.y, uoff);
     int lo = min(max((int)ceilf(u - 0.5f), 0), P - 1);
     int hi = lo + 1;
-    nodes = 1;
-    flops = 2 * (n - 1 - top) + 4 * P;
+    n32 = 1;
+    lsum = top;
+    // budget left for this task's uncommitted nodes (n32 counts them)
+    int left32 = 0x7fffffff;
+    if (a.budget > 0) {
+      const long long left = a.budget - committed;
+      left32 = left < 0 ? 0 : (left > 0x7fffffffll ? 0x7fffffff : (int)left);
+    }
     while (!stop) {
       // next child of the node at level i in Schnorr-Euchner order
       int k = -1;
@@ -375,16 +398,17 @@ __global__ void __launch_bounds__(kWarpsMax * 32) sd_kernel(SdArgs g) {
       if (k >= 0) {
         const float d = fmaf(-rii, (float)(2 * k - (P - 1)) * alpha, c);
         ped = fmaf(d, d, ped_par);
-        ++peds;
+        ++p32;
       }
       if (k < 0 || !(ped < bnd)) {
         if (i == top) break;  // the task's node is exhausted
         ++i;                  // backtrack: pop level i
-        ped_par = lv_ped[i];
-        c = lv_c[i];
-        u = lv_u[i];
-        rii = lv_rii[i];
-        const int lh = lv_lohi[i];
+        const float4 st = lv_st[i];
+        ped_par = st.x;
+        c = st.y;
+        u = st.z;
+        rii = lv_r[i].x;
+        const int lh = __float_as_int(st.w);
         lo = (lh & 0xffff) - 1;
         hi = lh >> 16;
         continue;
@@ -433,17 +457,14 @@ __global__ void __launch_bounds__(kWarpsMax * 32) sd_kernel(SdArgs g) {
         }
         continue;
       }
-      if (a.budget > 0 && committed + nodes >= a.budget) {
+      if (n32 >= left32) {
         if (lane == 0) atomicExch(&vs->budget_hit, 1);
         break;
       }
       // descend into child k: push level i, update the residuals of the rows below
       const float av = (float)(2 * k - (P - 1)) * alpha;
       if (lane == 0) {
-        lv_ped[i] = ped_par;
-        lv_c[i] = c;
-        lv_u[i] = u;
-        lv_lohi[i] = (lo + 1) | (hi << 16);
+        lv_st[i] = make_float4(ped_par, c, u, __int_as_float((lo + 1) | (hi << 16)));
         xs[i] = (uint8_t)k;
       }
       const float* zin = zs + col_off(i);
@@ -463,17 +484,19 @@ __global__ void __launch_bounds__(kWarpsMax * 32) sd_kernel(SdArgs g) {
       c = __shfl_sync(0xffffffffu, cnext, i & 31);
       __syncwarp();
       ped_par = ped;
-      rii = lv_rii[i];
-      u = fmaf(c, lv_rinv[i], uoff);
+      const float2 rl = lv_r[i];
+      rii = rl.x;
+      u = fmaf(c, rl.y, uoff);
       lo = min(max((int)ceilf(u - 0.5f), 0), P - 1);
       hi = lo + 1;
-      ++nodes;
+      ++n32;
+      lsum += i;
       ++task_nodes;
-      flops += 2 * (n - 1 - i) + 4 * P;
 
       // periodic: radius refresh, budget, and splitting while warps are idle
       if (++since >= kSplitEvery) {
         since = 0;
+        SD_FOLD();
         const float gr2 = __uint_as_float(
             __shfl_sync(0xffffffffu, lane == 0 ? *(volatile unsigned int*)&vs->r2bits : 0u, 0));
         if (gr2 < r2) {
@@ -496,6 +519,8 @@ __global__ void __launch_bounds__(kWarpsMax * 32) sd_kernel(SdArgs g) {
             stop = true;
             break;
           }
+          const long long left = a.budget - committed;
+          left32 = left > 0x7fffffffll ? 0x7fffffff : (int)left;
         }
         // split only while more warps wait than tasks are queued for them
         int want = 0;
@@ -525,13 +550,14 @@ __global__ void __launch_bounds__(kWarpsMax * 32) sd_kernel(SdArgs g) {
               lped = ped_par;
               lrii = rii;
             } else {
-              const int lh = lv_lohi[l];
+              const float4 st = lv_st[l];
+              const int lh = __float_as_int(st.w);
               llo = (lh & 0xffff) - 1;
               lhi = lh >> 16;
-              lc = lv_c[l];
-              lu = lv_u[l];
-              lped = lv_ped[l];
-              lrii = lv_rii[l];
+              lc = st.y;
+              lu = st.z;
+              lped = st.x;
+              lrii = lv_r[l].x;
             }
             if (llo < 0 && lhi >= P) continue;
             // children inside the sphere, in SE order: counted first, then written
@@ -599,7 +625,7 @@ __global__ void __launch_bounds__(kWarpsMax * 32) sd_kernel(SdArgs g) {
               lo = -1;
               hi = P;
             } else if (lane == 0) {
-              lv_lohi[l] = 0 | (P << 16);
+              reinterpret_cast<int*>(&lv_st[l])[3] = P << 16;
             }
             __syncwarp();
           }
@@ -612,6 +638,7 @@ __global__ void __launch_bounds__(kWarpsMax * 32) sd_kernel(SdArgs g) {
     }
 
     // ------------------------------------------------ task done: account
+    SD_FOLD();
     if (lane == 0) {
       atomicAdd(&vs->nodes, (unsigned long long)nodes);
       atomicAdd(&vs->peds, (unsigned long long)peds);
@@ -716,6 +743,8 @@ __global__ void __launch_bounds__(kWarpsMax * 32) sd_kernel(SdArgs g) {
     if (lane == 0) atomicSub(&g.sh->outstanding, 1);
   }
 }
+
+#undef SD_FOLD
 
 template <int ROWS>
 cudaError_t launch_rows(const SdArgs& g, int num_sms, cudaStream_t s) {
