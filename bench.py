@@ -73,6 +73,7 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="target CPU-baseline duration")
+    ap.add_argument("--no-autotune", action="store_true", help="uneven batch: keep the default tuning")
     return ap.parse_args()
 
 
@@ -457,7 +458,7 @@ def main_mixed(args, w, rank, world, local, dev, dist, torch, mdx):
     ctx = mdx.Context(local, max_batch=B, max_n_rx=max(w["antennas"]), max_n_tx=max(w["antennas"]))
     stream = torch.cuda.Stream(dev)
     with torch.cuda.stream(stream):
-        tune = mdx.autotune_mixed(ctx, reqs, H, y, nv, stream=stream)
+        tune = None if args.no_autotune else mdx.autotune_mixed(ctx, reqs, H, y, nv, stream=stream)
         out = mdx.detect_mixed(ctx, reqs, H, y, nv, stream=stream)
     flags = mdx.MDX_GRAPH
     for _ in range(args.warmup):
