@@ -28,7 +28,7 @@ _SO = os.path.join(_HERE, "liboracle.so")
 _lock = threading.Lock()
 _lib = None
 
-ALGO = {"sd": 0, "kbest": 1, "hybrid": 2, "ml": 3}
+ALGO = {"sd": 0, "kbest": 1, "hybrid": 2, "ml": 3, "sd_complex": 4, "kbest_complex": 5}
 ORDER = {"se": 0, "natural": 1, "reversed": 2, "random": 3}
 V_OK, V_EMPTY_RETRIED, V_BUDGET_EXCEEDED = 0, 1, 2
 
@@ -64,6 +64,10 @@ def lib():
             L.orc_sd.restype = i
             L.orc_kbest.argtypes = [i, i, vp, vp, vp, i, d, vp, vp, vp, vp]
             L.orc_kbest.restype = i
+            L.orc_sd_complex.argtypes = [i, i, vp, vp, vp, d, ll, i, vp, vp, vp, vp]
+            L.orc_sd_complex.restype = i
+            L.orc_kbest_complex.argtypes = [i, i, vp, vp, vp, i, d, vp, vp, vp, vp]
+            L.orc_kbest_complex.restype = i
             L.orc_hybrid.argtypes = [i, i, vp, vp, vp, i, i, d, i, ctypes.c_uint64, vp, vp, vp, vp]
             L.orc_hybrid.restype = i
             L.orc_detect_batch.argtypes = [i, i, i, i, i, vp, vp, vp, d, i, i, ll, i, i, vp, vp, vp,
@@ -168,6 +172,38 @@ def kbest(R, ybar, qam, K, r2=np.inf):
     st = Stats()
     rc = lib().orc_kbest(n, len(lev), _p(R), _p(ybar), _p(lev), int(K), float(r2), _p(k), _p(d1),
                          _p(gap), ctypes.byref(st))
+    if rc < 0:
+        raise ValueError("bad arguments")
+    return {"k": k, "d1": d1[0], "gap": gap[0], "status": rc, **st.as_dict()}
+
+
+def sd_complex(R, ybar, qam, r2=np.inf, budget=0, two_best=False):
+    """Complex-tree SD (orc_sd_complex): one level per complex antenna."""
+    R, ybar = _f64(R), _f64(ybar)
+    n = R.shape[0]
+    lev = pam_levels(qam)
+    k = np.zeros(n, dtype=np.int32)
+    d1 = np.zeros(1)
+    d2 = np.zeros(1)
+    st = Stats()
+    rc = lib().orc_sd_complex(n, len(lev), _p(R), _p(ybar), _p(lev), float(r2), int(budget), int(two_best), _p(k),
+                              _p(d1), _p(d2), ctypes.byref(st))
+    if rc < 0:
+        raise ValueError("bad arguments")
+    return {"k": k, "d1": d1[0], "d2": d2[0], "status": rc, **st.as_dict()}
+
+
+def kbest_complex(R, ybar, qam, K, r2=np.inf):
+    """Complex-tree K-best (orc_kbest_complex)."""
+    R, ybar = _f64(R), _f64(ybar)
+    n = R.shape[0]
+    lev = pam_levels(qam)
+    k = np.zeros(n, dtype=np.int32)
+    d1 = np.zeros(1)
+    gap = np.zeros(1)
+    st = Stats()
+    rc = lib().orc_kbest_complex(n, len(lev), _p(R), _p(ybar), _p(lev), int(K), float(r2), _p(k), _p(d1),
+                                 _p(gap), ctypes.byref(st))
     if rc < 0:
         raise ValueError("bad arguments")
     return {"k": k, "d1": d1[0], "gap": gap[0], "status": rc, **st.as_dict()}

@@ -18,6 +18,7 @@
 #endif
 
 #define ORC_MAX_P 16
+#define ORC_MAX_Q 64 /* complex-tree children (64-QAM) */
 
 int orc_max_threads(void) {
 #ifdef _OPENMP
@@ -584,6 +585,196 @@ int orc_hybrid(int n, int P, const double* R, const double* ybar, const double* 
 }
 
 /* ------------------------------------------------------------------------- */
+/* Complex tree: level j = real rows 2j+1 (Im) and 2j (Re) taken together.   */
+/* ------------------------------------------------------------------------- */
+
+/* Partial distances of the Q children of the node whose rows above 2j+1 are
+ * fixed in x: row 2j+1 takes k_im, then row 2j (whose residual now includes
+ * x[2j+1]) takes k_re.  Leaves x[2j], x[2j+1] modified. */
+static void complex_children(int n, int P, const double* R, const double* yb, const double* lev, int* x, int j,
+                             double ped_parent, double* ped) {
+  const int r1 = 2 * j + 1, r0 = 2 * j;
+  const double c1 = row_residual(n, R, yb, lev, x, r1);
+  for (int q = 0; q < P * P; ++q) {
+    const int k_re = q / P, k_im = q % P;
+    const double d1v = c1 - R[r1 * n + r1] * lev[k_im];
+    x[r1] = k_im;
+    const double c0 = row_residual(n, R, yb, lev, x, r0);
+    const double d0v = c0 - R[r0 * n + r0] * lev[k_re];
+    ped[q] = ped_parent + d1v * d1v + d0v * d0v;
+  }
+}
+
+static void sdc_visit(dfs_ctx* s, int j, double ped_parent) {
+  if (s->budget > 0 && s->st->nodes >= s->budget) {
+    s->budget_hit = 1;
+    return;
+  }
+  s->st->nodes++;
+  const int P = s->P, Q = P * P;
+  double ped[ORC_MAX_Q];
+  int ord[ORC_MAX_Q];
+  complex_children(s->n, P, s->R, s->yb, s->lev, s->x, j, ped_parent, ped);
+  s->st->peds += Q;
+  /* increasing partial distance, ties to the lower q (stable insertion sort) */
+  for (int q = 0; q < Q; ++q) {
+    int b = q - 1;
+    while (b >= 0 && ped[ord[b]] > ped[q]) {
+      ord[b + 1] = ord[b];
+      --b;
+    }
+    ord[b + 1] = q;
+  }
+  for (int t = 0; t < Q; ++t) {
+    const int q = ord[t];
+    const double bound = s->two_best ? s->r2b : s->r2;
+    if (!(ped[q] < bound)) continue;
+    s->x[2 * j + 1] = q % P;
+    s->x[2 * j] = q / P;
+    if (j == 0) sd_leaf(s, ped[q]);
+    else sdc_visit(s, j - 1, ped[q]);
+    if (s->budget_hit) return;
+  }
+}
+
+int orc_sd_complex(int n, int P, const double* R, const double* ybar, const double* levels, double r2_init,
+                   long long budget, int two_best, int* k_out, double* d1, double* d2, orc_stats* st) {
+  orc_stats local;
+  if (!st) st = &local;
+  memset(st, 0, sizeof(*st));
+  if (!(r2_init > 0.0) || (n & 1) || P * P > ORC_MAX_Q) return -1;
+  int* x = (int*)calloc(n, sizeof(int));
+  int* best = (int*)calloc(n, sizeof(int));
+  int status = ORC_V_OK;
+  double r2 = r2_init;
+  dfs_ctx s;
+  for (;;) {
+    memset(&s, 0, sizeof(s));
+    s.n = n;
+    s.P = P;
+    s.R = R;
+    s.yb = ybar;
+    s.lev = levels;
+    s.r2 = r2;
+    s.r2b = r2;
+    s.two_best = two_best;
+    s.budget = budget;
+    s.x = x;
+    s.best = best;
+    s.st = st;
+    sdc_visit(&s, n / 2 - 1, 0.0);
+    if (s.found || s.budget_hit) break;
+    r2 *= 4.0; /* empty sphere: double the radius and search again */
+    st->restarts++;
+    status = ORC_V_EMPTY_RETRIED;
+    if (!(r2 < 1e300)) break;
+  }
+  if (s.budget_hit) status = ORC_V_BUDGET_EXCEEDED;
+  if (s.found) {
+    memcpy(k_out, best, sizeof(int) * n);
+    if (d1) *d1 = s.r2;
+    if (d2) *d2 = two_best ? s.r2b : INFINITY;
+  } else {
+    memset(k_out, 0, sizeof(int) * n);
+    if (d1) *d1 = INFINITY;
+    if (d2) *d2 = INFINITY;
+  }
+  free(x);
+  free(best);
+  return status;
+}
+
+/* K-best over complex levels; kb_cand.k holds the child's q. */
+static int kbest_run_complex(int n, int P, const double* R, const double* yb, const double* lev, int K,
+                             double r2, int* cur, int* nxt, double* ped_cur, double* ped_nxt, kb_cand* cand,
+                             int* out_path, double* out_ped, double* min_gap, orc_stats* st) {
+  const int Q = P * P;
+  int S = 1;
+  double ped[ORC_MAX_Q];
+  memset(cur, 0, sizeof(int) * n);
+  ped_cur[0] = 0.0;
+  for (int j = n / 2 - 1; j >= 0; --j) {
+    int C = 0;
+    for (int p = 0; p < S; ++p) {
+      st->nodes++;
+      complex_children(n, P, R, yb, lev, cur + (size_t)p * n, j, ped_cur[p], ped);
+      st->peds += Q;
+      for (int q = 0; q < Q; ++q) {
+        if (ped[q] < r2) {
+          cand[C].ped = ped[q];
+          cand[C].parent = p;
+          cand[C].k = q;
+          ++C;
+        }
+      }
+    }
+    if (C == 0) return 0;
+    qsort(cand, C, sizeof(kb_cand), kb_cmp);
+    const int keep = C < K ? C : K;
+    if (C > K && min_gap) {
+      const double g = rel_gap(cand[K - 1].ped, cand[K].ped);
+      if (g < *min_gap) *min_gap = g;
+    }
+    for (int t = 0; t < keep; ++t) {
+      memcpy(nxt + (size_t)t * n, cur + (size_t)cand[t].parent * n, sizeof(int) * n);
+      nxt[(size_t)t * n + 2 * j + 1] = cand[t].k % P;
+      nxt[(size_t)t * n + 2 * j] = cand[t].k / P;
+      ped_nxt[t] = cand[t].ped;
+    }
+    int* ti = cur;
+    cur = nxt;
+    nxt = ti;
+    double* td = ped_cur;
+    ped_cur = ped_nxt;
+    ped_nxt = td;
+    S = keep;
+  }
+  if (S > 1 && min_gap) {
+    const double g = rel_gap(ped_cur[0], ped_cur[1]);
+    if (g < *min_gap) *min_gap = g;
+  }
+  memcpy(out_path, cur, sizeof(int) * n);
+  *out_ped = ped_cur[0];
+  return S;
+}
+
+int orc_kbest_complex(int n, int P, const double* R, const double* ybar, const double* levels, int K,
+                      double r2, int* k_out, double* d1, double* min_gap, orc_stats* st) {
+  orc_stats local;
+  if (!st) st = &local;
+  memset(st, 0, sizeof(*st));
+  if (K < 1 || !(r2 > 0.0) || (n & 1) || P * P > ORC_MAX_Q) return -1;
+  const size_t cap = (size_t)K * P * P;
+  int* cur = (int*)calloc(cap * n, sizeof(int));
+  int* nxt = (int*)calloc(cap * n, sizeof(int));
+  double* pc = (double*)calloc(cap, sizeof(double));
+  double* pn = (double*)calloc(cap, sizeof(double));
+  kb_cand* cand = (kb_cand*)malloc(sizeof(kb_cand) * cap);
+  double gap = 1.0, ped = INFINITY;
+  int status = ORC_V_OK;
+  for (;;) {
+    gap = 1.0;
+    const int S = kbest_run_complex(n, P, R, ybar, levels, K, r2, cur, nxt, pc, pn, cand, k_out, &ped, &gap, st);
+    if (S > 0) break;
+    r2 *= 4.0; /* empty sphere: double the radius */
+    st->restarts++;
+    status = ORC_V_EMPTY_RETRIED;
+    if (!(r2 < 1e300)) {
+      memset(k_out, 0, sizeof(int) * n);
+      break;
+    }
+  }
+  if (d1) *d1 = ped;
+  if (min_gap) *min_gap = gap;
+  free(cur);
+  free(nxt);
+  free(pc);
+  free(pn);
+  free(cand);
+  return status;
+}
+
+/* ------------------------------------------------------------------------- */
 /* Batch drivers                                                             */
 /* ------------------------------------------------------------------------- */
 
@@ -618,7 +809,8 @@ int orc_detect_batch(int algo, int B, int N, int M, int qam, const double* H, co
   double lev[ORC_MAX_P];
   const int P = orc_pam_levels(qam, lev);
   if (P < 0 || B < 0 || N < M || M < 1) return -1;
-  if ((algo == ORC_KBEST || algo == ORC_HYBRID) && K < 1) return -1;
+  if ((algo == ORC_KBEST || algo == ORC_HYBRID || algo == ORC_KBEST_COMPLEX) && K < 1) return -1;
+  if (algo < ORC_SD || algo > ORC_KBEST_COMPLEX) return -1;
   const int n = 2 * M, m = 2 * N;
 #ifdef _OPENMP
   if (nthreads > 0) omp_set_num_threads(nthreads);
@@ -652,6 +844,15 @@ int orc_detect_batch(int algo, int B, int N, int M, int qam, const double* H, co
           orc_sd(n, P, R, yb, lev, r2, budget, order, (uint64_t)b, 1, k2, NULL, &d2, &st2);
           g = rel_gap(d1, d2);
         }
+      } else if (algo == ORC_SD_COMPLEX) {
+        vs = orc_sd_complex(n, P, R, yb, lev, r2, budget, 0, k, &d1, NULL, &st);
+        if (want_gap) {
+          orc_stats st2;
+          orc_sd_complex(n, P, R, yb, lev, r2, budget, 1, k2, NULL, &d2, &st2);
+          g = rel_gap(d1, d2);
+        }
+      } else if (algo == ORC_KBEST_COMPLEX) {
+        vs = orc_kbest_complex(n, P, R, yb, lev, K, r2, k, &d1, &g, &st);
       } else if (algo == ORC_KBEST) {
         vs = orc_kbest(n, P, R, yb, lev, K, r2, k, &d1, &g, &st);
       } else if (algo == ORC_HYBRID) {

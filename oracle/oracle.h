@@ -38,7 +38,7 @@
 extern "C" {
 #endif
 
-enum { ORC_SD = 0, ORC_KBEST = 1, ORC_HYBRID = 2, ORC_ML = 3 };
+enum { ORC_SD = 0, ORC_KBEST = 1, ORC_HYBRID = 2, ORC_ML = 3, ORC_SD_COMPLEX = 4, ORC_KBEST_COMPLEX = 5 };
 /* child visiting order of the depth-first part (SD and the hybrid master) */
 enum { ORC_ORDER_SE = 0, ORC_ORDER_NATURAL = 1, ORC_ORDER_REVERSED = 2, ORC_ORDER_RANDOM = 3 };
 /* per-vector outcome */
@@ -97,6 +97,21 @@ int orc_kbest(int n, int P, const double* R, const double* ybar, const double* l
 int orc_hybrid(int n, int P, const double* R, const double* ybar, const double* levels, int K,
                int d, double r2_init, int order, uint64_t seed, int* k_out, double* d1,
                double* min_gap, orc_stats* st);
+
+/* Complex-tree searches: one tree level per complex antenna with the Q = P^2
+ * symbols of the QAM alphabet as children (the tree of Sec. III-B, which the
+ * paper's node counts refer to).  On the interleaved real (R, ybar) above,
+ * complex level j is the pair of real rows 2j+1 (imaginary part) and 2j
+ * (real part): child q = k_re * P + k_im has the partial distance of the
+ * real path that fixes row 2j+1 to k_im and then row 2j to k_re (Eq. inc
+ * applied twice), so a complex node is the real tree grouped two levels at
+ * a time.  Children are visited / selected in increasing partial distance,
+ * ties to the lower q (K-best: key (distance, parent rank, q)).  n = 2M must
+ * be even; nodes count complex-level branchings, peds count children. */
+int orc_sd_complex(int n, int P, const double* R, const double* ybar, const double* levels, double r2_init,
+                   long long budget, int two_best, int* k_out, double* d1, double* d2, orc_stats* st);
+int orc_kbest_complex(int n, int P, const double* R, const double* ybar, const double* levels, int K,
+                      double r2, int* k_out, double* d1, double* min_gap, orc_stats* st);
 
 /* Batch driver over B independent received vectors (complex H [B][N][M][2],
  * y [B][N][2], noise_var [B]).  radius_mode: r2 >= 0 uses that value,

@@ -354,3 +354,70 @@ def test_ml_ser_curves_match_paper_shape():
     w = wl.generate(77, 500, 10, 10, 16, 12.0 - 10.0)
     r = oracle.detect_batch("sd", w["H"], w["y"], w["noise_var"], 16, radius="paper")
     assert np.mean(r["sym"] != w["sym"]) > 4 * dict(g["curves"]["10"])[12]
+
+
+# --------------------------------------------------------------------- complex tree
+
+
+def _complex_sym(k, P):
+    k = np.asarray(k)
+    return k[0::2] * P + k[1::2]
+
+
+@pytest.mark.parametrize("M,qam,snr", [(4, 4, 6.0), (2, 16, 8.0), (3, 4, 2.0), (2, 64, 14.0), (3, 16, 10.0)])
+def test_complex_sd_equals_brute_force(M, qam, snr):
+    """One level per complex antenna (Q children) finds the ML point of Eq. 2."""
+    P = wl.pam_size(qam)
+    for seed in range(6):
+        w, Hr, yr, f = _system(700 + seed, M, M, qam, snr)
+        ml = oracle.ml_bruteforce(w["H"][0], w["y"][0], qam)
+        r = oracle.sd_complex(f["R"], f["ybar"], qam)
+        if (ml["d2"] - ml["d1"]) / ml["d2"] > 1e-9:
+            np.testing.assert_array_equal(_complex_sym(r["k"], P), ml["sym"])
+        assert r["d1"] == pytest.approx(oracle.metric(f["R"], f["ybar"], qam, r["k"]), rel=1e-12)
+
+
+def test_complex_kbest_counts_are_the_papers():
+    """The complex-tree K-best visits exactly the paper's node counts for
+    16x16 64-QAM (151 at K = 10, 481 at K = 32), and evaluates 64 children
+    per visited node."""
+    g = json.load(open(os.path.join(GOLDEN, "kbest_visited_nodes.json")))["complex_tree"]
+    w, Hr, yr, f = _system(711, g["M"], g["M"], g["qam"], 20.0)
+    for K, visited in g["points"]:
+        r = oracle.kbest_complex(f["R"], f["ybar"], g["qam"], K)
+        assert r["nodes"] == visited
+        assert r["peds"] == visited * g["qam"]
+
+
+@pytest.mark.parametrize("M,qam,K", [(2, 16, 16), (3, 4, 16), (2, 64, 64)])
+def test_complex_kbest_full_tree_is_ml(M, qam, K):
+    """With K >= Q^(M-1) nothing is dropped before the last level: K-best is ML."""
+    P = wl.pam_size(qam)
+    for seed in range(5):
+        w, Hr, yr, f = _system(720 + seed, M, M, qam, 6.0)
+        ml = oracle.ml_bruteforce(w["H"][0], w["y"][0], qam)
+        r = oracle.kbest_complex(f["R"], f["ybar"], qam, K)
+        if (ml["d2"] - ml["d1"]) / ml["d2"] > 1e-9:
+            np.testing.assert_array_equal(_complex_sym(r["k"], P), ml["sym"])
+
+
+def test_complex_kbest_one_is_babai():
+    """K = 1 keeps the best child of each complex level; the two real rows of a
+    level decouple (R[2j][2j+1] = 0), so this is the real Babai point."""
+    for seed in range(10):
+        w, Hr, yr, f = _system(730 + seed, 8, 6, 16, 10.0)
+        r = oracle.kbest_complex(f["R"], f["ybar"], 16, 1)
+        np.testing.assert_array_equal(r["k"], _babai(f["R"], f["ybar"], 16))
+
+
+def test_complex_sd_agrees_with_real_sd():
+    """Both trees hold the same leaves, so both exact searches return the ML
+    point; the complex tree branches half as often."""
+    P = 4
+    for seed in range(8):
+        w, Hr, yr, f = _system(740 + seed, 8, 8, 16, 12.0)
+        rc = oracle.sd_complex(f["R"], f["ybar"], 16, two_best=True)
+        rr = oracle.sd(f["R"], f["ybar"], 16)
+        if (rc["d2"] - rc["d1"]) / rc["d2"] > 1e-9:
+            np.testing.assert_array_equal(rc["k"], rr["k"])
+        assert rc["d1"] == pytest.approx(rr["d1"], rel=1e-12)
