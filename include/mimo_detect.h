@@ -90,6 +90,15 @@ enum {
   MDX_SEQUENTIAL_SEARCH = 1 << 3, /* detect_sd: one warp searches each vector's whole tree
                                      (no subtree splitting between warps), so visited-node
                                      counts are those of the sequential search */
+  MDX_COMPLEX_TREE = 1 << 6,      /* detect_sd / detect_kbest: search the complex tree of
+                                     Sec. III-B (one level per complex antenna, the QAM
+                                     alphabet's qam points as children; on the interleaved
+                                     real R a level is the real rows 2j+1 and 2j, i.e. the
+                                     real tree grouped two levels at a time).  Children in
+                                     increasing partial distance, ties to the lower index
+                                     q; K-best keeps K per complex level.  stats count
+                                     complex-level nodes and qam children per node.
+                                     detect_sd runs it one warp per vector (no splitting). */
   MDX_LEARNED_ORDER = 1 << 5      /* detect_sd: the MLP's per-row child ranking (mdx_mlp_load)
                                      proposes the first leaf x^ (the top-ranked PAM index
                                      of every real row, ties to the lower index); the
@@ -182,7 +191,8 @@ mdx_status detect_hybrid(mdx_ctx* ctx, const mdx_params* p, int batch, const dou
  * array; every other pointer is device memory.  The QR runs per (n_rx, n_tx)
  * class; the search is one persistent kernel whose warps take requests from a
  * global counter, heaviest classes first: exact SD (Algorithm 1, one warp per
- * request, node_budget honoured) or K-best (Sec. VI, tournament selection),
+ * request, node_budget honoured; real or complex tree) or K-best (Sec. VI,
+ * tournament selection),
  * with R and the search state in a per-warp shared-memory slice, or in a
  * per-warp global-memory slot for requests too large for the slice.  The slice
  * size and warps per CTA come from the context's tuning table
@@ -192,7 +202,7 @@ mdx_status detect_hybrid(mdx_ctx* ctx, const mdx_params* p, int batch, const dou
  * change between such calls).
  * Limits: n_tx <= MDX_MAX_TX, K <= MDX_MAX_K, nreq <= the context's max_batch
  * and the sum of per-request QR outputs within the workspace. */
-enum { MDX_ALGO_SD = 0, MDX_ALGO_KBEST = 1 };
+enum { MDX_ALGO_SD = 0, MDX_ALGO_KBEST = 1, MDX_ALGO_SD_COMPLEX = 2 /* complex-tree SD, as MDX_COMPLEX_TREE */ };
 enum { MDX_GRAPH = 1 << 4 };
 typedef struct {
   int n_rx, n_tx, qam;

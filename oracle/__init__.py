@@ -263,7 +263,7 @@ def count_errors(sym_hat, sym_true, qam):
 
 def detect_mixed(reqs, H, y, noise_var, want_gap=True, nthreads=0):
     """An uneven batch (request table with the fields of mdx_request: n_rx,
-    n_tx, qam, algo (0 = exact SD, 1 = K-best), K, init_radius_sq (negative =
+    n_tx, qam, algo (0 = exact SD, 1 = K-best, 2 = complex-tree SD), K, init_radius_sq (negative =
     the paper's N M sigma^2), node_budget and the offsets of each request's H,
     y and symbols in the flat arrays) detected request by request with
     detect_batch, grouping requests of equal parameters.  Returns flat symbols
@@ -278,15 +278,16 @@ def detect_mixed(reqs, H, y, noise_var, want_gap=True, nthreads=0):
     for i, r in enumerate(reqs):
         key = (int(r["n_rx"]), int(r["n_tx"]), int(r["qam"]), int(r["algo"]),
                int(r["K"]) if int(r["algo"]) == 1 else 0, float(r["init_radius_sq"]),
-               int(r["node_budget"]) if int(r["algo"]) == 0 else 0)
+               int(r["node_budget"]) if int(r["algo"]) != 1 else 0)
         groups.setdefault(key, []).append(i)
     for (N, M, qam, algo, K, r0, budget), idx in groups.items():
         Hb = np.stack([H[int(reqs[i]["h_offset"]):int(reqs[i]["h_offset"]) + 2 * N * M] for i in idx])
         yb = np.stack([y[int(reqs[i]["y_offset"]):int(reqs[i]["y_offset"]) + 2 * N] for i in idx])
         radius = "paper" if r0 < 0 else r0
-        out = detect_batch("sd" if algo == 0 else "kbest", Hb.reshape(len(idx), N, M, 2), yb.reshape(len(idx), N, 2),
+        name = {0: "sd", 1: "kbest", 2: "sd_complex"}[algo]
+        out = detect_batch(name, Hb.reshape(len(idx), N, M, 2), yb.reshape(len(idx), N, 2),
                            nv[idx], qam, radius=radius, K=max(K, 1), budget=budget,
-                           want_gap=want_gap and algo == 0, nthreads=nthreads)
+                           want_gap=want_gap and algo != 1, nthreads=nthreads)
         for j, i in enumerate(idx):
             s0 = int(reqs[i]["sym_offset"])
             sym[s0:s0 + M] = out["sym"][j]

@@ -195,7 +195,9 @@ mdx_status run_detect(int algo, mdx_ctx* c, const mdx_params* p, int batch, cons
   if (algo != ALGO_SD) {
     if (p->K < 1 || p->K > MDX_MAX_K) return fail(c, MDX_EINVAL, "K %d not in 1..%d", p->K, MDX_MAX_K);
   }
-  int keys_cap = pow2ceil(algo == ALGO_SD ? 2 : p->K * P);
+  const bool complex_tree = (p->flags & MDX_COMPLEX_TREE) != 0;
+  if (complex_tree && algo == ALGO_HYBRID) return fail(c, MDX_EUNSUPPORTED, "MDX_COMPLEX_TREE applies to SD and K-best");
+  int keys_cap = pow2ceil(algo == ALGO_SD ? 2 : p->K * (complex_tree ? P * P : P));
   if (algo == ALGO_HYBRID) {
     const int d = p->hybrid_depth;
     if (d < 0 || d > n || d > 12) return fail(c, MDX_EINVAL, "hybrid_depth %d not in 0..min(n, 12)", d);
@@ -299,13 +301,68 @@ mdx_status run_detect(int algo, mdx_ctx* c, const mdx_params* p, int batch, cons
   a.stats = dstats;
   e = cudaMemsetAsync(c->counter, 0, sizeof(unsigned int), s);
   if (e != cudaSuccess) return cuda_fail(c, e, "work counter reset");
-  if (ev) cudaEventRecord(ev[1], s);
-  if (algo == ALGO_SD) {
+  if (algo == ALGO_SD && complex_tree) {
+    // complex-tree SD: the persistent warp-per-vector kernel on a uniform batch
+    MixedArgs m{};
+    m.nreq = batch;
+    m.uniform.n_rx = N;
+    m.uniform.n_tx = M;
+    m.uniform.n = n;
+    m.uniform.P = P;
+    m.uniform.algo = MIX_ALGO_SD_COMPLEX;
+    m.uniform.mode = mixed_greedy_mode(MIX_ALGO_SD_COMPLEX, n, 0, P, c->mx_slice);
+    m.uniform.radius_mode = radius_mode;
+    m.uniform.radius_value = r0;
+    m.uniform.alpha = a.alpha;
+    m.uniform.alpha64 = a.alpha64;
+    m.uniform.budget = p->node_budget;
+    m.r2_vec = a.r2_vec;
+    m.R32 = c->R32;
+    m.yb32 = c->yb32;
+    m.R64 = c->R64;
+    m.yb64 = c->yb64;
+    m.singular = c->singular;
+    m.noise_var = dnv;
+    m.counter = c->counter;
+    m.slice_bytes = c->mx_slice;
+    m.flags = p->flags;
+    m.sym_out = dsym;
+    m.metric_out = dmet;
+    m.vstatus = dvst;
+    m.stats = dstats;
+    m.gslot_bytes = (m.uniform.mode & MIX_STATE_SMEM) ? 16 : mixed_state_bytes(MIX_ALGO_SD_COMPLEX, n, 0, P);
+    const int warps = mixed_resident_warps(c->mx_W, c->mx_slice, 0, c->num_sms);
+    if (warps < 1) return fail(c, MDX_EUNSUPPORTED, "no launch configuration fits this size");
+    const size_t sbytes = (size_t)warps * m.gslot_bytes;
+    if (c->mx_scratch_bytes < sbytes) {
+      // per-warp search state, allocated once on first use and kept
+      if (c->mx_graph) {
+        cudaGraphExecDestroy(c->mx_graph);
+        c->mx_graph = nullptr;
+      }
+      cudaStreamSynchronize(s);
+      if (c->mx_scratch) cudaFree(c->mx_scratch);
+      c->mx_scratch = nullptr;
+      c->mx_scratch_bytes = 0;
+      e = cudaMalloc(reinterpret_cast<void**>(&c->mx_scratch), sbytes);
+      if (e != cudaSuccess) return fail(c, MDX_ENOMEM, "%zu bytes of per-warp search state", sbytes);
+      c->mx_scratch_bytes = sbytes;
+    }
+    m.gscratch = c->mx_scratch;
+    if (ev) cudaEventRecord(ev[1], s);
+    e = launch_mixed(m, c->mx_W, 0, c->num_sms, s);
+  } else if (algo == ALGO_SD) {
+    if (ev) cudaEventRecord(ev[1], s);
     SdWorkspace w{c->sd_shared, c->sd_queue, kSdQueueSlots, c->sd_vstate, ++c->sd_epoch};
     e = launch_sd(a, w, c->num_sms, s);
   }
-  else if (algo == ALGO_KBEST) e = launch_kbest(a, c->num_sms, s);
-  else e = launch_hybrid(a, c->num_sms, s);
+  else if (algo == ALGO_KBEST) {
+    if (ev) cudaEventRecord(ev[1], s);
+    e = launch_kbest(a, c->num_sms, s);
+  } else {
+    if (ev) cudaEventRecord(ev[1], s);
+    e = launch_hybrid(a, c->num_sms, s);
+  }
   if (e == cudaErrorInvalidConfiguration)
     return fail(c, MDX_EUNSUPPORTED, "no launch configuration fits this size");
   if (e != cudaSuccess) return cuda_fail(c, e, "search launch");
@@ -334,17 +391,12 @@ unsigned long long class_key(const mdx_request& q) {
 bool mode_fits(int mode, int algo, int n, int K, int slice) {
   size_t need = 0;
   if (mode & MIX_STAGE_R) need += mixed_stage_bytes(n);
-  if (mode & MIX_STATE_SMEM) need += mixed_state_bytes(algo, n, K);
+  if (mode & MIX_STATE_SMEM) need += mixed_state_bytes(algo, n, K, 0);
   return need <= (size_t)slice;
 }
 
 // Most shared-memory use that fits: everything, else the state, else R.
-int greedy_mode(int algo, int n, int K, int slice) {
-  const int order[3] = {MIX_STAGE_R | MIX_STATE_SMEM, MIX_STATE_SMEM, MIX_STAGE_R};
-  for (int m : order)
-    if (mode_fits(m, algo, n, K, slice)) return m;
-  return 0;
-}
+int greedy_mode(int algo, int n, int K, int slice) { return mixed_greedy_mode(algo, n, K, 0, slice); }
 
 int mode_for(const mdx_ctx* c, const mdx_request& q) {
   const int n = 2 * q.n_tx;
@@ -361,8 +413,8 @@ mdx_status check_request(mdx_ctx* c, int r, const mdx_request& q) {
     return fail(c, MDX_EUNSUPPORTED, "request %d: %dx%d exceeds the context's %dx%d", r, q.n_rx, q.n_tx, c->max_rx,
                 c->max_tx);
   if (pam_of(q.qam) < 0) return fail(c, MDX_EINVAL, "request %d: qam %d not in {4, 16, 64}", r, q.qam);
-  if (q.algo != MDX_ALGO_SD && q.algo != MDX_ALGO_KBEST)
-    return fail(c, MDX_EINVAL, "request %d: algo %d is neither MDX_ALGO_SD nor MDX_ALGO_KBEST", r, q.algo);
+  if (q.algo != MDX_ALGO_SD && q.algo != MDX_ALGO_KBEST && q.algo != MDX_ALGO_SD_COMPLEX)
+    return fail(c, MDX_EINVAL, "request %d: algo %d is not MDX_ALGO_SD, _KBEST or _SD_COMPLEX", r, q.algo);
   if (q.algo == MDX_ALGO_KBEST && (q.K < 1 || q.K > MDX_MAX_K))
     return fail(c, MDX_EINVAL, "request %d: K %d not in 1..%d", r, q.K, MDX_MAX_K);
   if (isnan(q.init_radius_sq) || q.init_radius_sq == 0.0)
@@ -405,19 +457,21 @@ mdx_status mixed_upload(mdx_ctx* c, int nreq, const mdx_request* reqs, cudaStrea
     m.radius_value = r0;
     m.alpha64 = sqrt(3.0 / (2.0 * (q.qam - 1)));
     m.alpha = (float)m.alpha64;
-    m.budget = q.algo == MDX_ALGO_SD ? q.node_budget : 0;
+    m.budget = q.algo != MDX_ALGO_KBEST ? q.node_budget : 0;
     m.h_off = q.h_offset;
     m.yin_off = q.y_offset;
     m.sym_off = q.sym_offset;
     m.r_off = roff;
     m.y_off = yoff;
+    m.r_off64 = roff;
+    m.y_off64 = yoff;
     roff += tri_stride32(m.n);
     yoff += vec_stride32(m.n);
     if (m.K > maxK) maxK = m.K;
-    if (!(m.mode & MIX_STATE_SMEM)) gslot = std::max(gslot, mixed_state_bytes(m.algo, m.n, m.K));
+    if (!(m.mode & MIX_STATE_SMEM)) gslot = std::max(gslot, mixed_state_bytes(m.algo, m.n, m.K, m.P));
     // a cost proxy for the order: the exact SD's tree grows fastest with n
     const double n = m.n;
-    cost[r].first = (m.algo == MDX_ALGO_SD) ? n * n * n * m.P : n * m.K * (n + 8.0 * m.P);
+    cost[r].first = (m.algo != MDX_ALGO_KBEST) ? n * n * n * m.P : n * m.K * (n + 8.0 * m.P);
     cost[r].second = r;
   }
   std::stable_sort(cost.begin(), cost.end(),

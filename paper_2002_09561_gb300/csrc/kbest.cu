@@ -162,6 +162,75 @@ __device__ int kbest_levels(const KbCtx& c, int top, int S, uint8_t** xcur, uint
   return S;
 }
 
+// Complex-tree level steps (one level per complex antenna j: real rows 2j+1
+// then 2j, Q = P^2 children): thread t computes the interference of both rows
+// for survivor t and the partial distances of its Q children; keys
+// (distance, parent rank * Q + q) are sorted as in kbest_levels.
+__device__ int kbest_levels_complex(const KbCtx& c, int S, uint8_t** xcur, uint8_t** xnxt, float** pcur,
+                                    float** pnxt, const float* r2s, float E, long long* nodes, long long* peds,
+                                    long long* flops) {
+  const int n = c.n, P = c.P, Q = P * P, K = c.K, pp = c.pp, tid = c.tid, T = c.T;
+  for (int j = n / 2 - 1; j >= 0 && S > 0; --j) {
+    const int r1 = 2 * j + 1, r0 = 2 * j;
+    const float bnd = prune_bound(*r2s, E, n);
+    const int SQ = S * Q;
+    const int Cs = pow2ceil(SQ < 2 ? 2 : SQ);
+    for (int t = tid; t < S; t += T) {
+      const uint8_t* xp = *xcur + (size_t)t * pp;
+      float c1 = c.yb[r1], c0 = c.yb[r0];
+      for (int jj = n - 1; jj > r1; --jj) {
+        const float a = (float)(2 * (int)xp[jj] - (P - 1)) * c.alpha;
+        c1 = fmaf(-c.Rc[col_off(jj) + r1], a, c1);
+        c0 = fmaf(-c.Rc[col_off(jj) + r0], a, c0);
+      }
+      const float r11 = c.Rc[col_off(r1) + r1], r01 = c.Rc[col_off(r1) + r0], r00 = c.Rc[col_off(r0) + r0];
+      const float p0 = (*pcur)[t];
+      for (int q = 0; q < Q; ++q) {
+        const int kre = q / P, kim = q - kre * P;
+        const float aim = (float)(2 * kim - (P - 1)) * c.alpha, are = (float)(2 * kre - (P - 1)) * c.alpha;
+        const float d1 = fmaf(-r11, aim, c1);
+        const float p1 = fmaf(d1, d1, p0);
+        const float d0 = fmaf(-r00, are, fmaf(-r01, aim, c0));
+        const float pd = fmaf(d0, d0, p1);
+        const unsigned id = (unsigned)(t * Q + q);
+        c.keys[t * Q + q] = (pd < bnd) ? (((uint64_t)__float_as_uint(pd) << 32) | id) : kInfKey;
+      }
+    }
+    for (int q = SQ + tid; q < Cs; q += T) c.keys[q] = kInfKey;
+    if (tid == 0) c.misc[0] = 0;
+    __syncthreads();
+    bitonic_sort(c.keys, Cs, tid, T);
+    for (int q = tid; q < Cs; q += T)
+      if (c.keys[q] != kInfKey && (q + 1 == Cs || c.keys[q + 1] == kInfKey)) c.misc[0] = q + 1;
+    __syncthreads();
+    const int valid = c.misc[0];
+    const int kept = valid < K ? valid : K;
+    for (int t = tid; t < kept; t += T) {
+      const uint64_t key = c.keys[t];
+      const unsigned id = (unsigned)(key & 0xffffffffu);
+      const int par = (int)(id / (unsigned)Q), q = (int)(id % (unsigned)Q);
+      const uint32_t* src = reinterpret_cast<const uint32_t*>(*xcur + (size_t)par * pp);
+      uint32_t* dst = reinterpret_cast<uint32_t*>(*xnxt + (size_t)t * pp);
+      for (int w = 0; w < pp / 4; ++w) dst[w] = src[w];
+      (*xnxt)[(size_t)t * pp + r1] = (uint8_t)(q % P);
+      (*xnxt)[(size_t)t * pp + r0] = (uint8_t)(q / P);
+      (*pnxt)[t] = __uint_as_float((unsigned)(key >> 32));
+    }
+    *nodes += S;
+    *peds += SQ;
+    *flops += (long long)S * (4 * (n - 2 - r0) + 10 * Q);
+    __syncthreads();
+    uint8_t* tx = *xcur;
+    *xcur = *xnxt;
+    *xnxt = tx;
+    float* tp = *pcur;
+    *pcur = *pnxt;
+    *pnxt = tp;
+    S = kept;
+  }
+  return S;
+}
+
 // Stage R and ybar of vector v into shared memory and compute E and r2.
 __device__ void stage_vector(const SearchArgs& a, int v, const KbLayout& L, unsigned char* smem,
                              float* misc_f) {
@@ -289,7 +358,10 @@ __global__ void kbest_kernel(SearchArgs a, KbLayout L) {
       pnxt = reinterpret_cast<float*>(smem + L.off_pb);
       if (tid == 0) pcur[0] = 0.0f;
       __syncthreads();
-      S = kbest_levels(c, n - 1, 1, &xcur, &xnxt, &pcur, &pnxt, &misc_f[1], E, &nodes, &peds, &flops);
+      if (a.flags & MDX_COMPLEX_TREE)
+        S = kbest_levels_complex(c, 1, &xcur, &xnxt, &pcur, &pnxt, &misc_f[1], E, &nodes, &peds, &flops);
+      else
+        S = kbest_levels(c, n - 1, 1, &xcur, &xnxt, &pcur, &pnxt, &misc_f[1], E, &nodes, &peds, &flops);
       if (S > 0 || !(misc_f[1] < INFINITY) || restarts >= 64) break;
       __syncthreads();
       if (tid == 0) misc_f[1] *= 4.0f;  // empty sphere: double the radius
@@ -617,11 +689,12 @@ cudaError_t launch_generic(const void* fn, const SearchArgs& a, const KbLayout& 
 
 cudaError_t launch_kbest(const SearchArgs& a, int num_sms, cudaStream_t s) {
   if (a.batch <= 0) return cudaSuccess;
-  const int C = pow2ceil(a.K * a.P);
+  const int branching = (a.flags & MDX_COMPLEX_TREE) ? a.P * a.P : a.P;
+  const int C = pow2ceil(a.K * branching);
   KbLayout L;
   L.init(a.n, a.K, a.P, C < 2 ? 2 : C);
   if (L.bytes > 227 * 1024) return cudaErrorInvalidConfiguration;
-  return launch_generic((const void*)kbest_kernel, a, L, kb_threads(a.K, a.P), num_sms, s);
+  return launch_generic((const void*)kbest_kernel, a, L, kb_threads(a.K, branching), num_sms, s);
 }
 
 cudaError_t launch_hybrid(const SearchArgs& a, int num_sms, cudaStream_t s) {

@@ -85,20 +85,25 @@ struct MixedReq {
   long long budget;
   long long h_off, yin_off;  // H and y of the request (doubles)
   long long sym_off;
-  long long r_off, y_off;
+  long long r_off, y_off;      // FP32 R / ybar (elements)
+  long long r_off64, y_off64;  // FP64 R / ybar (elements)
 };
 // placement of a request's data: R and ybar staged in the warp's shared-memory
 // slice, and the search state (SD stacks / K-best survivors) in the slice;
 // otherwise each is read from / kept in global memory
 enum { MIX_STAGE_R = 1, MIX_STATE_SMEM = 2 };
+// detector of a request (MDX_ALGO_SD / MDX_ALGO_KBEST, or the complex-tree SD)
+enum { MIX_ALGO_SD_COMPLEX = 2 };
 
 cudaError_t launch_qr_gather(int count, int n_rx, int n_tx, const int* ids, const MixedReq* reqs,
                              const double* H, const double* y, QrOut out, cudaStream_t s);
 
 struct MixedArgs {
   int nreq;
-  const MixedReq* reqs;
-  const int* order;  // requests in the order warps take them
+  const MixedReq* reqs;  // null: a uniform batch described by `uniform` (request r = vector r)
+  const int* order;      // requests in the order warps take them (null: table order)
+  MixedReq uniform;      // uniform batch: the fields shared by every vector, offsets zero
+  const float* r2_vec;   // uniform batch with RADIUS_PER_VECTOR: initial r^2 per vector
   const float* R32;
   const float* yb32;
   const double* R64;
@@ -117,10 +122,12 @@ struct MixedArgs {
 };
 // Bytes of a request's staged R + ybar and of its search state.
 size_t mixed_stage_bytes(int n);
-size_t mixed_state_bytes(int algo, int n, int K);
+size_t mixed_state_bytes(int algo, int n, int K, int P);
 // Warps a launch with this shape keeps resident (for sizing gscratch).
 int mixed_resident_warps(int warps_per_cta, int slice_bytes, int max_K, int num_sms);
 cudaError_t launch_mixed(const MixedArgs& a, int warps_per_cta, int max_K, int num_sms, cudaStream_t s);
+// Placement of a uniform batch's vectors for a slice size (MIX_* bits).
+int mixed_greedy_mode(int algo, int n, int K, int P, int slice_bytes);
 // Global workspace of the sphere decoder's task queue (see sd.cu).
 struct SdWorkspace {
   void* shared;          // sd_shared_bytes()

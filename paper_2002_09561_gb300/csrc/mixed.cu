@@ -42,6 +42,17 @@ __host__ __device__ inline size_t sd_state_bytes(int n) {
   return (b + 15) / 16 * 16;
 }
 
+// Complex-tree SD: residual stack, per complex level {parent distance, c of
+// row 2j+1, c of row 2j before x_{2j+1}, visited-children mask low word} and
+// the mask's high word, level constants {R_{2j+1,2j+1}, R_{2j,2j+1}, R_{2j,2j}},
+// candidates, path.
+__host__ __device__ inline size_t sdc_state_bytes(int n) {
+  const size_t M = (size_t)n / 2;
+  const size_t b = sizeof(float) * round_up(tri(n), 4) + 16 * M + sizeof(unsigned) * round_up((int)M, 4) +
+                   16 * M + sizeof(float) * kMixCand + (size_t)mix_path_pad(n) * (1 + kMixCand);
+  return (b + 15) / 16 * 16;
+}
+
 __host__ __device__ inline size_t kb_state_bytes(int n, int K) {
   const size_t b = 16 + 2 * sizeof(float) * round_up(K, 4) + 2 * sizeof(uint16_t) * round_up(K, 8) +
                    2 * (size_t)path_stride(n) * K;
@@ -50,7 +61,8 @@ __host__ __device__ inline size_t kb_state_bytes(int n, int K) {
 
 __device__ float initial_r2(const MixedArgs& g, const MixedReq& q, int r) {
   float r2;
-  if (q.radius_mode == RADIUS_NONE) r2 = INFINITY;
+  if (q.radius_mode == RADIUS_PER_VECTOR) r2 = g.r2_vec[r];
+  else if (q.radius_mode == RADIUS_NONE) r2 = INFINITY;
   else if (q.radius_mode == RADIUS_PAPER) r2 = (float)((double)q.n_rx * q.n_tx * g.noise_var[r]);
   else r2 = (float)q.radius_value;
   return (r2 > 0.0f) ? r2 : INFINITY;
@@ -67,8 +79,8 @@ __device__ void finish_request(const MixedArgs& g, const MixedReq& q, int r, con
   float best = INFINITY;
   for (int k = 0; k < nc; ++k) best = fminf(best, cped[k]);
   const float keep = prune_bound(best, E, n);
-  const double* R64 = g.R64 + q.r_off;
-  const double* y64 = g.yb64 + q.y_off;
+  const double* R64 = g.R64 + q.r_off64;
+  const double* y64 = g.yb64 + q.y_off64;
   int win = -1;
   double win_m = INFINITY;
   long long rescored = 0;
@@ -265,6 +277,171 @@ __device__ void sd_request(const MixedArgs& g, const MixedReq& q, int r, const f
   finish_request(g, q, r, cx, cs, cped, ncand, E, status, nodes, peds, restarts, flops, lane);
 }
 
+// Complex-tree exact SD of one request by one warp: one tree level per complex
+// antenna j (real rows 2j+1, then 2j), Q = P^2 children.  The next child of a
+// node is the unvisited one of least partial distance (ties to the lower q),
+// found by a warp arg-min; a level is exhausted when that child leaves the
+// sphere.  A descent updates the residuals of the rows below by both fixed
+// rows; the rest (candidates, radius shrink and doubling, budget, FP64
+// re-scoring) is as in sd_request.
+template <int ROWS>
+__device__ void sdc_request(const MixedArgs& g, const MixedReq& q, int r, const float* Rc, const float* yb,
+                            unsigned char* st, float E, int lane) {
+  const int n = q.n, P = q.P, Q = P * P, M = n / 2;
+  const float alpha = q.alpha;
+  float* zs = reinterpret_cast<float*>(st);
+  float4* lv = reinterpret_cast<float4*>(zs + round_up(tri(n), 4));
+  unsigned* lv_hi = reinterpret_cast<unsigned*>(lv + M);
+  float4* lv_r = reinterpret_cast<float4*>(lv_hi + round_up(M, 4));
+  float* cped = reinterpret_cast<float*>(lv_r + M);
+  uint8_t* xs = reinterpret_cast<uint8_t*>(cped + kMixCand);
+  uint8_t* cx = xs + mix_path_pad(n);
+  const int cs = mix_path_pad(n);
+  for (int j = lane; j < M; j += 32) {
+    const int r1 = 2 * j + 1, r0 = 2 * j;
+    lv_r[j] = make_float4(Rc[col_off(r1) + r1], Rc[col_off(r1) + r0], Rc[col_off(r0) + r0], 0.0f);
+  }
+  float r2_start = initial_r2(g, q, r);
+  float r2 = r2_start;
+  long long nodes = 0, peds = 0, flops = 0;
+  int restarts = 0, ncand = 0;
+  bool bh = false;
+  for (;;) {
+#pragma unroll
+    for (int t = 0; t < ROWS; ++t) {
+      const int rr = lane + 32 * t;
+      if (rr < n) zs[col_off(n - 1) + rr] = yb[rr];
+    }
+    __syncwarp();
+    float bnd = prune_bound(r2, E, n);
+    int j = M - 1;
+    float ped_par = 0.0f;
+    float c1 = zs[col_off(n - 1) + n - 1], c0 = zs[col_off(n - 1) + n - 2];
+    float4 rl = lv_r[j];
+    unsigned long long mask = 0ull;
+    ++nodes;
+    peds += Q;
+    flops += 10 * Q;
+    for (;;) {
+      // the unvisited child of least partial distance
+      unsigned long long best = ~0ull;
+#pragma unroll
+      for (int t = 0; t < 2; ++t) {
+        const int qq = lane + 32 * t;
+        if (qq < Q && !((mask >> qq) & 1ull)) {
+          const int kre = qq / P, kim = qq - kre * P;
+          const float aim = (float)(2 * kim - (P - 1)) * alpha, are = (float)(2 * kre - (P - 1)) * alpha;
+          const float d1 = fmaf(-rl.x, aim, c1);
+          const float p1 = fmaf(d1, d1, ped_par);
+          const float d0 = fmaf(-rl.z, are, fmaf(-rl.y, aim, c0));
+          const float pd = fmaf(d0, d0, p1);
+          const unsigned long long key = ((unsigned long long)__float_as_uint(pd) << 32) | (unsigned)qq;
+          if (key < best) best = key;
+        }
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        const unsigned long long other = __shfl_xor_sync(0xffffffffu, best, o);
+        if (other < best) best = other;
+      }
+      const float ped = (best == ~0ull) ? INFINITY : __uint_as_float((unsigned)(best >> 32));
+      if (!(ped < bnd)) {
+        if (j == M - 1) break;  // the root is exhausted
+        ++j;                    // backtrack
+        const float4 s4 = lv[j];
+        ped_par = s4.x;
+        c1 = s4.y;
+        c0 = s4.z;
+        mask = (unsigned long long)__float_as_uint(s4.w) | ((unsigned long long)lv_hi[j] << 32);
+        rl = lv_r[j];
+        continue;
+      }
+      const int qk = (int)(best & 0xffffffffu);
+      mask |= 1ull << qk;
+      const int kre = qk / P, kim = qk - kre * P;
+      if (j == 0) {
+        // leaf inside the sphere: keep it among the kMixCand best, shrink the radius
+        int slot = -1;
+        if (lane == 0) {
+          xs[1] = (uint8_t)kim;
+          xs[0] = (uint8_t)kre;
+          if (ncand < kMixCand) {
+            slot = ncand;
+          } else {
+            float worst = -1.0f;
+            for (int t = 0; t < kMixCand; ++t)
+              if (cped[t] > worst) {
+                worst = cped[t];
+                slot = t;
+              }
+            if (!(ped < worst)) slot = -1;
+          }
+        }
+        slot = __shfl_sync(0xffffffffu, slot, 0);
+        __syncwarp();
+        if (slot >= 0) {
+          for (int rr = lane; rr < n; rr += 32) cx[(size_t)slot * cs + rr] = xs[rr];
+          if (lane == 0) cped[slot] = ped;
+          if (slot == ncand) ++ncand;
+        }
+        __syncwarp();
+        if (ped < r2) {
+          r2 = ped;
+          bnd = prune_bound(r2, E, n);
+        }
+        continue;
+      }
+      if (q.budget > 0 && nodes >= q.budget) {
+        bh = true;
+        break;
+      }
+      // descend: push level j, update the residuals of rows 0..2j-1 by both fixed rows
+      const float aim = (float)(2 * kim - (P - 1)) * alpha, are = (float)(2 * kre - (P - 1)) * alpha;
+      if (lane == 0) {
+        lv[j] = make_float4(ped_par, c1, c0, __uint_as_float((unsigned)mask));
+        lv_hi[j] = (unsigned)(mask >> 32);
+        xs[2 * j + 1] = (uint8_t)kim;
+        xs[2 * j] = (uint8_t)kre;
+      }
+      const float* zin = zs + col_off(2 * j + 1);
+      float* zout = zs + col_off(2 * j - 1);
+      const float* ra = Rc + col_off(2 * j + 1);
+      const float* rb = Rc + col_off(2 * j);
+      float n1 = 0.0f, n0 = 0.0f;
+#pragma unroll
+      for (int t = 0; t < ROWS; ++t) {
+        const int rr = lane + 32 * t;
+        if (rr < 2 * j) {
+          const float z = fmaf(-rb[rr], are, fmaf(-ra[rr], aim, zin[rr]));
+          zout[rr] = z;
+          if (rr == 2 * j - 1) n1 = z;
+          if (rr == 2 * j - 2) n0 = z;
+        }
+      }
+      --j;
+      c1 = __shfl_sync(0xffffffffu, n1, (2 * j + 1) & 31);
+      c0 = __shfl_sync(0xffffffffu, n0, (2 * j) & 31);
+      __syncwarp();
+      ped_par = ped;
+      rl = lv_r[j];
+      mask = 0ull;
+      ++nodes;
+      peds += Q;
+      flops += 4 * (n - 2 - 2 * j) + 10 * Q;
+    }
+    if (ncand == 0 && !bh && r2_start < INFINITY && restarts < 64) {
+      r2_start *= 4.0f;  // empty sphere: r^2 <- 4 r^2 and search again
+      r2 = r2_start;
+      ++restarts;
+      continue;
+    }
+    break;
+  }
+  __syncwarp();
+  const int status = bh ? MDX_V_BUDGET_EXCEEDED : (restarts > 0 ? MDX_V_EMPTY_RETRIED : MDX_V_OK);
+  finish_request(g, q, r, cx, cs, cped, ncand, E, status, nodes, peds, restarts, flops, lane);
+}
+
 // K-best of one request by one warp (SPL survivor slots per lane, K <= 32 SPL).
 template <int SPL>
 __device__ void kb_request(const MixedArgs& g, const MixedReq& q, int r, const float* Rc, const float* yb,
@@ -314,8 +491,18 @@ __global__ void mixed_kernel(MixedArgs g) {
     if (lane == 0) t = atomicAdd(g.counter, 1u);
     t = __shfl_sync(0xffffffffu, t, 0);
     if (t >= (unsigned int)g.nreq) break;
-    const int r = g.order[t];
-    const MixedReq q = g.reqs[r];
+    const int r = g.order ? g.order[t] : (int)t;
+    MixedReq q;
+    if (g.reqs) {
+      q = g.reqs[r];
+    } else {
+      q = g.uniform;
+      q.r_off = (long long)r * tri_stride32(q.n);
+      q.y_off = (long long)r * vec_stride32(q.n);
+      q.r_off64 = (long long)r * tri_stride64(q.n);
+      q.y_off64 = (long long)r * vec_stride64(q.n);
+      q.sym_off = (long long)r * q.n_tx;
+    }
     if (g.singular[r]) {
       for (int j = lane; j < q.n_tx; j += 32) g.sym_out[q.sym_off + j] = 0;
       if (lane == 0) {
@@ -349,6 +536,11 @@ __global__ void mixed_kernel(MixedArgs g) {
       else if (q.n <= 64) sd_request<2>(g, q, r, Rc, yb, st, E, lane);
       else if (q.n <= 128) sd_request<4>(g, q, r, Rc, yb, st, E, lane);
       else sd_request<7>(g, q, r, Rc, yb, st, E, lane);
+    } else if (q.algo == MIX_ALGO_SD_COMPLEX) {
+      if (q.n <= 32) sdc_request<1>(g, q, r, Rc, yb, st, E, lane);
+      else if (q.n <= 64) sdc_request<2>(g, q, r, Rc, yb, st, E, lane);
+      else if (q.n <= 128) sdc_request<4>(g, q, r, Rc, yb, st, E, lane);
+      else sdc_request<7>(g, q, r, Rc, yb, st, E, lane);
     } else {
       if (q.K <= 32) kb_request<1>(g, q, r, Rc, yb, st, E, lane);
       else if (KSPL <= 2 || q.K <= 64) kb_request<2>(g, q, r, Rc, yb, st, E, lane);
@@ -378,8 +570,19 @@ cudaError_t prepare(int W, int slice_bytes, int num_sms, int* grid) {
 
 size_t mixed_stage_bytes(int n) { return stage_bytes(n); }
 
-size_t mixed_state_bytes(int algo, int n, int K) {
-  return algo == MDX_ALGO_SD ? sd_state_bytes(n) : kb_state_bytes(n, K);
+size_t mixed_state_bytes(int algo, int n, int K, int P) {
+  (void)P;
+  if (algo == MDX_ALGO_SD) return sd_state_bytes(n);
+  if (algo == MIX_ALGO_SD_COMPLEX) return sdc_state_bytes(n);
+  return kb_state_bytes(n, K);
+}
+
+int mixed_greedy_mode(int algo, int n, int K, int P, int slice) {
+  const size_t stage = stage_bytes(n), state = mixed_state_bytes(algo, n, K, P);
+  if (stage + state <= (size_t)slice) return MIX_STAGE_R | MIX_STATE_SMEM;
+  if (state <= (size_t)slice) return MIX_STATE_SMEM;
+  if (stage <= (size_t)slice) return MIX_STAGE_R;
+  return 0;
 }
 
 int mixed_resident_warps(int W, int slice_bytes, int max_K, int num_sms) {

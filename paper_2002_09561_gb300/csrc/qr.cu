@@ -613,7 +613,7 @@ __global__ void __launch_bounds__(kQrdWarps * 32, 1)
   if ((int)blockIdx.x >= count) return;
   const int r = ids[blockIdx.x];
   const MixedReq q = reqs[r];
-  QrDst d{out.R64 + q.r_off, out.yb64 + q.y_off, out.R32 + q.r_off, out.yb32 + q.y_off, nullptr, nullptr,
+  QrDst d{out.R64 + q.r_off64, out.yb64 + q.y_off64, out.R32 + q.r_off, out.yb32 + q.y_off, nullptr, nullptr,
           out.singular + r};
   qr_dmma_one(q.n_rx, q.n_tx, reinterpret_cast<const double2*>(H + q.h_off),
               reinterpret_cast<const double2*>(y + q.yin_off), d);
@@ -657,7 +657,7 @@ __global__ void qr_gather_kernel(int count, const int* __restrict__ ids, const M
   if ((int)blockIdx.x >= count) return;
   const int r = ids[blockIdx.x];
   const MixedReq q = reqs[r];
-  QrDst d{out.R64 + q.r_off, out.yb64 + q.y_off, out.R32 + q.r_off, out.yb32 + q.y_off, nullptr, nullptr,
+  QrDst d{out.R64 + q.r_off64, out.yb64 + q.y_off64, out.R32 + q.r_off, out.yb32 + q.y_off, nullptr, nullptr,
           out.singular + r};
   qr_one<LPC>(q.n_rx, q.n_tx, reinterpret_cast<const double2*>(H + q.h_off),
               reinterpret_cast<const double2*>(y + q.yin_off), d);

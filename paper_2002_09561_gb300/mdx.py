@@ -21,8 +21,9 @@ MDX_OK, MDX_EINVAL, MDX_EUNSUPPORTED, MDX_ENOMEM, MDX_ECUDA = 0, -1, -2, -3, -4
 MDX_V_OK, MDX_V_EMPTY_RETRIED, MDX_V_BUDGET_EXCEEDED, MDX_V_SINGULAR = 0, 1, 2, 3
 MDX_HOST_BUFFERS, MDX_NO_RESCORE, MDX_LEARNED_RADIUS, MDX_SEQUENTIAL_SEARCH = 1, 2, 4, 8
 MDX_LEARNED_ORDER = 1 << 5
+MDX_COMPLEX_TREE = 1 << 6
 MDX_MAX_TX, MDX_MAX_RX, MDX_MAX_K = 100, 128, 256
-MDX_ALGO_SD, MDX_ALGO_KBEST = 0, 1
+MDX_ALGO_SD, MDX_ALGO_KBEST, MDX_ALGO_SD_COMPLEX = 0, 1, 2
 MDX_GRAPH = 1 << 4
 
 # Every symbol the header declares; the library must export all of them.
