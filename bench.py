@@ -49,6 +49,15 @@ WORKLOADS = {
                                    detector="hybrid", radius="paper", K=32, depth=4),
     "100x100-64qam-hybrid128": dict(n=100, qam=64, snr=[20.0, 24.0, 28.0, 32.0], vectors=10_000,
                                     detector="hybrid", radius="paper", K=128, depth=4),
+    # complex tree (one level per complex antenna, Q children): exact SD with the
+    # learned radius and K-best on the paper's 16x16 64-QAM configuration
+    # (the complex-tree SD runs one warp per vector without subtree splitting, so
+    # its low-SNR tail is one warp's: the sweep starts at 12 dB)
+    "16x16-16qam-sd-complex-learned": dict(n=16, qam=16, snr=[12.0, 14.0, 16.0, 18.0, 20.0], vectors=100_000,
+                                           detector="sd", radius="paper", K=0, depth=0, learned=True,
+                                           complex=True),
+    "16x16-64qam-kbest32-complex": dict(n=16, qam=64, snr=[16.0, 20.0, 24.0, 28.0], vectors=100_000,
+                                        detector="kbest", radius=math.inf, K=32, depth=0, complex=True),
     # uneven batch: n_tx = n_rx in {8, 16, 32, 64, 100}, {4, 16, 64}-QAM, SNR U(6, 30) dB,
     # half exact SD (paper radius, node budget) and half K-best K=64, one detect_mixed call
     "mixed-50k": dict(mixed=True, n=100, qam=64, antennas=(8, 16, 32, 64, 100), qams=(4, 16, 64),
@@ -212,7 +221,7 @@ def cpu_baseline(w, seed, target_s, start_offset):
     if w.get("mixed"):
         return cpu_baseline_mixed(w, seed, target_s)
     cores = oracle.max_threads()
-    algo = w["detector"]
+    algo = w["detector"] + ("_complex" if w.get("complex") else "")
     done = 0
     t0 = time.perf_counter()
     chunk = max(cores, 16)
@@ -263,7 +272,7 @@ def config_of(args, w, world):
                 "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
                 "l2": "inputs larger than L2 (no flush)"}
     return {"workload": args.workload, "n_tx": w["n"], "n_rx": w["n"], "qam": w["qam"],
-            "detector": w["detector"], "K": w["K"] or None, "hybrid_depth": w["depth"] or None,
+            "detector": w["detector"] + (" (complex tree)" if w.get("complex") else ""), "K": w["K"] or None, "hybrid_depth": w["depth"] or None,
             "initial_radius": "r^2 = N M sigma^2" if w["radius"] == "paper" else "none",
             "snr_db": w["snr"], "vectors_per_step_per_gpu": w["vectors"], "global_batch": w["vectors"] * world,
             "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
@@ -323,6 +332,8 @@ def main():
 
         model_meta = train.load_model(ctx, n, qam)
     flags = (mdx.MDX_LEARNED_RADIUS | mdx.MDX_LEARNED_ORDER) if learned else 0
+    if w.get("complex"):
+        flags |= mdx.MDX_COMPLEX_TREE
     params = mdx.make_params(n, n, qam, radius=w["radius"], K=max(w["K"], 1), depth=w["depth"], flags=flags)
     algo = w["detector"]
     out = mdx._outputs(B, n, dev, True)
@@ -367,7 +378,8 @@ def main():
     value = B * world * args.steps / (ms / 1e3)
     plain = None
     if learned and not args.no_plain:
-        pparams = mdx.make_params(n, n, qam, radius=w["radius"], K=max(w["K"], 1), depth=w["depth"])
+        pparams = mdx.make_params(n, n, qam, radius=w["radius"], K=max(w["K"], 1), depth=w["depth"],
+                                  flags=mdx.MDX_COMPLEX_TREE if w.get("complex") else 0)
         pout = mdx._outputs(B, n, dev, True)
         pms, _, perrs, _ = timed(pparams, pout, args.steps, 1)
         same = bool(torch.equal(pout[0], out[0]))
