@@ -263,7 +263,7 @@ def count_errors(sym_hat, sym_true, qam):
 
 def detect_mixed(reqs, H, y, noise_var, want_gap=True, nthreads=0):
     """An uneven batch (request table with the fields of mdx_request: n_rx,
-    n_tx, qam, algo (0 = exact SD, 1 = K-best, 2 = complex-tree SD), K, init_radius_sq (negative =
+    n_tx, qam, algo (0 = exact SD, 1 = K-best, 2 = complex-tree SD, 3 = natural-order SD), K, init_radius_sq (negative =
     the paper's N M sigma^2), node_budget and the offsets of each request's H,
     y and symbols in the flat arrays) detected request by request with
     detect_batch, grouping requests of equal parameters.  Returns flat symbols
@@ -284,10 +284,11 @@ def detect_mixed(reqs, H, y, noise_var, want_gap=True, nthreads=0):
         Hb = np.stack([H[int(reqs[i]["h_offset"]):int(reqs[i]["h_offset"]) + 2 * N * M] for i in idx])
         yb = np.stack([y[int(reqs[i]["y_offset"]):int(reqs[i]["y_offset"]) + 2 * N] for i in idx])
         radius = "paper" if r0 < 0 else r0
-        name = {0: "sd", 1: "kbest", 2: "sd_complex"}[algo]
+        name = {0: "sd", 1: "kbest", 2: "sd_complex", 3: "sd"}[algo]
         out = detect_batch(name, Hb.reshape(len(idx), N, M, 2), yb.reshape(len(idx), N, 2),
                            nv[idx], qam, radius=radius, K=max(K, 1), budget=budget,
-                           want_gap=want_gap and algo != 1, nthreads=nthreads)
+                           order="natural" if algo == 3 else "se", want_gap=want_gap and algo != 1,
+                           nthreads=nthreads)
         for j, i in enumerate(idx):
             s0 = int(reqs[i]["sym_offset"])
             sym[s0:s0 + M] = out["sym"][j]
@@ -295,3 +296,46 @@ def detect_mixed(reqs, H, y, noise_var, want_gap=True, nthreads=0):
         status[idx] = out["status"]
         gap[idx] = out["gap"]
     return {"sym": sym, "metric": met, "status": status, "gap": gap}
+
+
+def _slice(x, qam):
+    """Nearest PAM index of each real component (clipped to the grid) and the
+    relative distance of each component to its decision boundary."""
+    P = int(round(qam ** 0.5))
+    alpha = np.sqrt(3.0 / (2.0 * (qam - 1)))
+    u = (x / alpha + (P - 1)) / 2.0
+    k = np.clip(np.floor(u + 0.5), 0, P - 1).astype(np.int64)
+    frac = np.abs(u - np.floor(u) - 0.5)  # 0 at a boundary between two levels
+    inside = (u > 0.0) & (u < P - 1)
+    margin = np.where(inside, frac, 1.0)
+    return k, margin
+
+
+def detect_linear(kind, H, y, noise_var, qam):
+    """Linear detection of a batch (the controls of Sec. III-A): ZF, the
+    least-squares solution of the real system, or MMSE,
+    (Hr^T Hr + sigma^2 I)^-1 Hr^T yr (unit-energy symbols, sigma^2 per
+    complex entry), each component sliced to the nearest PAM level.  Returns
+    sym [B][M], metric ||ybar - R x^||^2 (oracle QR), and margin [B], the
+    smallest distance of a component to a decision boundary (in half PAM
+    steps; near 0 means the slicing is a near-tie)."""
+    H, y, nv = _f64(H), _f64(y), _f64(noise_var)
+    B, N, M = H.shape[0], H.shape[1], H.shape[2]
+    P = int(round(qam ** 0.5))
+    lev = pam_levels(qam)
+    sym = np.zeros((B, M), dtype=np.uint8)
+    met, margin = np.zeros(B), np.zeros(B)
+    R, yb = qr_batch(H, y)
+    for b in range(B):
+        Hr, yr = real_decompose(H[b], y[b])
+        if kind == "zf":
+            x = np.linalg.lstsq(Hr, yr, rcond=None)[0]
+        elif kind == "mmse":
+            x = np.linalg.solve(Hr.T @ Hr + nv[b] * np.eye(2 * M), Hr.T @ yr)
+        else:
+            raise ValueError(kind)
+        k, mg = _slice(x, qam)
+        sym[b] = k[0::2] * P + k[1::2]
+        met[b] = float(np.sum((yb[b] - R[b] @ lev[k]) ** 2))
+        margin[b] = mg.min()
+    return {"sym": sym, "metric": met, "margin": margin}
