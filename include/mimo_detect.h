@@ -99,6 +99,10 @@ enum {
                                      q; K-best keeps K per complex level.  stats count
                                      complex-level nodes and qam children per node.
                                      detect_sd runs it one warp per vector (no splitting). */
+  MDX_LINEAR_MMSE = 1 << 8,       /* detect_linear: MMSE instead of zero forcing */
+  MDX_ORDER_NATURAL = 1 << 7,     /* detect_sd: visit children in natural index order instead
+                                     of Schnorr-Euchner order (the unsorted depth-first
+                                     search of Sec. IV-A, a control); one warp per vector */
   MDX_LEARNED_ORDER = 1 << 5      /* detect_sd: the MLP's per-row child ranking (mdx_mlp_load)
                                      proposes the first leaf x^ (the top-ranked PAM index
                                      of every real row, ties to the lower index); the
@@ -180,6 +184,16 @@ mdx_status detect_kbest(mdx_ctx* ctx, const mdx_params* p, int batch, const doub
 mdx_status detect_hybrid(mdx_ctx* ctx, const mdx_params* p, int batch, const double* H,
                          const double* y, const double* noise_var, uint8_t* sym_out,
                          double* metric_out, int32_t* vstatus, int64_t* stats, void* stream);
+/* Linear detection, the controls of Sec. III-A: zero forcing
+ * x = H^+ y = R^-1 ybar (back substitution on the FP64 QR), or with
+ * MDX_LINEAR_MMSE in p->flags, x = (H^H H + sigma^2 I)^-1 H^H y
+ * (regularised normal equations, Cholesky; needs noise_var; n_tx <= 32).
+ * Every real component is sliced to the nearest PAM level (clipped); the
+ * outputs are as for detect_sd (metric ||ybar - R x^||^2 in FP64, stats
+ * zero except rescored = 1).  K, radius, depth and budget are ignored. */
+mdx_status detect_linear(mdx_ctx* ctx, const mdx_params* p, int batch, const double* H, const double* y,
+                         const double* noise_var, uint8_t* sym_out, double* metric_out, int32_t* vstatus,
+                         int64_t* stats, void* stream);
 
 /* ---------------------------------------------------------------------------
  * Uneven batches: one call detects many requests that differ in antennas,
@@ -202,7 +216,12 @@ mdx_status detect_hybrid(mdx_ctx* ctx, const mdx_params* p, int batch, const dou
  * change between such calls).
  * Limits: n_tx <= MDX_MAX_TX, K <= MDX_MAX_K, nreq <= the context's max_batch
  * and the sum of per-request QR outputs within the workspace. */
-enum { MDX_ALGO_SD = 0, MDX_ALGO_KBEST = 1, MDX_ALGO_SD_COMPLEX = 2 /* complex-tree SD, as MDX_COMPLEX_TREE */ };
+enum {
+  MDX_ALGO_SD = 0,
+  MDX_ALGO_KBEST = 1,
+  MDX_ALGO_SD_COMPLEX = 2, /* complex-tree SD, as MDX_COMPLEX_TREE */
+  MDX_ALGO_SD_NATURAL = 3  /* natural-order SD, as MDX_ORDER_NATURAL */
+};
 enum { MDX_GRAPH = 1 << 4 };
 typedef struct {
   int n_rx, n_tx, qam;

@@ -148,7 +148,7 @@ void free_all(mdx_ctx* c) {
   if (c->mx_pinned) cudaFreeHost(c->mx_pinned);
 }
 
-enum Algo { ALGO_SD = 0, ALGO_KBEST = 1, ALGO_HYBRID = 2 };
+enum Algo { ALGO_SD = 0, ALGO_KBEST = 1, ALGO_HYBRID = 2, ALGO_LINEAR = 3 };
 
 // Task-queue slots of the sphere decoder (tasks exist only while warps are idle).
 constexpr unsigned int kSdQueueSlots = 1u << 16;
@@ -192,11 +192,20 @@ mdx_status run_detect(int algo, mdx_ctx* c, const mdx_params* p, int batch, cons
     if (!nv) return fail(c, MDX_EINVAL, "noise_var needed for the learned radius / order (network input)");
   }
   if (p->node_budget < 0) return fail(c, MDX_EINVAL, "node_budget < 0");
-  if (algo != ALGO_SD) {
+  const bool mmse = (p->flags & MDX_LINEAR_MMSE) != 0;
+  if (algo == ALGO_LINEAR) {
+    if (mmse && !nv) return fail(c, MDX_EINVAL, "noise_var needed for MMSE");
+    if ((mmse && M > 32) || linear_smem_bytes(n, mmse) > 227 * 1024)
+      return fail(c, MDX_EUNSUPPORTED, "MMSE supports n_tx <= 32 (got %d)", M);
+  }
+  if (algo != ALGO_SD && algo != ALGO_LINEAR) {
     if (p->K < 1 || p->K > MDX_MAX_K) return fail(c, MDX_EINVAL, "K %d not in 1..%d", p->K, MDX_MAX_K);
   }
   const bool complex_tree = (p->flags & MDX_COMPLEX_TREE) != 0;
+  const bool natural = (p->flags & MDX_ORDER_NATURAL) != 0;
   if (complex_tree && algo == ALGO_HYBRID) return fail(c, MDX_EUNSUPPORTED, "MDX_COMPLEX_TREE applies to SD and K-best");
+  if (natural && (algo != ALGO_SD || complex_tree))
+    return fail(c, MDX_EUNSUPPORTED, "MDX_ORDER_NATURAL applies to detect_sd on the real tree");
   int keys_cap = pow2ceil(algo == ALGO_SD ? 2 : p->K * (complex_tree ? P * P : P));
   if (algo == ALGO_HYBRID) {
     const int d = p->hybrid_depth;
@@ -301,16 +310,17 @@ mdx_status run_detect(int algo, mdx_ctx* c, const mdx_params* p, int batch, cons
   a.stats = dstats;
   e = cudaMemsetAsync(c->counter, 0, sizeof(unsigned int), s);
   if (e != cudaSuccess) return cuda_fail(c, e, "work counter reset");
-  if (algo == ALGO_SD && complex_tree) {
-    // complex-tree SD: the persistent warp-per-vector kernel on a uniform batch
+  if (algo == ALGO_SD && (complex_tree || natural)) {
+    // complex-tree or natural-order SD: the persistent warp-per-vector kernel on a uniform batch
+    const int malgo = complex_tree ? MIX_ALGO_SD_COMPLEX : MIX_ALGO_SD_NATURAL;
     MixedArgs m{};
     m.nreq = batch;
     m.uniform.n_rx = N;
     m.uniform.n_tx = M;
     m.uniform.n = n;
     m.uniform.P = P;
-    m.uniform.algo = MIX_ALGO_SD_COMPLEX;
-    m.uniform.mode = mixed_greedy_mode(MIX_ALGO_SD_COMPLEX, n, 0, P, c->mx_slice);
+    m.uniform.algo = malgo;
+    m.uniform.mode = mixed_greedy_mode(malgo, n, 0, P, c->mx_slice);
     m.uniform.radius_mode = radius_mode;
     m.uniform.radius_value = r0;
     m.uniform.alpha = a.alpha;
@@ -330,7 +340,7 @@ mdx_status run_detect(int algo, mdx_ctx* c, const mdx_params* p, int batch, cons
     m.metric_out = dmet;
     m.vstatus = dvst;
     m.stats = dstats;
-    m.gslot_bytes = (m.uniform.mode & MIX_STATE_SMEM) ? 16 : mixed_state_bytes(MIX_ALGO_SD_COMPLEX, n, 0, P);
+    m.gslot_bytes = (m.uniform.mode & MIX_STATE_SMEM) ? 16 : mixed_state_bytes(malgo, n, 0, P);
     const int warps = mixed_resident_warps(c->mx_W, c->mx_slice, 0, c->num_sms);
     if (warps < 1) return fail(c, MDX_EUNSUPPORTED, "no launch configuration fits this size");
     const size_t sbytes = (size_t)warps * m.gslot_bytes;
@@ -359,6 +369,9 @@ mdx_status run_detect(int algo, mdx_ctx* c, const mdx_params* p, int batch, cons
   else if (algo == ALGO_KBEST) {
     if (ev) cudaEventRecord(ev[1], s);
     e = launch_kbest(a, c->num_sms, s);
+  } else if (algo == ALGO_LINEAR) {
+    if (ev) cudaEventRecord(ev[1], s);
+    e = launch_linear(a, mmse, c->num_sms, s);
   } else {
     if (ev) cudaEventRecord(ev[1], s);
     e = launch_hybrid(a, c->num_sms, s);
@@ -413,8 +426,9 @@ mdx_status check_request(mdx_ctx* c, int r, const mdx_request& q) {
     return fail(c, MDX_EUNSUPPORTED, "request %d: %dx%d exceeds the context's %dx%d", r, q.n_rx, q.n_tx, c->max_rx,
                 c->max_tx);
   if (pam_of(q.qam) < 0) return fail(c, MDX_EINVAL, "request %d: qam %d not in {4, 16, 64}", r, q.qam);
-  if (q.algo != MDX_ALGO_SD && q.algo != MDX_ALGO_KBEST && q.algo != MDX_ALGO_SD_COMPLEX)
-    return fail(c, MDX_EINVAL, "request %d: algo %d is not MDX_ALGO_SD, _KBEST or _SD_COMPLEX", r, q.algo);
+  if (q.algo != MDX_ALGO_SD && q.algo != MDX_ALGO_KBEST && q.algo != MDX_ALGO_SD_COMPLEX &&
+      q.algo != MDX_ALGO_SD_NATURAL)
+    return fail(c, MDX_EINVAL, "request %d: algo %d is not an MDX_ALGO_* detector", r, q.algo);
   if (q.algo == MDX_ALGO_KBEST && (q.K < 1 || q.K > MDX_MAX_K))
     return fail(c, MDX_EINVAL, "request %d: K %d not in 1..%d", r, q.K, MDX_MAX_K);
   if (isnan(q.init_radius_sq) || q.init_radius_sq == 0.0)
@@ -973,6 +987,12 @@ mdx_status detect_hybrid(mdx_ctx* ctx, const mdx_params* p, int batch, const dou
                          double* metric_out, int32_t* vstatus, int64_t* stats, void* stream) {
   return run_detect(ALGO_HYBRID, ctx, p, batch, H, y, noise_var, sym_out, metric_out, vstatus, stats,
                     stream);
+}
+
+mdx_status detect_linear(mdx_ctx* ctx, const mdx_params* p, int batch, const double* H, const double* y,
+                         const double* noise_var, uint8_t* sym_out, double* metric_out, int32_t* vstatus,
+                         int64_t* stats, void* stream) {
+  return run_detect(ALGO_LINEAR, ctx, p, batch, H, y, noise_var, sym_out, metric_out, vstatus, stats, stream);
 }
 
 mdx_status detect_mixed(mdx_ctx* ctx, int nreq, const mdx_request* reqs, const double* H, const double* y,

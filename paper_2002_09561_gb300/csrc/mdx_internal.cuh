@@ -93,7 +93,7 @@ struct MixedReq {
 // otherwise each is read from / kept in global memory
 enum { MIX_STAGE_R = 1, MIX_STATE_SMEM = 2 };
 // detector of a request (MDX_ALGO_SD / MDX_ALGO_KBEST, or the complex-tree SD)
-enum { MIX_ALGO_SD_COMPLEX = 2 };
+enum { MIX_ALGO_SD_COMPLEX = 2, MIX_ALGO_SD_NATURAL = 3 };
 
 cudaError_t launch_qr_gather(int count, int n_rx, int n_tx, const int* ids, const MixedReq* reqs,
                              const double* H, const double* y, QrOut out, cudaStream_t s);
@@ -144,6 +144,9 @@ size_t sd_vec_state_bytes(int n);
 cudaError_t launch_sd(const SearchArgs& a, const SdWorkspace& w, int num_sms, cudaStream_t s);
 cudaError_t launch_kbest(const SearchArgs& a, int num_sms, cudaStream_t s);
 cudaError_t launch_hybrid(const SearchArgs& a, int num_sms, cudaStream_t s);
+// Linear detectors (linear.cu): ZF or MMSE on the QR workspace.
+size_t linear_smem_bytes(int n, bool mmse);
+cudaError_t launch_linear(const SearchArgs& a, bool mmse, int num_sms, cudaStream_t s);
 // Shared memory the hybrid needs for (n, K, P, depth), or (size_t)-1 if it does not fit.
 size_t hybrid_smem_bytes(int n, int K, int P, int depth);
 // Learned radius model (mlp.cu).

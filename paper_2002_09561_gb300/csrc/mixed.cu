@@ -126,7 +126,10 @@ __device__ void finish_request(const MixedArgs& g, const MixedReq& q, int r, con
 }
 
 // Exact SD of one request by one warp (ROWS = rows per lane, n <= 32 ROWS).
-template <int ROWS>
+// NAT: children in natural index order (the unsorted depth-first search the
+// paper compares against, Sec. IV-A) instead of Schnorr-Euchner order; a
+// child outside the sphere then does not end its level.
+template <int ROWS, bool NAT>
 __device__ void sd_request(const MixedArgs& g, const MixedReq& q, int r, const float* Rc, const float* yb,
                            unsigned char* st, float E, int lane) {
   const int n = q.n, P = q.P, n4 = round_up(n, 4);
@@ -167,13 +170,15 @@ __device__ void sd_request(const MixedArgs& g, const MixedReq& q, int r, const f
     float c = zs[col_off(i) + i];
     float rii = lv_rii[i];
     float u = fmaf(c, lv_rinv[i], uoff);
-    int lo = min(max((int)ceilf(u - 0.5f), 0), P - 1);
-    int hi = lo + 1;
+    int lo = NAT ? 0 : min(max((int)ceilf(u - 0.5f), 0), P - 1);
+    int hi = NAT ? P : lo + 1;
     ++nodes;
     flops += 4 * P;
     for (;;) {
       int k = -1;
-      if (lo >= 0 || hi < P) {
+      if (NAT) {
+        if (lo < P) k = lo++;
+      } else if (lo >= 0 || hi < P) {
         if (hi >= P || (lo >= 0 && fabsf(u - (float)lo) <= fabsf((float)hi - u))) k = lo--;
         else k = hi++;
       }
@@ -183,6 +188,7 @@ __device__ void sd_request(const MixedArgs& g, const MixedReq& q, int r, const f
         ped = fmaf(d, d, ped_par);
         ++peds;
       }
+      if (NAT && k >= 0 && !(ped < bnd)) continue;  // unsorted: try the next child
       if (k < 0 || !(ped < bnd)) {
         if (i == n - 1) break;  // the root is exhausted
         ++i;                    // backtrack
@@ -258,8 +264,8 @@ __device__ void sd_request(const MixedArgs& g, const MixedReq& q, int r, const f
       ped_par = ped;
       rii = lv_rii[i];
       u = fmaf(c, lv_rinv[i], uoff);
-      lo = min(max((int)ceilf(u - 0.5f), 0), P - 1);
-      hi = lo + 1;
+      lo = NAT ? 0 : min(max((int)ceilf(u - 0.5f), 0), P - 1);
+      hi = NAT ? P : lo + 1;
       ++nodes;
       flops += 2 * (n - 1 - i) + 4 * P;
     }
@@ -532,10 +538,15 @@ __global__ void mixed_kernel(MixedArgs g) {
     __syncwarp();
     const float E = error_scale_warp(q.n, q.P, q.alpha, Rc, yb, lane);
     if (q.algo == MDX_ALGO_SD) {
-      if (q.n <= 32) sd_request<1>(g, q, r, Rc, yb, st, E, lane);
-      else if (q.n <= 64) sd_request<2>(g, q, r, Rc, yb, st, E, lane);
-      else if (q.n <= 128) sd_request<4>(g, q, r, Rc, yb, st, E, lane);
-      else sd_request<7>(g, q, r, Rc, yb, st, E, lane);
+      if (q.n <= 32) sd_request<1, false>(g, q, r, Rc, yb, st, E, lane);
+      else if (q.n <= 64) sd_request<2, false>(g, q, r, Rc, yb, st, E, lane);
+      else if (q.n <= 128) sd_request<4, false>(g, q, r, Rc, yb, st, E, lane);
+      else sd_request<7, false>(g, q, r, Rc, yb, st, E, lane);
+    } else if (q.algo == MIX_ALGO_SD_NATURAL) {
+      if (q.n <= 32) sd_request<1, true>(g, q, r, Rc, yb, st, E, lane);
+      else if (q.n <= 64) sd_request<2, true>(g, q, r, Rc, yb, st, E, lane);
+      else if (q.n <= 128) sd_request<4, true>(g, q, r, Rc, yb, st, E, lane);
+      else sd_request<7, true>(g, q, r, Rc, yb, st, E, lane);
     } else if (q.algo == MIX_ALGO_SD_COMPLEX) {
       if (q.n <= 32) sdc_request<1>(g, q, r, Rc, yb, st, E, lane);
       else if (q.n <= 64) sdc_request<2>(g, q, r, Rc, yb, st, E, lane);
@@ -572,7 +583,7 @@ size_t mixed_stage_bytes(int n) { return stage_bytes(n); }
 
 size_t mixed_state_bytes(int algo, int n, int K, int P) {
   (void)P;
-  if (algo == MDX_ALGO_SD) return sd_state_bytes(n);
+  if (algo == MDX_ALGO_SD || algo == MIX_ALGO_SD_NATURAL) return sd_state_bytes(n);
   if (algo == MIX_ALGO_SD_COMPLEX) return sdc_state_bytes(n);
   return kb_state_bytes(n, K);
 }

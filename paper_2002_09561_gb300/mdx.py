@@ -22,8 +22,10 @@ MDX_V_OK, MDX_V_EMPTY_RETRIED, MDX_V_BUDGET_EXCEEDED, MDX_V_SINGULAR = 0, 1, 2, 
 MDX_HOST_BUFFERS, MDX_NO_RESCORE, MDX_LEARNED_RADIUS, MDX_SEQUENTIAL_SEARCH = 1, 2, 4, 8
 MDX_LEARNED_ORDER = 1 << 5
 MDX_COMPLEX_TREE = 1 << 6
+MDX_ORDER_NATURAL = 1 << 7
+MDX_LINEAR_MMSE = 1 << 8
 MDX_MAX_TX, MDX_MAX_RX, MDX_MAX_K = 100, 128, 256
-MDX_ALGO_SD, MDX_ALGO_KBEST, MDX_ALGO_SD_COMPLEX = 0, 1, 2
+MDX_ALGO_SD, MDX_ALGO_KBEST, MDX_ALGO_SD_COMPLEX, MDX_ALGO_SD_NATURAL = 0, 1, 2, 3
 MDX_GRAPH = 1 << 4
 
 # Every symbol the header declares; the library must export all of them.
@@ -31,7 +33,7 @@ EXPORTS = ["mdx_create", "mdx_destroy", "mdx_strerror", "mdx_last_error", "mdx_w
            "mdx_qr", "detect_sd", "detect_kbest", "detect_hybrid", "mdx_count_errors",
            "mdx_profile", "mdx_profile_read", "detect_kbest_noalloc", "mdx_mlp_param_count",
            "mdx_mlp_dims", "mdx_mlp_init", "mdx_mlp_set_params", "mdx_mlp_get_params", "mdx_mlp_predict",
-           "mdx_mlp_train_step", "mdx_mlp_error", "detect_mixed", "mdx_autotune_mixed"]
+           "mdx_mlp_train_step", "mdx_mlp_error", "detect_mixed", "mdx_autotune_mixed", "detect_linear"]
 NOALLOC_SCRATCH_BYTES = 16 << 20
 STATS = 5  # per-vector stats: nodes, peds, restarts, rescored, algorithmic FP32 flops
 
@@ -89,7 +91,7 @@ def lib():
             L.mdx_workspace_bytes.restype = ctypes.c_size_t
             L.mdx_qr.argtypes = [vp, i, i, i, vp, vp, vp, vp, i, vp]
             L.mdx_qr.restype = i
-            for name in ("detect_sd", "detect_kbest", "detect_hybrid"):
+            for name in ("detect_sd", "detect_kbest", "detect_hybrid", "detect_linear"):
                 f = getattr(L, name)
                 f.argtypes = [vp, ctypes.POINTER(Params), i, vp, vp, vp, vp, vp, vp, vp, vp]
                 f.restype = i
