@@ -58,6 +58,13 @@ WORKLOADS = {
                                            complex=True),
     "16x16-64qam-kbest32-complex": dict(n=16, qam=64, snr=[16.0, 20.0, 24.0, 28.0], vectors=100_000,
                                         detector="kbest", radius=math.inf, K=32, depth=0, complex=True),
+    # the paper's controls: unsorted depth-first SD and the linear detectors
+    "16x16-16qam-sd-natural": dict(n=16, qam=16, snr=[18.0, 20.0], vectors=100_000, detector="sd",
+                                   radius="paper", K=0, depth=0, natural=True),
+    "16x16-16qam-zf": dict(n=16, qam=16, snr=SWEEP_16, vectors=100_000, detector="linear", radius=math.inf,
+                           K=0, depth=0),
+    "16x16-16qam-mmse": dict(n=16, qam=16, snr=SWEEP_16, vectors=100_000, detector="linear", radius=math.inf,
+                             K=0, depth=0, mmse=True),
     # uneven batch: n_tx = n_rx in {8, 16, 32, 64, 100}, {4, 16, 64}-QAM, SNR U(6, 30) dB,
     # half exact SD (paper radius, node budget) and half K-best K=64, one detect_mixed call
     "mixed-50k": dict(mixed=True, n=100, qam=64, antennas=(8, 16, 32, 64, 100), qams=(4, 16, 64),
@@ -222,14 +229,20 @@ def cpu_baseline(w, seed, target_s, start_offset):
         return cpu_baseline_mixed(w, seed, target_s)
     cores = oracle.max_threads()
     algo = w["detector"] + ("_complex" if w.get("complex") else "")
+    if algo == "linear":
+        cores = 1  # numpy, one thread
     done = 0
     t0 = time.perf_counter()
     chunk = max(cores, 16)
     pos = start_offset
     while time.perf_counter() - t0 < target_s and done < w["vectors"]:
         d = generate(w, seed, chunk, start=pos)
-        oracle.detect_batch(algo, d["H"], d["y"], d["noise_var"], w["qam"], radius=w["radius"],
-                            K=max(w["K"], 1), depth=w["depth"])
+        if algo == "linear":
+            oracle.detect_linear("mmse" if w.get("mmse") else "zf", d["H"], d["y"], d["noise_var"], w["qam"])
+        else:
+            oracle.detect_batch(algo, d["H"], d["y"], d["noise_var"], w["qam"], radius=w["radius"],
+                                K=max(w["K"], 1), depth=w["depth"],
+                                order="natural" if w.get("natural") else "se")
         done += chunk
         pos += chunk
     dt = time.perf_counter() - t0
@@ -272,7 +285,9 @@ def config_of(args, w, world):
                 "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
                 "l2": "inputs larger than L2 (no flush)"}
     return {"workload": args.workload, "n_tx": w["n"], "n_rx": w["n"], "qam": w["qam"],
-            "detector": w["detector"] + (" (complex tree)" if w.get("complex") else ""), "K": w["K"] or None, "hybrid_depth": w["depth"] or None,
+            "detector": w["detector"] + (" (complex tree)" if w.get("complex") else "")
+            + (" (natural child order)" if w.get("natural") else "") + (" MMSE" if w.get("mmse") else "")
+            + (" ZF" if w["detector"] == "linear" and not w.get("mmse") else ""), "K": w["K"] or None, "hybrid_depth": w["depth"] or None,
             "initial_radius": "r^2 = N M sigma^2" if w["radius"] == "paper" else "none",
             "snr_db": w["snr"], "vectors_per_step_per_gpu": w["vectors"], "global_batch": w["vectors"] * world,
             "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
@@ -334,6 +349,10 @@ def main():
     flags = (mdx.MDX_LEARNED_RADIUS | mdx.MDX_LEARNED_ORDER) if learned else 0
     if w.get("complex"):
         flags |= mdx.MDX_COMPLEX_TREE
+    if w.get("natural"):
+        flags |= mdx.MDX_ORDER_NATURAL
+    if w.get("mmse"):
+        flags |= mdx.MDX_LINEAR_MMSE
     params = mdx.make_params(n, n, qam, radius=w["radius"], K=max(w["K"], 1), depth=w["depth"], flags=flags)
     algo = w["detector"]
     out = mdx._outputs(B, n, dev, True)
