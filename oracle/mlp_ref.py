@@ -10,6 +10,10 @@ learned component; this follows the definition in include/mimo_detect.h:
 
 with t = log(d_ML / sigma^2) and k_br the ML PAM index of real row r
 (row 2j is Re s_j, index q // P; row 2j+1 is Im s_j, index q % P).
+Systems with n_tx > 32 use summary features instead (reduced_features):
+log R_ii, the Babai point's distance log(d_B / sigma^2) / 10,
+log(||ybar||^2 / (n sigma^2)) / 10 and SNR_dB / 30, and the radius head only
+(no cross-entropy term, n = 0 rows in loss_and_grad).
 Parity pinned: the backward pass is checked against central finite
 differences in tests/test_mlp_ref.py.
 """
@@ -74,14 +78,16 @@ def loss_and_grad(p, X, t, krow, d_in, d_out, n, P, round_hidden=None):
     lp = np.mean(np.where(e >= 0.0, TAU * e, (TAU - 1.0) * e))
     do = np.zeros_like(o)
     do[:, 0] = np.where(e > 0.0, -TAU, 1.0 - TAU) / B
-    lg = o[:, 1:1 + n * P].reshape(B, n, P)
-    lg = lg - lg.max(axis=2, keepdims=True)
-    pr = np.exp(lg)
-    pr /= pr.sum(axis=2, keepdims=True)
-    onehot = np.zeros_like(pr)
-    np.put_along_axis(onehot, krow[:, :, None], 1.0, axis=2)
-    lc = -np.mean(np.sum(onehot * np.log(np.maximum(pr, 1e-300)), axis=2))
-    do[:, 1:1 + n * P] = (LAMBDA * (pr - onehot) / (B * n)).reshape(B, n * P)
+    lc = 0.0
+    if n > 0:
+        lg = o[:, 1:1 + n * P].reshape(B, n, P)
+        lg = lg - lg.max(axis=2, keepdims=True)
+        pr = np.exp(lg)
+        pr /= pr.sum(axis=2, keepdims=True)
+        onehot = np.zeros_like(pr)
+        np.put_along_axis(onehot, krow[:, :, None], 1.0, axis=2)
+        lc = -np.mean(np.sum(onehot * np.log(np.maximum(pr, 1e-300)), axis=2))
+        do[:, 1:1 + n * P] = (LAMBDA * (pr - onehot) / (B * n)).reshape(B, n * P)
     dW3 = do.T @ h2
     db3 = do.sum(axis=0)
     dh2 = (do @ W3) * (h2 > 0)
@@ -99,3 +105,28 @@ def bf16(a):
     u = f.view(np.uint32).astype(np.uint64)
     r = ((u + 0x7FFF + ((u >> 16) & 1)) >> 16) << 16
     return r.astype(np.uint32).view(np.float32).astype(np.float64)
+
+
+def reduced_features(R, ybar, noise_var, qam, d_in):
+    """Summary features of one system from its QR (R row-major n x n, ybar):
+    [log R_ii (n), log(d_B / sigma^2) / 10, log(||ybar||^2 / (n sigma^2)) / 10,
+    SNR_dB / 30], zero-padded to d_in.  d_B is the distance of the Babai
+    point: rows from the top, each rounded to the nearest PAM level (clipped)
+    given the rows above."""
+    R, ybar = np.asarray(R, dtype=np.float64), np.asarray(ybar, dtype=np.float64)
+    n = R.shape[0]
+    P = int(round(qam ** 0.5))
+    alpha = np.sqrt(3.0 / (2.0 * (qam - 1)))
+    x = np.zeros(n)
+    db = 0.0
+    for i in range(n - 1, -1, -1):
+        c = ybar[i] - R[i, i + 1:] @ x[i + 1:]
+        k = min(max(np.floor(c / (2.0 * alpha * R[i, i]) + 0.5 * (P - 1) + 0.5), 0), P - 1)
+        x[i] = (2.0 * k - (P - 1)) * alpha
+        db += (c - R[i, i] * x[i]) ** 2
+    f = np.zeros(d_in)
+    f[:n] = np.log(np.diag(R))
+    f[n] = np.log(db / noise_var) / 10.0
+    f[n + 1] = np.log(ybar @ ybar / (n * noise_var)) / 10.0
+    f[n + 2] = -10.0 * np.log10(noise_var) / 30.0
+    return f
