@@ -47,6 +47,8 @@ WORKLOADS = {
                                  radius=math.inf, K=256, depth=0),
     "100x100-64qam-hybrid32": dict(n=100, qam=64, snr=[20.0, 24.0, 28.0, 32.0], vectors=10_000,
                                    detector="hybrid", radius="paper", K=32, depth=4),
+    "100x100-64qam-hybrid32-learned": dict(n=100, qam=64, snr=[20.0, 24.0, 28.0, 32.0], vectors=10_000,
+                                           detector="hybrid", radius="paper", K=32, depth=4, learned=True),
     "100x100-64qam-hybrid128": dict(n=100, qam=64, snr=[20.0, 24.0, 28.0, 32.0], vectors=10_000,
                                     detector="hybrid", radius="paper", K=128, depth=4),
     # complex tree (one level per complex antenna, Q children): exact SD with the
@@ -346,7 +348,10 @@ def main():
         from paper_2002_09561_gb300 import train
 
         model_meta = train.load_model(ctx, n, qam)
-    flags = (mdx.MDX_LEARNED_RADIUS | mdx.MDX_LEARNED_ORDER) if learned else 0
+    flags = 0
+    if learned:
+        # the ordering head exists for models with full features (detect_sd)
+        flags = mdx.MDX_LEARNED_RADIUS | (mdx.MDX_LEARNED_ORDER if w["detector"] == "sd" else 0)
     if w.get("complex"):
         flags |= mdx.MDX_COMPLEX_TREE
     if w.get("natural"):

@@ -270,7 +270,14 @@ mdx_status mdx_count_errors(mdx_ctx* ctx, int batch, int n_tx, int qam, const ui
  * with MDX_LEARNED_ORDER the logits' top-ranked leaf caps that radius.
  * Parameter vector (FP32, this order): W1 [256][d_in], b1 [256],
  * W2 [256][256], b2 [256], W3 [d_out][256], b3 [d_out].
- * Models exist for square systems n_rx = n_tx <= 32. */
+ * Models are for square systems n_rx = n_tx.  Above n_tx = 32 the input is a
+ * summary of the system instead (d_in = round_up(n + 3, 64), d_out = 128):
+ * [log R_ii (n), log(d_B / sigma^2) / 10 with d_B the distance of the
+ * Babai point, log(||ybar||^2 / (n sigma^2)) / 10, SNR_dB / 30]; such a
+ * model has the radius head only (trained on any detector's answer metric,
+ * e.g. the hybrid's) and serves MDX_LEARNED_RADIUS in detect_sd and
+ * detect_hybrid (whose answer is likewise unchanged: a radius below the
+ * answer's distance empties the sphere and is doubled). */
 size_t mdx_mlp_param_count(int n_tx, int qam);
 mdx_status mdx_mlp_dims(int n_tx, int qam, int* d_in, int* d_out);
 /* Create (or replace) the context's model for n_tx x n_tx, qam, with a
@@ -286,9 +293,10 @@ mdx_status mdx_mlp_get_params(mdx_ctx* ctx, float* params, size_t count);
  * (the features before BF16 rounding) or NULL. */
 mdx_status mdx_mlp_predict(mdx_ctx* ctx, const mdx_params* p, int batch, const double* H, const double* y,
                            const double* noise_var, float* out, float* feat_out, void* stream);
-/* One training step on `batch` vectors with their ML targets (ml_sym
+/* One training step on `batch` vectors with their targets (ml_sym
  * uint8 [batch][n_tx] and ml_metric double [batch], as returned by
- * detect_sd): forward, loss, backward on the tensor cores; if `update`,
+ * detect_sd; ml_sym may be NULL for a summary model, whose target is the
+ * metric alone): forward, loss, backward on the tensor cores; if `update`,
  * one Adam step with learning rate lr (beta 0.9 / 0.999).  grad_out float
  * [param_count] receives the gradient and loss_out float [2] the batch's
  * (pinball, cross-entropy) losses; both device pointers or NULL. */

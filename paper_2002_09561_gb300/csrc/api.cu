@@ -185,11 +185,16 @@ mdx_status run_detect(int algo, mdx_ctx* c, const mdx_params* p, int batch, cons
   const bool learned = (p->flags & MDX_LEARNED_RADIUS) != 0;
   const bool order = (p->flags & MDX_LEARNED_ORDER) != 0;
   if (learned || order) {
-    if (algo != ALGO_SD) return fail(c, MDX_EUNSUPPORTED, "MDX_LEARNED_RADIUS / MDX_LEARNED_ORDER apply to detect_sd");
+    if (algo != ALGO_SD && !(algo == ALGO_HYBRID && !order))
+      return fail(c, MDX_EUNSUPPORTED, "MDX_LEARNED_RADIUS applies to detect_sd and detect_hybrid, "
+                                      "MDX_LEARNED_ORDER to detect_sd");
     if (!c->mlp || mlp_ntx(c->mlp) != M || mlp_qam(c->mlp) != p->qam || N != M)
       return fail(c, MDX_EUNSUPPORTED, "the learned radius / order needs a model for this %dx%d %d-QAM (mdx_mlp_init)",
                   N, M, p->qam);
     if (!nv) return fail(c, MDX_EINVAL, "noise_var needed for the learned radius / order (network input)");
+    if (order && mlp_reduced(c->mlp))
+      return fail(c, MDX_EUNSUPPORTED, "MDX_LEARNED_ORDER needs a model with the ordering head (n_tx <= %d)",
+                  kFullFeaturesMaxTx);
   }
   if (p->node_budget < 0) return fail(c, MDX_EINVAL, "node_budget < 0");
   const bool mmse = (p->flags & MDX_LINEAR_MMSE) != 0;
@@ -1057,8 +1062,8 @@ mdx_status mdx_mlp_dims(int n_tx, int qam, int* d_in, int* d_out) {
 
 mdx_status mdx_mlp_init(mdx_ctx* c, int n_tx, int qam, int max_train_batch, unsigned long long seed) {
   if (!c) return MDX_EINVAL;
-  if (n_tx < 1 || n_tx > c->max_tx || n_tx > 32 || pam_of(qam) < 0)
-    return fail(c, MDX_EINVAL, "the learned radius supports n_tx <= 32 within the context");
+  if (n_tx < 1 || n_tx > c->max_tx || pam_of(qam) < 0)
+    return fail(c, MDX_EINVAL, "model size n_tx %d, qam %d not within the context", n_tx, qam);
   if (max_train_batch < 0) return fail(c, MDX_EINVAL, "max_train_batch < 0");
   DeviceGuard g(c->device);
   if (c->mlp) {
@@ -1078,7 +1083,8 @@ mdx_status mdx_mlp_init(mdx_ctx* c, int n_tx, int qam, int max_train_batch, unsi
   int D0, DO;
   mlp_dims(n_tx, qam, &D0, &DO);
   const int n = 2 * n_tx, P = pam_of(qam);
-  const int din = n * (n + 1) / 2 + n + 1, dout = 1 + n * P;
+  const bool reduced = n_tx > kFullFeaturesMaxTx;
+  const int din = reduced ? n + 3 : n * (n + 1) / 2 + n + 1, dout = reduced ? 1 : 1 + n * P;
   const long long cnt = mlp_count(n_tx, qam);
   float* h = new float[cnt]();
   uint64_t st = seed * 0x9E3779B97F4A7C15ull + 0x5DEECE66Dull;
@@ -1181,8 +1187,10 @@ mdx_status mdx_mlp_train_step(mdx_ctx* c, const mdx_params* p, int batch, const 
                               const double* nv, const uint8_t* ml_sym, const double* ml_metric, float lr,
                               int update, float* grad_out, float* loss_out, void* stream) {
   if (!c) return MDX_EINVAL;
-  if (!ml_sym || !ml_metric) return fail(c, MDX_EINVAL, "NULL targets");
-  if (!is_device_ptr(ml_sym, c->device) || !is_device_ptr(ml_metric, c->device))
+  if (!c->mlp) return fail(c, MDX_EUNSUPPORTED, "no model (mdx_mlp_init)");
+  const bool need_sym = !mlp_reduced(c->mlp);
+  if (!ml_metric || (need_sym && !ml_sym)) return fail(c, MDX_EINVAL, "NULL targets");
+  if ((ml_sym && !is_device_ptr(ml_sym, c->device)) || !is_device_ptr(ml_metric, c->device))
     return fail(c, MDX_EINVAL, "targets must be device memory");
   if (!(lr >= 0.0f)) return fail(c, MDX_EINVAL, "learning rate");
   DeviceGuard g(c->device);

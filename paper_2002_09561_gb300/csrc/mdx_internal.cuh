@@ -149,7 +149,10 @@ size_t linear_smem_bytes(int n, bool mmse);
 cudaError_t launch_linear(const SearchArgs& a, bool mmse, int num_sms, cudaStream_t s);
 // Shared memory the hybrid needs for (n, K, P, depth), or (size_t)-1 if it does not fit.
 size_t hybrid_smem_bytes(int n, int K, int P, int depth);
-// Learned radius model (mlp.cu).
+// Learned radius model (mlp.cu).  Systems with n_tx <= kFullFeaturesMaxTx use
+// the full features (R's upper triangle, ybar, SNR) and both heads; larger
+// ones summary features and the radius head only.
+constexpr int kFullFeaturesMaxTx = 32;
 struct MlpState;
 void mlp_dims(int n_tx, int qam, int* D0, int* DO);
 long long mlp_count(int n_tx, int qam);
@@ -176,6 +179,7 @@ int* mlp_err(MlpState* s);
 int mlp_cap(MlpState* s);
 int mlp_ntx(MlpState* s);
 int mlp_qam(MlpState* s);
+bool mlp_reduced(MlpState* s);
 size_t mlp_bytes(MlpState* s);
 
 cudaError_t launch_count_errors(int batch, int n_tx, int qam, const uint8_t* a, const uint8_t* b,

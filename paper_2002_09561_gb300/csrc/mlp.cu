@@ -374,9 +374,69 @@ __global__ void mlp_features_kernel(int batch, int rows, int n, int D0, const fl
 
 // One warp per vector: pinball loss on o[0] (target log(d_ML / sigma^2)) and
 // cross-entropy of every row's ML PAM index; writes dL/do (BF16, both layouts).
+// Summary features of a large system (n_tx > 32), one warp per vector: log R_ii
+// (n values), log(d_B / sigma^2) / 10 with d_B the FP32 distance of the Babai
+// point (successive rounding, top row first, clipped to the PAM grid),
+// log(||ybar||^2 / (n sigma^2)) / 10 and SNR_dB / 30; zero-padded to D0.
+__global__ void reduced_features_kernel(int batch, int rows, int n, int P, float alpha, int D0,
+                                        const float* __restrict__ R32, const float* __restrict__ yb32,
+                                        const double* __restrict__ nv, __nv_bfloat16* X, __nv_bfloat16* Xt,
+                                        float* F) {
+  const int lane = threadIdx.x & 31;
+  const int w0 = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, nw = (gridDim.x * blockDim.x) >> 5;
+  const int ts = tri_stride32(n), vs = vec_stride32(n);
+  for (int v = w0; v < rows; v += nw) {
+    float db = 0.0f, ybn = 0.0f, s2 = 1.0f;
+    const float* R = R32 + (size_t)v * ts;
+    if (v < batch) {
+      const float* yb = yb32 + (size_t)v * vs;
+      s2 = (float)nv[v];
+      float z[7];
+#pragma unroll
+      for (int t = 0; t < 7; ++t) {
+        const int r = lane + 32 * t;
+        z[t] = (r < n) ? yb[r] : 0.0f;
+        ybn = fmaf(z[t], z[t], ybn);
+      }
+      ybn = warp_sum(ybn);
+      for (int i = n - 1; i >= 0; --i) {
+        float zi = 0.0f;
+#pragma unroll
+        for (int t = 0; t < 7; ++t)
+          if (t == (i >> 5)) zi = z[t];
+        const float c = __shfl_sync(0xffffffffu, zi, i & 31);
+        const float rii = R[col_off(i) + i];
+        const float u = c / (2.0f * alpha * rii) + 0.5f * (float)(P - 1);
+        const float k = fminf(fmaxf(floorf(u + 0.5f), 0.0f), (float)(P - 1));
+        const float a = (2.0f * k - (float)(P - 1)) * alpha;
+        const float d = fmaf(-rii, a, c);
+        db = fmaf(d, d, db);
+#pragma unroll
+        for (int t = 0; t < 7; ++t) {
+          const int r = lane + 32 * t;
+          if (r < i) z[t] = fmaf(-R[col_off(i) + r], a, z[t]);
+        }
+      }
+    }
+    for (int f = lane; f < D0; f += 32) {
+      float x = 0.0f;
+      if (v < batch) {
+        if (f < n) x = logf(R[col_off(f) + f]);
+        else if (f == n) x = logf(fmaxf(db, 1e-30f) / s2) / 10.0f;
+        else if (f == n + 1) x = logf(fmaxf(ybn, 1e-30f) / ((float)n * s2)) / 10.0f;
+        else if (f == n + 2) x = (float)(-10.0 * log10(nv[v]) / 30.0);
+      }
+      const __nv_bfloat16 b = __float2bfloat16(x);
+      X[(size_t)v * D0 + f] = b;
+      if (Xt) Xt[(size_t)f * rows + v] = b;
+      if (F && v < batch) F[(size_t)v * D0 + f] = x;
+    }
+  }
+}
+
 __global__ void mlp_loss_kernel(int batch, int rows, int n, int P, int n_tx, int DO, const float* __restrict__ O,
                                 const double* __restrict__ ml_metric, const double* __restrict__ nv,
-                                const uint8_t* __restrict__ ml_sym, float tau, float lambda,
+                                const uint8_t* __restrict__ ml_sym, float tau, float lambda, int ce_rows,
                                 __nv_bfloat16* dO, __nv_bfloat16* dOt, float* loss) {
   const int warps = blockDim.x / 32;
   const int v = blockIdx.x * warps + threadIdx.x / 32, lane = threadIdx.x & 31;
@@ -391,7 +451,7 @@ __global__ void mlp_loss_kernel(int batch, int rows, int n, int P, int n_tx, int
         const float e = t - O[(size_t)v * DO];
         lr = (e >= 0.0f ? tau * e : (tau - 1.0f) * e);
         g = (e > 0.0f ? -tau : (1.0f - tau)) * inv_b;
-      } else if (j < 1 + n * P) {
+      } else if (j < 1 + ce_rows * P) {
         const int r = (j - 1) / P, k = (j - 1) % P;
         const float* lg = O + (size_t)v * DO + 1 + r * P;
         float mx = lg[0];
@@ -524,6 +584,7 @@ int grid_for(long long total, int threads) {
 
 struct MlpState {
   int n = 0, P = 0, n_tx = 0, qam = 0, D0 = 0, DO = 0, cap = 0;
+  bool reduced = false;  // summary features (n_tx > 32), radius head only
   long long count = 0, step = 0;
   // FP32 master parameters, gradients, Adam moments (same layout)
   float *w = nullptr, *g = nullptr, *m = nullptr, *v = nullptr;
@@ -548,6 +609,11 @@ struct MlpState {
 void mlp_dims(int n_tx, int qam, int* D0, int* DO) {
   const int n = 2 * n_tx;
   const int P = qam == 4 ? 2 : qam == 16 ? 4 : 8;
+  if (n_tx > kFullFeaturesMaxTx) {
+    *D0 = round_up(n + 3, 64);
+    *DO = 128;
+    return;
+  }
   *D0 = round_up(n * (n + 1) / 2 + n + 1, 64);
   *DO = round_up(1 + n * P, 128);
 }
@@ -573,6 +639,7 @@ cudaError_t mlp_alloc(MlpState** out, int n_tx, int qam, int cap) {
   s->n_tx = n_tx;
   s->qam = qam;
   s->n = 2 * n_tx;
+  s->reduced = n_tx > kFullFeaturesMaxTx;
   s->P = qam == 4 ? 2 : qam == 16 ? 4 : 8;
   mlp_dims(n_tx, qam, &s->D0, &s->DO);
   s->cap = round_up(cap, 128);
@@ -633,6 +700,12 @@ cudaError_t mlp_pack(MlpState* s, cudaStream_t st) {
 // workspace) into s->X (and s->Xt when `train`), zero rows up to rows.
 cudaError_t mlp_features(MlpState* s, int batch, int rows, const float* R32, const float* yb32, const double* nv,
                          bool train, float* F, cudaStream_t st) {
+  if (s->reduced) {
+    const float alpha = (float)sqrt(3.0 / (2.0 * (s->qam - 1)));
+    reduced_features_kernel<<<grid_for((long long)rows * 32, 256), 256, 0, st>>>(
+        batch, rows, s->n, s->P, alpha, s->D0, R32, yb32, nv, s->X, train ? s->Xt : nullptr, F);
+    return cudaGetLastError();
+  }
   mlp_features_kernel<<<grid_for((long long)rows * s->D0, 256), 256, 0, st>>>(
       batch, rows, s->n, s->D0, R32, yb32, nv, s->X, train ? s->Xt : nullptr, F);
   return cudaGetLastError();
@@ -672,7 +745,8 @@ cudaError_t mlp_backward(MlpState* s, int batch, int rows, const double* ml_metr
   cudaError_t r = cudaMemsetAsync(s->loss, 0, 2 * sizeof(float), st);
   if (r != cudaSuccess) return r;
   mlp_loss_kernel<<<(rows + 7) / 8, 256, 0, st>>>(batch, rows, s->n, s->P, s->n_tx, s->DO, s->O, ml_metric, nv,
-                                                  ml_sym, 0.9f, 0.2f, s->dO, s->dOt, s->loss);
+                                                  ml_sym, 0.9f, 0.2f, s->reduced ? 0 : s->n, s->dO, s->dOt,
+                                                  s->loss);
   if ((r = cudaGetLastError()) != cudaSuccess) return r;
   TcEpi e{};
   e.err = s->err;
@@ -753,5 +827,6 @@ int* mlp_err(MlpState* s) { return s->err; }
 int mlp_cap(MlpState* s) { return s->cap; }
 int mlp_ntx(MlpState* s) { return s->n_tx; }
 int mlp_qam(MlpState* s) { return s->qam; }
+bool mlp_reduced(MlpState* s) { return s->reduced; }
 size_t mlp_bytes(MlpState* s) { return s->bytes; }
 }  // namespace mdx

@@ -189,3 +189,94 @@ def test_training_reduces_nodes(env):
           f"fallback {fallback:.3f}; learned radius + order {n_both:.0f}")
     assert n_learned < n_plain
     assert n_both <= n_learned * 1.02
+
+
+# ----------------------------------------------------------- summary-feature models (n_tx > 32)
+
+
+@pytest.fixture(scope="module")
+def big_env():
+    import torch
+
+    import __graft_entry__
+
+    __graft_entry__.build()
+    from paper_2002_09561_gb300 import mdx
+
+    ctx = mdx.Context(0, max_batch=2048, max_n_rx=100, max_n_tx=100)
+    yield torch, mdx, ctx
+    ctx.close()
+
+
+def test_summary_features_match_reference(big_env):
+    torch, mdx, ctx = big_env
+    n_tx, qam = 40, 16
+    mdx.mlp_init(ctx, n_tx, qam, max_train_batch=256, seed=3)
+    w = wl.generate(21, 64, n_tx, n_tx, qam, 14.0)
+    H, y, nv = _dev(torch, w)
+    params = mdx.make_params(n_tx, n_tx, qam)
+    out, feat = mdx.mlp_predict(ctx, params, H, y, nv, want_features=True)
+    torch.cuda.synchronize()
+    d_in, d_out = mdx.mlp_dims(n_tx, qam)
+    assert (d_in, d_out) == (128, 128)
+    Ro, ybo = oracle.qr_batch(w["H"], w["y"])
+    f = feat.cpu().numpy()
+    bad = 0
+    for b in range(64):
+        ref = mlp_ref.reduced_features(Ro[b], ybo[b], w["noise_var"][b], qam, d_in)
+        np.testing.assert_allclose(f[b, :2 * n_tx], ref[:2 * n_tx], atol=1e-5)
+        np.testing.assert_allclose(f[b, 2 * n_tx + 1:], ref[2 * n_tx + 1:], atol=1e-5)
+        # the Babai distance: FP32 rounding may flip a decision on a near-tie
+        bad += abs(f[b, 2 * n_tx] - ref[2 * n_tx]) > 1e-4
+    assert bad <= 2
+
+
+def test_summary_model_gradient_matches_reference(big_env):
+    torch, mdx, ctx = big_env
+    n_tx, qam, B = 40, 16, 512
+    mdx.mlp_init(ctx, n_tx, qam, max_train_batch=B, seed=4)
+    w = wl.generate(22, B, n_tx, n_tx, qam, 16.0)
+    H, y, nv = _dev(torch, w)
+    met = torch.from_numpy(w["noise_var"] * (2 * n_tx) * (1.0 + np.random.default_rng(1).random(B))).cuda()
+    params = mdx.make_params(n_tx, n_tx, qam)
+    _, feat = mdx.mlp_predict(ctx, params, H, y, nv, want_features=True)
+    loss, grad = mdx.mlp_train_step(ctx, params, H, y, nv, None, met, update=False, want_grad=True)
+    torch.cuda.synchronize()
+    assert mdx.mlp_error(ctx) == 0
+    d_in, d_out = mdx.mlp_dims(n_tx, qam)
+    p = mdx.mlp_get_params(ctx, n_tx, qam).astype(np.float64)
+    W1, b1, W2, b2, W3, b3 = mlp_ref.unpack(p, d_in, d_out)
+    pr = mlp_ref.pack(mlp_ref.bf16(W1), b1, mlp_ref.bf16(W2), b2, mlp_ref.bf16(W3), b3)
+    X = mlp_ref.bf16(feat.cpu().numpy().astype(np.float64))
+    t = np.log(met.cpu().numpy() / w["noise_var"])
+    lp, lc, gref = mlp_ref.loss_and_grad(pr, X, t, np.zeros((B, 0), dtype=np.int64), d_in, d_out, 0, 4,
+                                         round_hidden=mlp_ref.bf16)
+    g = grad.cpu().numpy().astype(np.float64)
+    cos = g @ gref / (np.linalg.norm(g) * np.linalg.norm(gref))
+    print(f"GRADCHECK summary model: cosine {cos:.6f}")
+    assert cos > 0.999 and lc == 0.0
+    assert float(loss[0]) == pytest.approx(lp, rel=2e-2)
+
+
+def test_learned_hybrid_keeps_the_answer(big_env):
+    """The trained 100x100 64-QAM model: the hybrid from the learned radius
+    (doubled on an empty sphere) returns the plain hybrid's decisions and
+    visits fewer nodes."""
+    torch, mdx, ctx = big_env
+    from paper_2002_09561_gb300 import train
+
+    meta = train.load_model(ctx, 100, 64)
+    assert meta.get("detector") == "hybrid"
+    w = wl.generate(23, 300, 100, 100, 64, 24.0)
+    H, y, nv = _dev(torch, w)
+    plain = mdx.detect("hybrid", ctx, mdx.make_params(100, 100, 64, radius="paper", K=32, depth=4), H, y, nv)
+    learned = mdx.detect("hybrid", ctx, mdx.make_params(100, 100, 64, radius="paper", K=32, depth=4,
+                                                        flags=mdx.MDX_LEARNED_RADIUS), H, y, nv)
+    torch.cuda.synchronize()
+    assert torch.equal(plain[0], learned[0])
+    npl, nle = plain[3][:, 0].double().sum().item(), learned[3][:, 0].double().sum().item()
+    print(f"HYBRID learned radius: nodes {npl:.0f} -> {nle:.0f}")
+    assert nle < npl
+    with pytest.raises(mdx.MdxError):  # no ordering head in a summary model
+        mdx.detect("sd", ctx, mdx.make_params(100, 100, 64, radius="paper", budget=100,
+                                             flags=mdx.MDX_LEARNED_ORDER), H, y, nv)
