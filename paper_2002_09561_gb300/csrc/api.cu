@@ -153,17 +153,6 @@ enum Algo { ALGO_SD = 0, ALGO_KBEST = 1, ALGO_HYBRID = 2, ALGO_LINEAR = 3 };
 // Task-queue slots of the sphere decoder (tasks exist only while warps are idle).
 constexpr unsigned int kSdQueueSlots = 1u << 16;
 
-size_t kbest_layout_bytes(int n, int K, int P, int keys_cap) {
-  // mirrors KbLayout::init in kbest.cu
-  int w = round_up(n, 4) / 4;
-  if ((w & 1) == 0) ++w;
-  const size_t pp = 4 * (size_t)w;
-  size_t o = sizeof(uint64_t) * keys_cap + sizeof(float) * tri_stride32(n) +
-             sizeof(float) * round_up(n, 4) + 2 * sizeof(float) * round_up(K, 4) +
-             sizeof(float) * 8 + 64 + pp * (2 * (size_t)K + 8);
-  return (size_t)round_up((int)o, 16);
-}
-
 mdx_status run_detect(int algo, mdx_ctx* c, const mdx_params* p, int batch, const double* H,
                       const double* y, const double* nv, uint8_t* sym, double* met, int32_t* vst,
                       int64_t* stats, void* stream) {
@@ -220,7 +209,7 @@ mdx_status run_detect(int algo, mdx_ctx* c, const mdx_params* p, int batch, cons
     if (np > 4096) return fail(c, MDX_EUNSUPPORTED, "P^depth = %lld > 4096 prefixes", np);
     keys_cap += pow2ceil(np < 2 ? 2 : (int)np);
   }
-  if (algo == ALGO_KBEST && kbest_layout_bytes(n, p->K, P, keys_cap) > 227 * 1024)
+  if (algo == ALGO_KBEST && kbest_smem_bytes(n, p->K, P, keys_cap) > 227 * 1024)
     return fail(c, MDX_EUNSUPPORTED, "K=%d at n=%d, P=%d needs more than 227 KB of shared memory", p->K,
                 n, P);
   if (algo == ALGO_HYBRID && hybrid_smem_bytes(n, p->K, P, p->hybrid_depth) == (size_t)-1)

@@ -33,7 +33,7 @@ namespace {
 
 struct KbLayout {
   int n, K, P, keys_cap, pp, ts;
-  size_t off_R, off_yb, off_keys, off_xa, off_xb, off_pa, off_pb, off_cx, off_cp, off_misc, bytes;
+  size_t off_R, off_yb, off_keys, off_xa, off_xb, off_pa, off_pb, off_cx, off_cp, off_cc, off_misc, bytes;
   __host__ __device__ void init(int n_, int K_, int P_, int keys_cap_) {
     n = n_;
     K = K_;
@@ -54,6 +54,8 @@ struct KbLayout {
     o += sizeof(float) * round_up(K, 4);
     off_cp = o;
     o += sizeof(float) * kCandMax;
+    off_cc = o;  // complex levels: the two rows' interference per survivor
+    o += 2 * sizeof(float) * round_up(K, 4);
     off_misc = o;
     o += 64;
     off_xa = o;
@@ -100,6 +102,7 @@ struct KbCtx {
   const float* yb;
   uint64_t* keys;
   int* misc;  // misc[0]: valid-candidate count
+  float* cc;  // complex levels: [2][K] interference of rows 2j+1 and 2j per survivor
 };
 
 // Runs the K-best level steps over rows top..0 from the S survivors in
@@ -125,7 +128,8 @@ __device__ int kbest_levels(const KbCtx& c, int top, int S, uint8_t** xcur, uint
         const float d = fmaf(-rii, (float)(2 * k - (P - 1)) * c.alpha, ci);
         const float ped = fmaf(d, d, p0);
         const unsigned id = (unsigned)(tid * P + k);
-        c.keys[tid * P + k] = (ped < bnd) ? (((uint64_t)__float_as_uint(ped) << 32) | id) : kInfKey;
+        // child-major slots: consecutive threads write consecutive keys
+        c.keys[k * S + tid] = (ped < bnd) ? (((uint64_t)__float_as_uint(ped) << 32) | id) : kInfKey;
       }
     }
     for (int q = SP + tid; q < Cs; q += T) c.keys[q] = kInfKey;
@@ -175,6 +179,7 @@ __device__ int kbest_levels_complex(const KbCtx& c, int S, uint8_t** xcur, uint8
     const float bnd = prune_bound(*r2s, E, n);
     const int SQ = S * Q;
     const int Cs = pow2ceil(SQ < 2 ? 2 : SQ);
+    // interference of both rows, one thread per survivor
     for (int t = tid; t < S; t += T) {
       const uint8_t* xp = *xcur + (size_t)t * pp;
       float c1 = c.yb[r1], c0 = c.yb[r0];
@@ -183,18 +188,22 @@ __device__ int kbest_levels_complex(const KbCtx& c, int S, uint8_t** xcur, uint8
         c1 = fmaf(-c.Rc[col_off(jj) + r1], a, c1);
         c0 = fmaf(-c.Rc[col_off(jj) + r0], a, c0);
       }
-      const float r11 = c.Rc[col_off(r1) + r1], r01 = c.Rc[col_off(r1) + r0], r00 = c.Rc[col_off(r0) + r0];
-      const float p0 = (*pcur)[t];
-      for (int q = 0; q < Q; ++q) {
-        const int kre = q / P, kim = q - kre * P;
-        const float aim = (float)(2 * kim - (P - 1)) * c.alpha, are = (float)(2 * kre - (P - 1)) * c.alpha;
-        const float d1 = fmaf(-r11, aim, c1);
-        const float p1 = fmaf(d1, d1, p0);
-        const float d0 = fmaf(-r00, are, fmaf(-r01, aim, c0));
-        const float pd = fmaf(d0, d0, p1);
-        const unsigned id = (unsigned)(t * Q + q);
-        c.keys[t * Q + q] = (pd < bnd) ? (((uint64_t)__float_as_uint(pd) << 32) | id) : kInfKey;
-      }
+      c.cc[t] = c1;
+      c.cc[K + t] = c0;
+    }
+    __syncthreads();
+    // the S Q children over all threads, child-major
+    const float r11 = c.Rc[col_off(r1) + r1], r01 = c.Rc[col_off(r1) + r0], r00 = c.Rc[col_off(r0) + r0];
+    for (int e = tid; e < SQ; e += T) {
+      const int q = e / S, t = e - q * S;
+      const int kre = q / P, kim = q - kre * P;
+      const float aim = (float)(2 * kim - (P - 1)) * c.alpha, are = (float)(2 * kre - (P - 1)) * c.alpha;
+      const float d1 = fmaf(-r11, aim, c.cc[t]);
+      const float p1 = fmaf(d1, d1, (*pcur)[t]);
+      const float d0 = fmaf(-r00, are, fmaf(-r01, aim, c.cc[K + t]));
+      const float pd = fmaf(d0, d0, p1);
+      const unsigned id = (unsigned)(t * Q + q);
+      c.keys[e] = (pd < bnd) ? (((uint64_t)__float_as_uint(pd) << 32) | id) : kInfKey;
     }
     for (int q = SQ + tid; q < Cs; q += T) c.keys[q] = kInfKey;
     if (tid == 0) c.misc[0] = 0;
@@ -336,7 +345,7 @@ __global__ void kbest_kernel(SearchArgs a, KbLayout L) {
   int* misc = reinterpret_cast<int*>(smem + L.off_misc);
   float* misc_f = reinterpret_cast<float*>(misc + 4);
   KbCtx c{n, P, a.K, L.pp, tid, T, a.alpha, reinterpret_cast<float*>(smem + L.off_R),
-          reinterpret_cast<float*>(smem + L.off_yb), keys, misc};
+          reinterpret_cast<float*>(smem + L.off_yb), keys, misc, reinterpret_cast<float*>(smem + L.off_cc)};
 
   for (;;) {
     if (tid == 0) misc[1] = (int)atomicAdd(a.work_counter, 1u);
@@ -686,6 +695,12 @@ cudaError_t launch_generic(const void* fn, const SearchArgs& a, const KbLayout& 
 }
 
 }  // namespace
+
+size_t kbest_smem_bytes(int n, int K, int P, int keys_cap) {
+  KbLayout L;
+  L.init(n, K, P, keys_cap);
+  return L.bytes;
+}
 
 cudaError_t launch_kbest(const SearchArgs& a, int num_sms, cudaStream_t s) {
   if (a.batch <= 0) return cudaSuccess;
