@@ -74,6 +74,12 @@ WORKLOADS = {
                       K=64, depth=0, budget=20_000),
 }
 METRIC = "decoded vectors/s at matched BER (16x16 16QAM, 100x100 64QAM), learned vs plain"
+# DRAM bytes (read + write) of the dominant kernel per vector, from one ncu
+# capture of the same kernel on a smaller run of the same workload (traffic
+# grows with the number of vectors); None where no capture of the current
+# kernel exists.  Source: profiles/sd_kernel_16x16_16qam_sweep_20k.md
+# (sd_kernel, 20,000 vectors: 154.1 MB read + 5.4 MB written).
+TRAFFIC_PER_VECTOR = {"16x16-16qam-sd-learned": (154.095616e6 + 5.353216e6) / 20000}
 FP32_LANES_PER_SM = 128  # FP32 FMA lanes per SM (4 sub-partitions x 32)
 
 
@@ -335,8 +341,11 @@ def main():
         main_mixed(args, w, rank, world, local, dev, dist, torch, mdx)
         return
 
+    from paper_2002_09561_gb300 import replicas
+
     B, n, qam = w["vectors"], w["n"], w["qam"]
-    data = generate(w, args.seed, B, start=rank * B)
+    start, _ = replicas.shard(rank, world, B)
+    data = generate(w, args.seed, B, start=start)
     H = torch.from_numpy(data["H"]).to(dev)
     y = torch.from_numpy(data["y"]).to(dev)
     nv = torch.from_numpy(data["noise_var"]).to(dev)
@@ -392,10 +401,7 @@ def main():
         el = e0.elapsed_time(e1)
         prof = ctx.profile_read()
         ctx.profile(False)
-        if dist is not None:
-            t = torch.tensor([el], device=dev, dtype=torch.float64)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            el = float(t.item())
+        el = replicas.max_over_ranks(el, dist, dev)
         return el, prof, errs, sampler
 
     ms, (qr_ms, search_ms, calls), errs, sampler = timed(params, out, args.steps, args.warmup)
@@ -416,9 +422,13 @@ def main():
 
     stats = out[3].cpu().numpy()
     vst = out[2].cpu().numpy()
-    bit_err, sym_err = (int(v) for v in errs.cpu().tolist())
     P = int(round(qam ** 0.5))
-    bits = B * n * 2 * int(round(math.log2(P)))
+    # whole-job counters (one sum-reduction over the ranks)
+    tot = replicas.sum_counters({"bit_errors": int(errs[0]), "symbol_errors": int(errs[1]),
+                                 "budget_exceeded": int((vst == 2).sum()), "radius_doublings": int((vst == 1).sum()),
+                                 "nodes": int(stats[:, 0].sum())}, dist, dev)
+    bit_err, sym_err = tot["bit_errors"], tot["symbol_errors"]
+    bits = B * world * n * 2 * int(round(math.log2(P)))
 
     # dominant kernel: the tree search; algorithmic FP32 flops per launch from the
     # kernel's own count, sum over branched nodes at row i of 2(n-1-i) + 4P
@@ -429,8 +439,10 @@ def main():
     flops = float(stats[:, 4].sum())
     per_launch_s = (search_ms / max(calls, 1)) / 1e3
     achieved = flops / per_launch_s / 1e12 if per_launch_s > 0 else 0.0
+    tpv = TRAFFIC_PER_VECTOR.get(args.workload)
     roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-            "traffic": None, "kernel": f"{algo} search", "search_ms_per_launch": 1e3 * per_launch_s,
+            "traffic": tpv * B if tpv else None, "traffic_unit": "bytes per launch (ncu capture, scaled by vectors)",
+            "kernel": f"{algo} search", "search_ms_per_launch": 1e3 * per_launch_s,
             "qr_ms_per_launch": qr_ms / max(calls, 1),
             "peak_source": f"derived: {sms} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 x {sm_max:.0f} MHz"}
 
@@ -449,11 +461,7 @@ def main():
         t0 = time.perf_counter()
         for _ in range(args.steps):
             mdx.detect_host(algo, ctx, params, hH, hy, hnv, hsym, hmet, hvst, stream=stream)
-        el = time.perf_counter() - t0
-        if dist is not None:
-            t = torch.tensor([el], device=dev, dtype=torch.float64)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            el = float(t.item())
+        el = replicas.max_over_ranks(time.perf_counter() - t0, dist, dev)
         e2e = {"value": B * world * args.steps / el, "unit": "vectors/s",
                "h2d_bytes_per_step": int(hH.nbytes + hy.nbytes + hnv.nbytes),
                "d2h_bytes_per_step": int(hsym.nbytes + hmet.nbytes + hvst.nbytes)}
@@ -474,9 +482,9 @@ def main():
                 "data": "synthetic (seeded Rayleigh channels, uniform QAM symbols, AWGN)",
                 "config": cfg, "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
                 "gpu_launches": (8 if learned else 3) * args.steps, "clocks": sampler.summary(), "plain": plain,
-                "quality": {"ber": bit_err / bits, "ser": sym_err / (B * n),
-                            "budget_exceeded": int((vst == 2).sum()), "radius_doublings": int((vst == 1).sum()),
-                            "mean_nodes": float(stats[:, 0].mean()), "max_nodes": int(stats[:, 0].max())}}
+                "quality": {"ber": bit_err / bits, "ser": sym_err / (B * world * n),
+                            "budget_exceeded": tot["budget_exceeded"], "radius_doublings": tot["radius_doublings"],
+                            "mean_nodes": tot["nodes"] / (B * world), "max_nodes_rank0": int(stats[:, 0].max())}}
         print(json.dumps(line), flush=True)
     ctx.close()
     if dist is not None:
@@ -486,8 +494,10 @@ def main():
 def main_mixed(args, w, rank, world, local, dev, dist, torch, mdx):
     """The uneven batch: autotune once (untimed), then time detect_mixed
     replayed from its captured CUDA graph."""
+    from paper_2002_09561_gb300 import replicas
+
     B = w["vectors"]
-    d, reqs = mixed_table(w, args.seed + rank, B)
+    d, reqs = mixed_table(w, args.seed + rank, B)  # each rank its own table (seed + rank)
     H = torch.from_numpy(d["H"]).to(dev)
     y = torch.from_numpy(d["y"]).to(dev)
     nv = torch.from_numpy(d["noise_var"]).to(dev)
@@ -516,11 +526,7 @@ def main_mixed(args, w, rank, world, local, dev, dist, torch, mdx):
         dist.barrier()
     torch.cuda.synchronize(dev)
     sampler.stop()
-    ms = e0.elapsed_time(e1)
-    if dist is not None:
-        t = torch.tensor([ms], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = replicas.max_over_ranks(e0.elapsed_time(e1), dist, dev)
     value = B * world * args.steps / (ms / 1e3)
     # kernel split from one profiled direct call (events around QR and search)
     ctx.profile(True)
@@ -561,11 +567,7 @@ def main_mixed(args, w, rank, world, local, dev, dist, torch, mdx):
         t0 = time.perf_counter()
         for _ in range(args.steps):
             mdx.detect_mixed_host(ctx, reqs, hH, hy, hnv, hsym, hmet, hvst, flags=flags, stream=stream)
-        el = time.perf_counter() - t0
-        if dist is not None:
-            t = torch.tensor([el], device=dev, dtype=torch.float64)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            el = float(t.item())
+        el = replicas.max_over_ranks(time.perf_counter() - t0, dist, dev)
         e2e = {"value": B * world * args.steps / el, "unit": "requests/s",
                "h2d_bytes_per_step": int(hH.nbytes + hy.nbytes + hnv.nbytes),
                "d2h_bytes_per_step": int(hsym.nbytes + hmet.nbytes + hvst.nbytes)}
