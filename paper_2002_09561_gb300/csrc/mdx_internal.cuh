@@ -203,6 +203,16 @@ __device__ __forceinline__ float prune_bound(float r2, float E, int n) {
   return r2 + 4.0f * sqrtf(r2) * E + 4.0f * (float)n * kU32 * r2;
 }
 
+// Warp-wide minimum of 64-bit keys (every lane gets it): the high words are
+// reduced first, then the low words of the lanes holding that high word; two
+// single-instruction 32-bit reductions instead of five shuffle rounds.
+__device__ __forceinline__ unsigned long long warp_min_u64(unsigned long long key) {
+  const unsigned hi = (unsigned)(key >> 32), lo = (unsigned)key;
+  const unsigned mhi = __reduce_min_sync(0xffffffffu, hi);
+  const unsigned mlo = __reduce_min_sync(0xffffffffu, hi == mhi ? lo : 0xffffffffu);
+  return ((unsigned long long)mhi << 32) | mlo;
+}
+
 __device__ __forceinline__ float warp_sum(float v) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);

@@ -345,11 +345,7 @@ __device__ void sdc_request(const MixedArgs& g, const MixedReq& q, int r, const 
           if (key < best) best = key;
         }
       }
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) {
-        const unsigned long long other = __shfl_xor_sync(0xffffffffu, best, o);
-        if (other < best) best = other;
-      }
+      best = warp_min_u64(best);
       const float ped = (best == ~0ull) ? INFINITY : __uint_as_float((unsigned)(best >> 32));
       if (!(ped < bnd)) {
         if (j == M - 1) break;  // the root is exhausted

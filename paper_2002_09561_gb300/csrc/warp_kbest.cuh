@@ -96,11 +96,7 @@ __device__ int warp_kbest(const float* Rc, const float* yb, int n, int P, int K,
           if (key < best) best = key;
         }
       }
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) {
-        const uint64_t other = __shfl_xor_sync(0xffffffffu, best, o);
-        if (other < best) best = other;
-      }
+      best = warp_min_u64(best);
       if (best == kInfKey) break;
       const int sv = (int)(best & 0xffffffffu);
       if ((sv & 31) == lane) {
