@@ -33,7 +33,7 @@ namespace {
 
 struct KbLayout {
   int n, K, P, keys_cap, pp, ts;
-  size_t off_R, off_yb, off_keys, off_xa, off_xb, off_pa, off_pb, off_cx, off_cp, off_cc, off_misc, bytes;
+  size_t off_R, off_yb, off_keys, off_xa, off_xb, off_pa, off_pb, off_cx, off_cp, off_cc, off_misc, off_m, bytes;
   __host__ __device__ void init(int n_, int K_, int P_, int keys_cap_) {
     n = n_;
     K = K_;
@@ -58,6 +58,8 @@ struct KbLayout {
     o += 2 * sizeof(float) * round_up(K, 4);
     off_misc = o;
     o += 64;
+    off_m = o;  // FP64 metrics of the re-scored candidates
+    o += sizeof(double) * kCandMax;
     off_xa = o;
     o += (size_t)pp * K;
     off_xb = o;
@@ -246,6 +248,13 @@ __device__ void stage_vector(const SearchArgs& a, int v, const KbLayout& L, unsi
   const int tid = threadIdx.x, T = blockDim.x;
   float* Rc = reinterpret_cast<float*>(smem + L.off_R);
   float* yb = reinterpret_cast<float*>(smem + L.off_yb);
+  {
+    // the FP64 R and ybar are read only by the final re-scoring: bring them
+    // into L2 now, so that it does not wait on DRAM
+    const char* r64 = reinterpret_cast<const char*>(a.R64 + (size_t)v * tri_stride64(a.n));
+    const int rbytes = (int)sizeof(double) * tri_stride64(a.n);
+    for (int off = tid * 128; off < rbytes; off += T * 128) asm volatile("prefetch.global.L2 [%0];" ::"l"(r64 + off));
+  }
   const float4* src = reinterpret_cast<const float4*>(a.R32 + (size_t)v * L.ts);
   for (int t = tid; t < L.ts / 4; t += T) reinterpret_cast<float4*>(Rc)[t] = src[t];
   const float* ys = a.yb32 + (size_t)v * vec_stride32(a.n);
@@ -267,31 +276,89 @@ __device__ void stage_vector(const SearchArgs& a, int v, const KbLayout& L, unsi
   __syncthreads();
 }
 
-// Re-score candidate paths (cx, cped; count nc, sorted or not) in FP64 with
-// warp 0, write the outputs of vector v.
+// FP64 ||ybar - R x||^2 of the path x with the columns split over the CTA's
+// nw warps (warp w takes j = w, w + nw, ...; a chain of dependent FP64 FMAs is
+// slow on this GPU, so shorter chains on all four schedulers finish sooner);
+// warp 0 adds the warps' residual partials in warp order and returns the
+// metric on its lanes (the other warps return 0).  part: nw * 224 doubles of
+// shared memory.  Every thread of the CTA calls this.
+__device__ double rescore_fp64_cta(int n, int P, double alpha64, const double* __restrict__ R64,
+                                   const double* __restrict__ y64, const uint8_t* x, double* part) {
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
+  double rr[7];
+#pragma unroll
+  for (int t = 0; t < 7; ++t) {
+    const int r = lane + 32 * t;
+    rr[t] = (warp == 0 && r < n) ? y64[r] : 0.0;
+  }
+  const double lv = (double)(2 * (lane < P ? lane : 0) - (P - 1)) * alpha64;
+  for (int j = warp; j < n; j += nw) {
+    const double xj = __shfl_sync(0xffffffffu, lv, (int)x[j]);
+    const double* col = R64 + col_off(j);
+#pragma unroll
+    for (int t = 0; t < 7; ++t) {
+      const int r = lane + 32 * t;
+      if (32 * t <= j && r <= j) rr[t] = fma(-col[r], xj, rr[t]);
+    }
+  }
+#pragma unroll
+  for (int t = 0; t < 7; ++t) part[warp * 224 + lane + 32 * t] = rr[t];
+  __syncthreads();
+  double m = 0.0;
+  if (warp == 0) {
+    double s = 0.0;
+#pragma unroll
+    for (int t = 0; t < 7; ++t) {
+      const int r = lane + 32 * t;
+      double z = 0.0;
+      for (int w = 0; w < nw; ++w) z += part[w * 224 + r];
+      if (r < n) s = fma(z, z, s);
+    }
+    m = __shfl_sync(0xffffffffu, warp_sum(s), 0);
+  }
+  __syncthreads();
+  return m;
+}
+
+// Re-score candidate paths (cx, cped; count nc, sorted or not) in FP64 and
+// write the outputs of vector v with warp 0 (every thread calls this).
+// part == nullptr: one candidate per warp; else each candidate by the whole
+// CTA (rescore_fp64_cta, part its scratch).  mbuf: kCandMax doubles of
+// shared memory.
 __device__ void finish_vector(const SearchArgs& a, int v, const uint8_t* cx, const float* cped,
                               int nc, int pp, float E, int status, long long nodes, long long peds,
-                              long long restarts, long long flops) {
-  const int tid = threadIdx.x;
-  if (tid >= 32) return;
-  const int lane = tid, n = a.n, P = a.P;
+                              long long restarts, long long flops, double* mbuf, double* part) {
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
+  const int n = a.n, P = a.P;
   float best = INFINITY;
   for (int q = 0; q < nc; ++q) best = fminf(best, cped[q]);
   const float keep = prune_bound(best, E, n);
   const double* R64 = a.R64 + (size_t)v * tri_stride64(n);
   const double* y64 = a.yb64 + (size_t)v * vec_stride64(n);
+  if (part && !(a.flags & MDX_NO_RESCORE)) {
+    for (int q = 0; q < nc; ++q) {
+      const double m = (cped[q] <= keep) ? rescore_fp64_cta(n, P, a.alpha64, R64, y64, cx + (size_t)q * pp, part)
+                                         : (double)INFINITY;
+      if (tid == 0) mbuf[q] = m;
+    }
+  } else {
+    for (int q = warp; q < nc; q += nw) {
+      double m = INFINITY;
+      if (cped[q] <= keep)
+        m = (a.flags & MDX_NO_RESCORE) ? (double)cped[q]
+                                       : rescore_fp64_warp(n, P, a.alpha64, R64, y64, cx + (size_t)q * pp, lane);
+      if (lane == 0) mbuf[q] = m;
+    }
+  }
+  __syncthreads();
+  if (warp != 0) return;
   int win = -1;
   double win_m = INFINITY;
   long long rescored = 0;
   for (int q = 0; q < nc; ++q) {
     if (!(cped[q] <= keep)) continue;
-    double m;
-    if (a.flags & MDX_NO_RESCORE) {
-      m = (double)cped[q];
-    } else {
-      m = rescore_fp64_warp(n, P, a.alpha64, R64, y64, cx + (size_t)q * pp, lane);
-      ++rescored;
-    }
+    const double m = mbuf[q];
+    if (!(a.flags & MDX_NO_RESCORE)) ++rescored;
     bool better = m < win_m;
     if (!better && m == win_m && win >= 0) {
       for (int j = n - 1; j >= 0; --j) {
@@ -337,7 +404,7 @@ __device__ bool singular_vector(const SearchArgs& a, int v) {
   return true;
 }
 
-__global__ void kbest_kernel(SearchArgs a, KbLayout L) {
+__global__ void __launch_bounds__(1024) kbest_kernel(SearchArgs a, KbLayout L) {
   extern __shared__ __align__(16) unsigned char smem[];
   const int tid = threadIdx.x, T = blockDim.x;
   const int n = a.n, P = a.P;
@@ -379,7 +446,7 @@ __global__ void kbest_kernel(SearchArgs a, KbLayout L) {
     }
     const int nc = S < kCandMax ? S : kCandMax;
     finish_vector(a, v, xcur, pcur, nc, L.pp, E, restarts > 0 ? MDX_V_EMPTY_RETRIED : MDX_V_OK,
-                  nodes, peds, restarts, flops);
+                  nodes, peds, restarts, flops, reinterpret_cast<double*>(smem + L.off_m), nullptr);
     __syncthreads();
   }
 }
@@ -392,8 +459,171 @@ __global__ void kbest_kernel(SearchArgs a, KbLayout L) {
 // phase the warp workspaces double as the prefix sort buffer.
 struct HyLayout {
   int n, K, P, W, pp, ts, Cw;  // Cw: key capacity per warp
-  size_t off_R, off_yb, off_idx, off_cx, off_cp, off_misc, off_warp, warp_bytes, bytes;
+  size_t off_R, off_yb, off_idx, off_cx, off_cp, off_misc, off_m, off_warp, warp_bytes, bytes;
+  // the best prefix's run by the whole CTA (cta = 0: by warp 0 alone): G threads
+  // per survivor, E keys per thread, lp = log2 P; buffers at off_warp + run_*
+  int cta, G, E, lp;
+  size_t run_xa, run_xb, run_pa, run_pb, run_cc, run_buf, run_cnt, run_bytes;
 };
+
+// ---------------------------------------------------------------------------
+// K-best level steps by a whole CTA (T = 32 W threads), for one run from one
+// node.  Per level: survivor t's interference (row_interference, G threads per
+// survivor, the same bits as a warp's single-lane chains), then one key per
+// child e = t P + k held in registers (E per thread, warp w holding the 32 E
+// elements from 32 E w).  A key orders the children as the tournament of
+// warp_kbest emits them: its distance field is the running maximum of the
+// partial distances along the survivor's Schnorr-Euchner order (a stream ends
+// at its first child outside the bound, and a child leaves its stream only
+// after the ones before it), then parent rank, Schnorr-Euchner rank, child.
+// Each warp sorts its keys in registers (bitonic: shuffles below stride 32,
+// in-thread exchanges above); the warps' sorted runs are then merged pairwise
+// through shared memory, keeping the 32 E smallest at each step (elementwise
+// minimum against the partner's reversed run, then a bitonic merge), so that
+// warp 0 ends with the level's survivors.
+struct CtaRun {
+  float* cc;      // [Kp] interference per survivor
+  uint64_t* buf;  // [W][32 E] merge runs; [0, K) the level's survivor keys
+  int* cnt;       // valid keys of the level
+};
+
+// Ascending sort of a bitonic run (size 64 E: every element ascends).
+template <int E>
+__device__ __forceinline__ void run_merge(uint64_t (&key)[E], int lane) {
+#pragma unroll
+  for (int stride = 16 * E; stride > 0; stride >>= 1) run_stage<E>(key, lane, 64 * E, stride);
+}
+
+template <int E>
+__device__ int cta_kbest_levels(const float* Rc, const float* yb, int n, int P, int lp, int K, int pp,
+                                float alpha, int G, int top, const unsigned int* r2bits, float Es,
+                                const CtaRun& w, uint8_t** xcur, uint8_t** xnxt, float** pcur, float** pnxt,
+                                long long* nodes, long long* flops) {
+  constexpr int R = 32 * E;
+  const int tid = threadIdx.x, T = blockDim.x, lane = tid & 31, warp = tid >> 5, W = T >> 5;
+  const float uoff = 0.5f * (float)(P - 1);
+  const int wpp = pp >> 2;
+  int S = 1, i = top;
+  while (i >= 0 && S > 0) {
+    if (S * P <= 32 && P <= 8) {
+      // levels whose children fit in one warp: warp 0 alone, no CTA barrier
+      if (warp == 0) {
+        int steps = 0;
+        while (i >= 0 && S > 0 && S * P <= 32) {
+          const float b = prune_bound(__uint_as_float(*(volatile const unsigned int*)r2bits), Es, n);
+          const int kept = warp_level_small(Rc, yb, n, P, K, pp, alpha, i, b, S, *xcur, *xnxt, *pcur, *pnxt, lane);
+          *nodes += S;
+          *flops += (long long)S * (2 * (n - 1 - i) + 4 * P);
+          uint8_t* tx = *xcur;
+          *xcur = *xnxt;
+          *xnxt = tx;
+          float* tp = *pcur;
+          *pcur = *pnxt;
+          *pnxt = tp;
+          S = kept;
+          --i;
+          ++steps;
+        }
+        if (lane == 0) {
+          w.cnt[1] = S;
+          w.cnt[2] = i;
+          w.cnt[3] = steps;
+        }
+      }
+      __syncthreads();
+      S = w.cnt[1];
+      i = w.cnt[2];
+      if (warp != 0 && (w.cnt[3] & 1)) {
+        uint8_t* tx = *xcur;
+        *xcur = *xnxt;
+        *xnxt = tx;
+        float* tp = *pcur;
+        *pcur = *pnxt;
+        *pnxt = tp;
+      }
+      continue;
+    }
+    const float bnd = prune_bound(__uint_as_float(*(volatile const unsigned int*)r2bits), Es, n);
+    {
+      const int t = tid / G, s = tid - t * G;
+      const bool act = t < S;
+      const uint8_t* xp = *xcur + (size_t)(act ? t : 0) * pp;
+      float ci;
+      if (G == 8) ci = row_interference<8>(Rc, yb, xp, n, P, alpha, i, s);
+      else if (G == 4) ci = row_interference<4>(Rc, yb, xp, n, P, alpha, i, s);
+      else if (G == 2) ci = row_interference<2>(Rc, yb, xp, n, P, alpha, i, s);
+      else ci = row_interference<1>(Rc, yb, xp, n, P, alpha, i, 0);
+      if (act && s == 0) w.cc[t] = ci;
+    }
+    __syncthreads();
+    const float rii = Rc[col_off(i) + i];
+    const float rinv = 0.5f / (alpha * rii);
+    uint64_t key[E];
+#pragma unroll
+    for (int r = 0; r < E; ++r) {
+      const int e = warp * R + r * 32 + lane;
+      const int t = e >> lp, k = e & (P - 1);
+      const bool act = t < S;
+      const float c = act ? w.cc[t] : 0.0f;
+      const float p0 = act ? (*pcur)[t] : 0.0f;
+      const float u = fmaf(c, rinv, uoff);
+      const float d = fmaf(-rii, (float)(2 * k - (P - 1)) * alpha, c);
+      const float ped = fmaf(d, d, p0);
+      key[r] = child_key(ped, u, t, k, P, act, bnd, lane);
+    }
+    run_sort<E>(key, lane);
+    for (int h = 1; h < W; h <<= 1) {
+      if ((warp & (2 * h - 1)) == h) {
+#pragma unroll
+        for (int r = 0; r < E; ++r) w.buf[warp * R + r * 32 + lane] = key[r];
+      }
+      __syncthreads();
+      if ((warp & (2 * h - 1)) == 0 && warp + h < W) {
+#pragma unroll
+        for (int r = 0; r < E; ++r) key[r] = kmin(key[r], w.buf[(warp + h) * R + (R - 1 - (r * 32 + lane))]);
+        run_merge<E>(key, lane);
+      }
+    }
+    if (warp == 0) {
+      int valid = 0;
+#pragma unroll
+      for (int r = 0; r < E; ++r) {
+        valid += __popc(__ballot_sync(0xffffffffu, key[r] != kInfKey));
+        if (r * 32 + lane < K) w.buf[r * 32 + lane] = key[r];
+      }
+      if (lane == 0) *w.cnt = valid;
+    }
+    __syncthreads();
+    const int kept = min(K, *w.cnt);
+    for (int idx = tid; idx < kept * wpp; idx += T) {
+      const int s = idx / wpp, wd = idx - s * wpp;
+      const unsigned lo = (unsigned)w.buf[s];
+      const int t = (int)(lo >> 8), k = (int)(lo & 15u);
+      uint32_t word = reinterpret_cast<const uint32_t*>(*xcur + (size_t)t * pp)[wd];
+      if (wd == (i >> 2)) {
+        const int sh = 8 * (i & 3);
+        word = (word & ~(0xffu << sh)) | ((uint32_t)k << sh);
+      }
+      reinterpret_cast<uint32_t*>(*xnxt + (size_t)s * pp)[wd] = word;
+      if (wd == 0) {
+        const float d = fmaf(-rii, (float)(2 * k - (P - 1)) * alpha, w.cc[t]);
+        (*pnxt)[s] = fmaf(d, d, (*pcur)[t]);
+      }
+    }
+    *nodes += S;
+    *flops += (long long)S * (2 * (n - 1 - i) + 4 * P);
+    __syncthreads();
+    uint8_t* tx = *xcur;
+    *xcur = *xnxt;
+    *xnxt = tx;
+    float* tp = *pcur;
+    *pcur = *pnxt;
+    *pnxt = tp;
+    S = kept;
+    --i;
+  }
+  return S;
+}
 
 __host__ __device__ inline size_t hy_warp_bytes(int n, int K, int P) {
   const size_t pp = path_stride(n);
@@ -421,13 +651,45 @@ __host__ __device__ inline void hy_layout(HyLayout& L, int n, int K, int P, int 
   o += sizeof(float) * kCandMax;
   L.off_misc = o;
   o += 128;
+  L.off_m = o;
+  o += sizeof(double) * kCandMax;
   L.off_cx = o;
   o += (size_t)L.pp * kCandMax;
   o = (o + 15) / 16 * 16;
   L.off_warp = o;
   L.warp_bytes = hy_warp_bytes(n, K, P);
-  // the warp workspaces double as the master's prefix sort buffer
-  const size_t need = ((sort_bytes + W - 1) / W + 15) / 16 * 16;
+  // the warp workspaces double as the master's prefix sort buffer and as the
+  // buffers of the CTA's run
+  size_t need = ((sort_bytes + W - 1) / W + 15) / 16 * 16;
+  const int T = 32 * W, Kp = pow2ceil(K);
+  L.lp = 0;
+  while ((1 << L.lp) < P) ++L.lp;
+  L.E = 1;
+  while (L.E <= 4 && (T * L.E < Kp * P || 32 * L.E < Kp)) L.E <<= 1;
+  L.G = 1;
+  while (L.G < 8 && 2 * L.G * Kp <= T) L.G <<= 1;
+  L.cta = (Kp <= T && L.E <= 4 && (1 << L.lp) == P && P <= 16) ? 1 : 0;
+  {
+    size_t r = 0;
+    auto take = [&](size_t bytes) {
+      const size_t at = r;
+      r += (bytes + 15) / 16 * 16;
+      return at;
+    };
+    L.run_xa = take((size_t)L.pp * K);
+    L.run_xb = take((size_t)L.pp * K);
+    L.run_pa = take(sizeof(float) * K);
+    L.run_pb = take(sizeof(float) * K);
+    L.run_cc = take(sizeof(float) * Kp);
+    L.run_buf = take(sizeof(uint64_t) * (size_t)T * L.E);
+    L.run_cnt = take(16);
+    L.run_bytes = r;
+  }
+  if (L.cta) {
+    const size_t per = ((L.run_bytes + W - 1) / W + 15) / 16 * 16;
+    if (need < per) need = per;
+  }
+  if (need < sizeof(double) * 224) need = sizeof(double) * 224;  // re-scoring partials, one row block per warp
   if (L.warp_bytes < need) L.warp_bytes = need;
   o += L.warp_bytes * W;
   L.bytes = o;
@@ -455,7 +717,6 @@ __global__ void hybrid_kernel(SearchArgs a, HyLayout L) {
   uint64_t* sortbuf = reinterpret_cast<uint64_t*>(smem + L.off_warp);  // master phase only
   int np = 1;
   for (int l = 0; l < d; ++l) np *= P;
-  const int nprefix = pow2ceil(np < 2 ? 2 : np);
 
   for (;;) {
     if (tid == 0) misc[0] = (int)atomicAdd(a.work_counter, 1u);
@@ -488,37 +749,34 @@ __global__ void hybrid_kernel(SearchArgs a, HyLayout L) {
     long long nodes = 0, peds = 0, restarts = 0, flops = 0;
     for (;;) {
       // ---- master: every depth-d prefix inside the sphere, sorted by partial distance
+      // (the in-sphere prefixes are compacted first, so that only they are sorted)
       const float bnd0 = prune_bound(__uint_as_float((unsigned)misc[5]), E, n);
-      for (int q = tid; q < nprefix; q += T) {
-        uint64_t key = kInfKey;
-        if (q < np) {
-          int rem = q;
-          float ped = 0.0f;
-          uint8_t xs[16];
-          for (int l = 0; l < d; ++l) {
-            const int i = n - 1 - l;
-            xs[l] = (uint8_t)(rem % P);
-            rem /= P;
-            float ci = yb[i];
-            for (int m = 0; m < l; ++m)
-              ci = fmaf(-Rc[col_off(n - 1 - m) + i], (float)(2 * (int)xs[m] - (P - 1)) * a.alpha, ci);
-            const float dd = fmaf(-Rc[col_off(i) + i], (float)(2 * (int)xs[l] - (P - 1)) * a.alpha, ci);
-            ped = fmaf(dd, dd, ped);
-          }
-          if (ped < bnd0) key = ((uint64_t)__float_as_uint(ped) << 32) | (unsigned)q;
+      if (tid == 0) misc[18] = 0;
+      __syncthreads();
+      for (int q = tid; q < np; q += T) {
+        int rem = q;
+        float ped = 0.0f;
+        uint8_t xs[16];
+        for (int l = 0; l < d; ++l) {
+          const int i = n - 1 - l;
+          xs[l] = (uint8_t)(rem % P);
+          rem /= P;
+          float ci = yb[i];
+          for (int m = 0; m < l; ++m)
+            ci = fmaf(-Rc[col_off(n - 1 - m) + i], (float)(2 * (int)xs[m] - (P - 1)) * a.alpha, ci);
+          const float dd = fmaf(-Rc[col_off(i) + i], (float)(2 * (int)xs[l] - (P - 1)) * a.alpha, ci);
+          ped = fmaf(dd, dd, ped);
         }
-        sortbuf[q] = key;
+        if (ped < bnd0) sortbuf[atomicAdd(&misc[18], 1)] = ((uint64_t)__float_as_uint(ped) << 32) | (unsigned)q;
       }
       __syncthreads();
-      bitonic_sort(sortbuf, nprefix, tid, T);
-      if (tid == 0) misc[1] = 0;
+      const int nin = misc[18];
+      const int Cs = pow2ceil(nin < 2 ? 2 : nin);
+      for (int q = nin + tid; q < Cs; q += T) sortbuf[q] = kInfKey;
       __syncthreads();
-      for (int q = tid; q < nprefix; q += T) {
-        if (sortbuf[q] != kInfKey) {
-          pidx[q] = (uint16_t)(sortbuf[q] & 0xffffu);
-          if (q + 1 == nprefix || sortbuf[q + 1] == kInfKey) misc[1] = q + 1;
-        }
-      }
+      bitonic_sort(sortbuf, Cs, tid, T);
+      for (int q = tid; q < nin; q += T) pidx[q] = (uint16_t)(sortbuf[q] & 0xffffu);
+      if (tid == 0) misc[1] = nin;
       if (tid == 0) {
         misc[2] = 0;
         misc[7] = 0;
@@ -526,11 +784,88 @@ __global__ void hybrid_kernel(SearchArgs a, HyLayout L) {
       nodes += (tid == 0) ? 1 : 0;
       __syncthreads();
       const int nvalid = misc[1];
-      // ---- workers: the best prefix is finished first by warp 0 alone (its leaf
-      // sets the radius, as the paper's SD master explores best-first); then
-      // every warp takes the remaining prefixes in order
+      // ---- workers: the best prefix is finished first (its leaf sets the
+      // radius, as the paper's SD master explores best-first), by the whole CTA
+      // or else by warp 0 alone; then every warp takes the remaining prefixes
+      // in order
       long long wnodes = 0, wflops = 0;
-      for (int phase = 0; phase < 2; ++phase) {
+      if (L.cta && nvalid > 0) {
+        unsigned char* rb = smem + L.off_warp;
+        uint8_t* xcur = rb + L.run_xa;
+        uint8_t* xnxt = rb + L.run_xb;
+        float* pcur = reinterpret_cast<float*>(rb + L.run_pa);
+        float* pnxt = reinterpret_cast<float*>(rb + L.run_pb);
+        const CtaRun run{reinterpret_cast<float*>(rb + L.run_cc), reinterpret_cast<uint64_t*>(rb + L.run_buf),
+                         reinterpret_cast<int*>(rb + L.run_cnt)};
+        const int q = pidx[0];
+        float pped = 0.0f;
+        {
+          int rem = q;
+          for (int l = 0; l < d; ++l) {
+            const int i = n - 1 - l;
+            const int k = rem % P;
+            rem /= P;
+            if (tid == 0) xcur[i] = (uint8_t)k;
+            float ci = yb[i];
+            int rr = q;
+            for (int m = 0; m < l; ++m) {
+              const int km = rr % P;
+              rr /= P;
+              ci = fmaf(-Rc[col_off(n - 1 - m) + i], (float)(2 * km - (P - 1)) * a.alpha, ci);
+            }
+            const float dd = fmaf(-Rc[col_off(i) + i], (float)(2 * k - (P - 1)) * a.alpha, ci);
+            pped = fmaf(dd, dd, pped);
+          }
+        }
+        const float r2 = __uint_as_float(*(volatile unsigned int*)r2bits);
+        if (!(pped < prune_bound(r2, E, n))) {
+          if (tid == 0) misc[7] = 1;  // sorted best-first: no prefix is inside the sphere
+        } else {
+          if (tid == 0) {
+            pcur[0] = pped;
+            misc[2] = 1;
+            wnodes += 1;
+            wflops += 2 * (d > 0 ? d - 1 : 0) + 4 * P;
+          }
+          __syncthreads();
+          long long rn = 0, rf = 0;
+          int S;
+          if (L.E == 1)
+            S = cta_kbest_levels<1>(Rc, yb, n, P, L.lp, K, L.pp, a.alpha, L.G, n - 1 - d, r2bits, E, run, &xcur,
+                                    &xnxt, &pcur, &pnxt, &rn, &rf);
+          else if (L.E == 2)
+            S = cta_kbest_levels<2>(Rc, yb, n, P, L.lp, K, L.pp, a.alpha, L.G, n - 1 - d, r2bits, E, run, &xcur,
+                                    &xnxt, &pcur, &pnxt, &rn, &rf);
+          else
+            S = cta_kbest_levels<4>(Rc, yb, n, P, L.lp, K, L.pp, a.alpha, L.G, n - 1 - d, r2bits, E, run, &xcur,
+                                    &xnxt, &pcur, &pnxt, &rn, &rf);
+          if (tid == 0) {
+            wnodes += rn;
+            wflops += rf;
+          }
+          if (S > 0) {
+            // the run's leaves within FP32 error of its best start the candidate list
+            const float lim = prune_bound(fminf(pcur[0], r2), E, n);
+            int nc = 0;
+            while (nc < S && nc < kCandMax && pcur[nc] <= lim) ++nc;
+            const int wpp = L.pp / 4;
+            for (int idx = tid; idx < nc * wpp; idx += T)
+              reinterpret_cast<uint32_t*>(cx)[idx] = reinterpret_cast<const uint32_t*>(xcur)[idx];
+            if (tid < nc) cped[tid] = pcur[tid];
+            if (tid == 0) {
+              misc[3] = nc;
+              atomicMin(r2bits, __float_as_uint(pcur[0]));
+            }
+          }
+          if (a.budget > 0 && tid == 0) {
+            const unsigned long long tot = atomicAdd(acc_budget, (unsigned long long)wnodes) + wnodes;
+            if ((long long)tot >= a.budget) misc[8] = 1;
+            wnodes = 0;
+          }
+        }
+        __syncthreads();
+      }
+      for (int phase = L.cta ? 1 : 0; phase < 2; ++phase) {
        if (phase == 1) __syncthreads();
        if (phase == 1 || warp == 0) {
         for (;;) {
@@ -667,7 +1002,8 @@ __global__ void hybrid_kernel(SearchArgs a, HyLayout L) {
     flops = (long long)*acc_flops;
     peds = nodes * P;
     const int status = misc[8] ? MDX_V_BUDGET_EXCEEDED : (restarts > 0 ? MDX_V_EMPTY_RETRIED : MDX_V_OK);
-    finish_vector(a, v, cx, cped, misc[3], L.pp, E, status, nodes, peds, restarts, flops);
+    finish_vector(a, v, cx, cped, misc[3], L.pp, E, status, nodes, peds, restarts, flops,
+                  reinterpret_cast<double*>(smem + L.off_m), reinterpret_cast<double*>(smem + L.off_warp));
     __syncthreads();
   }
 }

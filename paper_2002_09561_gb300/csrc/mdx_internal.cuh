@@ -230,7 +230,9 @@ namespace mdx {
 
 // ||ybar - R x||^2 in FP64 for the PAM-index path x (n <= 224), computed by
 // the calling warp (all 32 lanes) column by column: lane l accumulates the
-// residual of rows l, l+32, ...  Every lane returns the same value.
+// residual of rows l, l+32, ...  Every lane returns the same value.  Lane k < P
+// holds the FP64 level (2k - (P-1)) alpha, fetched per column by a shuffle
+// (an FP64 conversion and product per column would occupy the FP64 unit).
 __device__ __forceinline__ double rescore_fp64_warp(int n, int P, double alpha64,
                                                      const double* __restrict__ R64,
                                                      const double* __restrict__ y64,
@@ -241,8 +243,9 @@ __device__ __forceinline__ double rescore_fp64_warp(int n, int P, double alpha64
     const int r = lane + 32 * t;
     rr[t] = (r < n) ? y64[r] : 0.0;
   }
+  const double lv = (double)(2 * (lane < P ? lane : 0) - (P - 1)) * alpha64;
   for (int j = 0; j < n; ++j) {
-    const double xj = (double)(2 * (int)x[j] - (P - 1)) * alpha64;
+    const double xj = __shfl_sync(0xffffffffu, lv, (int)x[j]);
     const double* col = R64 + col_off(j);
 #pragma unroll
     for (int t = 0; t < 7; ++t) {

@@ -470,7 +470,7 @@ __device__ void kb_request(const MixedArgs& g, const MixedReq& q, int r, const f
       pa[0] = 0.0f;
     }
     __syncwarp();
-    S = warp_kbest<SPL>(Rc, yb, n, P, K, pp, q.alpha, n - 1, r2w, E, sel, &xcur, &xnxt, &pcur, &pnxt, lane, &nodes,
+    S = warp_kbest<SPL, false>(Rc, yb, n, P, K, pp, q.alpha, n - 1, r2w, E, sel, &xcur, &xnxt, &pcur, &pnxt, lane, &nodes,
                         &flops);
     __syncwarp();
     if (S > 0 || !(r2 < INFINITY) || restarts >= 64) break;

@@ -189,6 +189,16 @@ def test_hybrid_8x8_64qam(env, K, d):
     _compare(gpu, ref, KB_GAP, label=f"hybrid 8x8 64-QAM K={K} d={d}")
 
 
+@pytest.mark.parametrize("N,qam,K,d,snr", [(16, 16, 64, 4, 8.0), (12, 4, 32, 3, 6.0), (10, 16, 128, 2, 10.0)])
+def test_hybrid_survivor_widths(env, N, qam, K, d, snr):
+    """The best prefix runs on the whole CTA with 1, 2 or 4 keys per thread
+    (K P up to 1024 children per level); the rest on single warps."""
+    w = wl.generate(80 + K + d, 200, N, N, qam, snr)
+    gpu = _run(env, "hybrid", w, qam, K=K, depth=d, radius="paper")
+    ref = oracle.detect_batch("hybrid", w["H"], w["y"], w["noise_var"], qam, K=K, depth=d, radius="paper")
+    _compare(gpu, ref, KB_GAP, label=f"hybrid {N}x{N} {qam}-QAM K={K} d={d}")
+
+
 def test_hybrid_100x100_64qam_sample(env):
     w = wl.generate(71, 6, 100, 100, 64, 28.0)
     gpu = _run(env, "hybrid", w, 64, K=32, depth=4, radius="paper")
