@@ -619,6 +619,217 @@ __global__ void __launch_bounds__(kQrdWarps * 32, 1)
               reinterpret_cast<const double2*>(y + q.yin_off), d);
 }
 
+// ---------------------------------------------------------------------------
+// Small systems (n_rx <= 16): the same reflectors, column by column in the
+// left-looking order (column j receives reflectors 0..j-1, then forms its own),
+// for 16 matrices per warp with two lanes per matrix: lane 2m + h holds rows
+// r = 2q + h (q < 8) of matrix m's current column in registers.  An FP64
+// instruction occupies its scheduler's FP64 unit for about 70 cycles however
+// many lanes it serves, so here every lane does useful FMAs and a reflector
+// costs one two-lane reduction, where one CTA per matrix spends most of its
+// FP64 instructions on cross-lane sums and idle rows.  The reflectors v_k
+// (rows k..N-1) and tau_k live in shared memory, entry-major with the 16
+// matrices innermost (consecutive lanes read consecutive 16-byte entries);
+// the phases of R's rows stay in the registers of the lanes owning them.
+constexpr int kQsMats = 16;  // matrices per warp
+constexpr int kQsSlots = 8;  // rows per lane (n_rx <= 16)
+
+__host__ __device__ inline int qs_vo(int k, int N) { return k * N - k * (k - 1) / 2; }  // first entry of v_k
+__host__ __device__ inline size_t qs_smem(int N, int M) {
+  return sizeof(double2) * kQsMats * (size_t)qs_vo(M, N) + sizeof(double) * kQsMats * (size_t)M;
+}
+
+// One R entry z = R_kc (complex, after the phase fix) in the real interleaved
+// outputs: the block [[Re, -Im], [Im, Re]] at rows 2k.., columns 2c..
+__device__ __forceinline__ void qs_put(const QrDst& out, int n, int k, int c, double re, double im) {
+  const double vals[4] = {re, -im, im, re};
+  const int rows[4] = {2 * k, 2 * k, 2 * k + 1, 2 * k + 1};
+  const int cols[4] = {2 * c, 2 * c + 1, 2 * c, 2 * c + 1};
+#pragma unroll
+  for (int e = 0; e < 4; ++e) {
+    const int rr = rows[e], cc = cols[e];
+    if (rr > cc) continue;
+    if (out.R64) out.R64[col_off(cc) + rr] = vals[e];
+    if (out.R32) out.R32[col_off(cc) + rr] = (float)vals[e];
+    if (out.Rdense) out.Rdense[(size_t)rr * n + cc] = vals[e];
+  }
+}
+
+// Factorises the [H | y] of this lane pair (act: the pair has a matrix).
+// Hb: row-major N x M complex, yb: N complex.  Every lane of the warp calls
+// this with the same N, M (shuffles inside).
+__device__ void qr_small_pair(int N, int M, bool act, const double2* __restrict__ Hb,
+                              const double2* __restrict__ yv, const QrDst& out, double2* V, double* Tau) {
+  const int lane = threadIdx.x & 31, m = lane >> 1, h = lane & 1;
+  const int n = 2 * M;
+  double2 a[kQsSlots], ph[kQsSlots];
+#pragma unroll
+  for (int q = 0; q < kQsSlots; ++q) ph[q] = make_double2(1.0, 0.0);
+  int sing = 0;
+  for (int j = 0; j <= M; ++j) {
+#pragma unroll
+    for (int q = 0; q < kQsSlots; ++q) {
+      const int r = 2 * q + h;
+      a[q] = make_double2(0.0, 0.0);
+      if (act && r < N) a[q] = (j < M) ? Hb[(size_t)r * M + j] : yv[r];
+    }
+    // reflectors 0 .. j-1: a <- a - v_k tau_k (v_k^H a) over rows k..N-1
+    const int kend = j < M ? j : M;
+    for (int k = 0; k < kend; ++k) {
+      const double2* vk = V + (size_t)(qs_vo(k, N) - k) * kQsMats + m;  // entry r at vk[r * 16]
+      double wr = 0.0, wi = 0.0;
+#pragma unroll
+      for (int q = 0; q < kQsSlots; ++q) {
+        const int r = 2 * q + h;
+        if (2 * q + 1 < k || 2 * q >= N) continue;  // neither lane of the pair has this row
+        if (r >= k && r < N) {
+          const double2 v = vk[(size_t)r * kQsMats];
+          wr = fma(v.x, a[q].x, fma(v.y, a[q].y, wr));
+          wi = fma(v.x, a[q].y, fma(-v.y, a[q].x, wi));
+        }
+      }
+      wr += __shfl_xor_sync(0xffffffffu, wr, 1);
+      wi += __shfl_xor_sync(0xffffffffu, wi, 1);
+      const double tk = Tau[k * kQsMats + m];
+      wr *= tk;
+      wi *= tk;
+#pragma unroll
+      for (int q = 0; q < kQsSlots; ++q) {
+        const int r = 2 * q + h;
+        if (2 * q + 1 < k || 2 * q >= N) continue;
+        if (r >= k && r < N) {
+          const double2 v = vk[(size_t)r * kQsMats];
+          a[q].x = fma(-v.x, wr, fma(v.y, wi, a[q].x));
+          a[q].y = fma(-v.x, wi, fma(-v.y, wr, a[q].y));
+        }
+      }
+    }
+    if (j < M) {
+      // column j of R above the diagonal: rows k < j, final now, phase-fixed
+#pragma unroll
+      for (int q = 0; q < kQsSlots; ++q) {
+        const int r = 2 * q + h;
+        if (act && r < j) {
+          const double re = a[q].x * ph[q].x + a[q].y * ph[q].y, im = a[q].y * ph[q].x - a[q].x * ph[q].y;
+          qs_put(out, n, r, j, re, im);
+        }
+      }
+      // reflector j from rows j..N-1
+      double s = 0.0;
+      double2 x0 = make_double2(0.0, 0.0);
+#pragma unroll
+      for (int q = 0; q < kQsSlots; ++q) {
+        const int r = 2 * q + h;
+        if (r >= j && r < N) s = fma(a[q].x, a[q].x, fma(a[q].y, a[q].y, s));
+        if (r == j) x0 = a[q];
+      }
+      s += __shfl_xor_sync(0xffffffffu, s, 1);
+      const int h0 = j & 1;
+      x0.x = __shfl_sync(0xffffffffu, x0.x, (lane & ~1) | h0);
+      x0.y = __shfl_sync(0xffffffffu, x0.y, (lane & ~1) | h0);
+      double sigma = 0.0, tj = 0.0;
+      double2 phr = make_double2(1.0, 0.0), al = make_double2(0.0, 0.0);
+      if (s > 0.0) {
+        const double rs = rsqrt_nr(s);
+        sigma = s * rs;
+        const double qq = fma(x0.x, x0.x, x0.y * x0.y);
+        double ax0 = 0.0;
+        double2 p0 = make_double2(1.0, 0.0);
+        if (qq > 0.0) {
+          const double rq = rsqrt_nr(qq);
+          ax0 = qq * rq;
+          p0 = make_double2(x0.x * rq, x0.y * rq);
+        }
+        // alpha = -e^{i arg x0} sigma keeps v_j = x0 - alpha free of cancellation
+        al = make_double2(-p0.x * sigma, -p0.y * sigma);
+        phr = make_double2(-p0.x, -p0.y);
+        tj = rcp_nr(sigma * (sigma + ax0));
+      } else {
+        sing = 1;
+      }
+      double2* vj = V + (size_t)(qs_vo(j, N) - j) * kQsMats + m;
+#pragma unroll
+      for (int q = 0; q < kQsSlots; ++q) {
+        const int r = 2 * q + h;
+        if (r >= j && r < N) vj[(size_t)r * kQsMats] = (r == j) ? make_double2(x0.x - al.x, x0.y - al.y) : a[q];
+        if (r == j) ph[q] = phr;
+      }
+      if (h == 0) Tau[j * kQsMats + m] = tj;
+      if (act && h == h0) qs_put(out, n, j, j, sigma, 0.0);
+    } else {
+      // ybar = Q^H y: rows k < M of the y column, phase-fixed
+#pragma unroll
+      for (int q = 0; q < kQsSlots; ++q) {
+        const int r = 2 * q + h;
+        if (act && r < M) {
+          const double re = a[q].x * ph[q].x + a[q].y * ph[q].y, im = a[q].y * ph[q].x - a[q].x * ph[q].y;
+          if (out.yb64) {
+            out.yb64[2 * r] = re;
+            out.yb64[2 * r + 1] = im;
+          }
+          if (out.yb32) {
+            out.yb32[2 * r] = (float)re;
+            out.yb32[2 * r + 1] = (float)im;
+          }
+          if (out.ybdense) {
+            out.ybdense[2 * r] = re;
+            out.ybdense[2 * r + 1] = im;
+          }
+        }
+      }
+    }
+    __syncwarp();
+  }
+  if (act) {
+    if (out.Rdense)
+      for (int t = h; t < n * n; t += 2)
+        if (t / n > t % n) out.Rdense[t] = 0.0;
+    if (h == 0 && out.singular) *out.singular = sing;
+  }
+}
+
+__global__ void __launch_bounds__(32) qr_small_kernel(int batch, int N, int M, const double* __restrict__ H,
+                                                      const double* __restrict__ y, QrOut out) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  double2* V = reinterpret_cast<double2*>(smem_raw);
+  double* Tau = reinterpret_cast<double*>(V + (size_t)kQsMats * qs_vo(M, N));
+  const int lane = threadIdx.x & 31;
+  const int b = blockIdx.x * kQsMats + (lane >> 1);
+  const bool act = b < batch;
+  const int n = 2 * M;
+  const int bb = act ? b : 0;
+  QrDst d;
+  d.R64 = out.R64 ? out.R64 + (size_t)bb * tri_stride64(n) : nullptr;
+  d.yb64 = out.yb64 ? out.yb64 + (size_t)bb * vec_stride64(n) : nullptr;
+  d.R32 = out.R32 ? out.R32 + (size_t)bb * tri_stride32(n) : nullptr;
+  d.yb32 = out.yb32 ? out.yb32 + (size_t)bb * vec_stride32(n) : nullptr;
+  d.Rdense = out.Rdense ? out.Rdense + (size_t)bb * n * n : nullptr;
+  d.ybdense = out.ybdense ? out.ybdense + (size_t)bb * n : nullptr;
+  d.singular = out.singular ? out.singular + bb : nullptr;
+  qr_small_pair(N, M, act, reinterpret_cast<const double2*>(H) + (size_t)bb * N * M,
+                reinterpret_cast<const double2*>(y) + (size_t)bb * N, d, V, Tau);
+}
+
+// Uneven batches: the listed requests (all N x M) at their own offsets.
+__global__ void __launch_bounds__(32) qr_small_gather_kernel(int count, const int* __restrict__ ids,
+                                                             const MixedReq* __restrict__ reqs,
+                                                             const double* __restrict__ H,
+                                                             const double* __restrict__ y, int N, int M,
+                                                             QrOut out) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  double2* V = reinterpret_cast<double2*>(smem_raw);
+  double* Tau = reinterpret_cast<double*>(V + (size_t)kQsMats * qs_vo(M, N));
+  const int lane = threadIdx.x & 31;
+  const int i = blockIdx.x * kQsMats + (lane >> 1);
+  const bool act = i < count;
+  const MixedReq q = reqs[ids[act ? i : 0]];
+  const int r = ids[act ? i : 0];
+  QrDst d{out.R64 + q.r_off64, out.yb64 + q.y_off64, out.R32 + q.r_off, out.yb32 + q.y_off, nullptr, nullptr,
+          out.singular + r};
+  qr_small_pair(N, M, act, reinterpret_cast<const double2*>(H + q.h_off),
+                reinterpret_cast<const double2*>(y + q.yin_off), d, V, Tau);
+}
+
 // The tensor-core form for n_tx >= kQrdMinTx when its shared memory fits.
 #ifndef MDX_QRD_MIN_TX
 #define MDX_QRD_MIN_TX 48
@@ -678,11 +889,14 @@ cudaError_t launch_qr_gather(int count, int n_rx, int n_tx, const int* ids, cons
     qr_dmma_gather_kernel<<<count, kQrdWarps * 32, sm, s>>>(count, ids, reqs, H, y, out);
     return cudaGetLastError();
   }
-  const size_t smem = qr_smem(n_rx, n_tx);
   if (n_rx <= 16) {
-    cudaFuncSetAttribute(qr_gather_kernel<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    qr_gather_kernel<16><<<count, 32, smem, s>>>(count, ids, reqs, H, y, out);
-  } else {
+    const size_t sm = qs_smem(n_rx, n_tx);
+    cudaFuncSetAttribute(qr_small_gather_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    qr_small_gather_kernel<<<(count + kQsMats - 1) / kQsMats, 32, sm, s>>>(count, ids, reqs, H, y, n_rx, n_tx, out);
+    return cudaGetLastError();
+  }
+  const size_t smem = qr_smem(n_rx, n_tx);
+  {
     const int threads = n_tx <= 32 ? 128 : 256;
     cudaFuncSetAttribute(qr_gather_kernel<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     qr_gather_kernel<32><<<count, threads, smem, s>>>(count, ids, reqs, H, y, out);
@@ -699,12 +913,15 @@ cudaError_t launch_qr(int batch, int n_rx, int n_tx, const double* H, const doub
     qr_dmma_kernel<<<batch, kQrdWarps * 32, sm, s>>>(batch, n_rx, n_tx, H, y, out);
     return cudaGetLastError();
   }
-  const size_t smem = qr_smem(n_rx, n_tx);
   if (n_rx <= 16) {
-    // two 16-lane workers per warp
-    cudaFuncSetAttribute(qr_kernel<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    qr_kernel<16><<<batch, 32, smem, s>>>(batch, n_rx, n_tx, H, y, out);
-  } else {
+    // 16 matrices per warp, two lanes per matrix
+    const size_t sm = qs_smem(n_rx, n_tx);
+    cudaFuncSetAttribute(qr_small_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    qr_small_kernel<<<(batch + kQsMats - 1) / kQsMats, 32, sm, s>>>(batch, n_rx, n_tx, H, y, out);
+    return cudaGetLastError();
+  }
+  const size_t smem = qr_smem(n_rx, n_tx);
+  {
     const int threads = n_tx <= 32 ? 128 : 256;
     cudaFuncSetAttribute(qr_kernel<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     qr_kernel<32><<<batch, threads, smem, s>>>(batch, n_rx, n_tx, H, y, out);
