@@ -200,16 +200,14 @@ mdx_status run_detect(int algo, mdx_ctx* c, const mdx_params* p, int batch, cons
   if (complex_tree && algo == ALGO_HYBRID) return fail(c, MDX_EUNSUPPORTED, "MDX_COMPLEX_TREE applies to SD and K-best");
   if (natural && (algo != ALGO_SD || complex_tree))
     return fail(c, MDX_EUNSUPPORTED, "MDX_ORDER_NATURAL applies to detect_sd on the real tree");
-  int keys_cap = pow2ceil(algo == ALGO_SD ? 2 : p->K * (complex_tree ? P * P : P));
   if (algo == ALGO_HYBRID) {
     const int d = p->hybrid_depth;
     if (d < 0 || d > n || d > 12) return fail(c, MDX_EINVAL, "hybrid_depth %d not in 0..min(n, 12)", d);
     long long np = 1;
     for (int l = 0; l < d; ++l) np *= P;
     if (np > 4096) return fail(c, MDX_EUNSUPPORTED, "P^depth = %lld > 4096 prefixes", np);
-    keys_cap += pow2ceil(np < 2 ? 2 : (int)np);
   }
-  if (algo == ALGO_KBEST && kbest_smem_bytes(n, p->K, P, keys_cap) > 227 * 1024)
+  if (algo == ALGO_KBEST && kbest_smem_bytes(n, p->K, P, complex_tree) > 227 * 1024)
     return fail(c, MDX_EUNSUPPORTED, "K=%d at n=%d, P=%d needs more than 227 KB of shared memory", p->K,
                 n, P);
   if (algo == ALGO_HYBRID && hybrid_smem_bytes(n, p->K, P, p->hybrid_depth) == (size_t)-1)

@@ -144,7 +144,7 @@ size_t sd_vec_state_bytes(int n);
 cudaError_t launch_sd(const SearchArgs& a, const SdWorkspace& w, int num_sms, cudaStream_t s);
 cudaError_t launch_kbest(const SearchArgs& a, int num_sms, cudaStream_t s);
 // Shared memory of the K-best kernel for (n, K, P, key capacity).
-size_t kbest_smem_bytes(int n, int K, int P, int keys_cap);
+size_t kbest_smem_bytes(int n, int K, int P, bool complex_tree);
 cudaError_t launch_hybrid(const SearchArgs& a, int num_sms, cudaStream_t s);
 // Linear detectors (linear.cu): ZF or MMSE on the QR workspace.
 size_t linear_smem_bytes(int n, bool mmse);

@@ -102,9 +102,14 @@ __device__ __forceinline__ void run_sort(uint64_t (&key)[E], int lane) {
 // and prunes the children exactly as the tournament of warp_kbest emits them:
 // a survivor's stream ends at its first child outside the bound, and a child
 // leaves its stream only after the ones before it.  Every lane of the warp
-// must call this (shuffles inside).
-template <int P>
+// must call this (shuffles inside).  SE = false gives the plain key
+// (distance, parent rank, child) of the K-best of Sec. VI instead, each child
+// pruned on its own distance.
+template <int P, bool SE = true>
 __device__ __forceinline__ uint64_t child_key(float ped, float u, int t, int k, bool act, float bnd, int lane) {
+  if (!SE)
+    return (act && ped < bnd) ? (((uint64_t)__float_as_uint(ped) << 32) | ((unsigned)t << 8) | (unsigned)k)
+                              : kInfKey;
   const float dk = fabsf(u - (float)k);
   const int base = lane & ~(P - 1);
   float run = ped;
@@ -123,12 +128,13 @@ __device__ __forceinline__ uint64_t child_key(float ped, float u, int t, int k, 
              : kInfKey;
 }
 
+template <bool SE = true>
 __device__ __forceinline__ uint64_t child_key(float ped, float u, int t, int k, int P, bool act, float bnd,
                                               int lane) {
-  if (P == 8) return child_key<8>(ped, u, t, k, act, bnd, lane);
-  if (P == 4) return child_key<4>(ped, u, t, k, act, bnd, lane);
-  if (P == 2) return child_key<2>(ped, u, t, k, act, bnd, lane);
-  return child_key<16>(ped, u, t, k, act, bnd, lane);
+  if (P == 8) return child_key<8, SE>(ped, u, t, k, act, bnd, lane);
+  if (P == 4) return child_key<4, SE>(ped, u, t, k, act, bnd, lane);
+  if (P == 2) return child_key<2, SE>(ped, u, t, k, act, bnd, lane);
+  return child_key<16, SE>(ped, u, t, k, act, bnd, lane);
 }
 
 // One K-best level (row i) by one warp when the S P children fit in its lanes
@@ -138,7 +144,7 @@ __device__ __forceinline__ uint64_t child_key(float ped, float u, int t, int k, 
 // empty) are sorted in registers.  Writes the kept
 // survivors (paths and partial distances, sorted) to xnxt / pnxt and returns
 // their number.
-template <int P>
+template <int P, bool SE>
 __device__ int warp_level_small_p(const float* Rc, const float* yb, int n, int K, int pp, float alpha, int i,
                                   float bnd, int S, const uint8_t* xcur, uint8_t* xnxt, const float* pcur,
                                   float* pnxt, int lane) {
@@ -153,7 +159,7 @@ __device__ int warp_level_small_p(const float* Rc, const float* yb, int n, int K
   const float u = fmaf(c, rinv, 0.5f * (float)(P - 1));
   const float d = fmaf(-rii, (float)(2 * k - (P - 1)) * alpha, c);
   const float ped = fmaf(d, d, p0);
-  uint64_t key[1] = {child_key<P>(ped, u, t, k, act, bnd, lane)};
+  uint64_t key[1] = {child_key<P, SE>(ped, u, t, k, act, bnd, lane)};
   const int valid = __popc(__ballot_sync(0xffffffffu, key[0] != kInfKey));
   const int kept = min(K, valid);
   if (kept <= 8) {
@@ -196,12 +202,13 @@ __device__ int warp_level_small_p(const float* Rc, const float* yb, int n, int K
   return kept;
 }
 
+template <bool SE = true>
 __device__ int warp_level_small(const float* Rc, const float* yb, int n, int P, int K, int pp, float alpha, int i,
                                 float bnd, int S, const uint8_t* xcur, uint8_t* xnxt, const float* pcur,
                                 float* pnxt, int lane) {
-  if (P == 8) return warp_level_small_p<8>(Rc, yb, n, K, pp, alpha, i, bnd, S, xcur, xnxt, pcur, pnxt, lane);
-  if (P == 4) return warp_level_small_p<4>(Rc, yb, n, K, pp, alpha, i, bnd, S, xcur, xnxt, pcur, pnxt, lane);
-  return warp_level_small_p<2>(Rc, yb, n, K, pp, alpha, i, bnd, S, xcur, xnxt, pcur, pnxt, lane);
+  if (P == 8) return warp_level_small_p<8, SE>(Rc, yb, n, K, pp, alpha, i, bnd, S, xcur, xnxt, pcur, pnxt, lane);
+  if (P == 4) return warp_level_small_p<4, SE>(Rc, yb, n, K, pp, alpha, i, bnd, S, xcur, xnxt, pcur, pnxt, lane);
+  return warp_level_small_p<2, SE>(Rc, yb, n, K, pp, alpha, i, bnd, S, xcur, xnxt, pcur, pnxt, lane);
 }
 
 // One warp's K-best run over rows top..0 from the node (prefix path in
