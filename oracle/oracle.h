@@ -20,7 +20,7 @@
  *   K-best              keep the K best per level        Sec. VI
  *   hybrid SD-K-best    SD master hands nodes to K-best  Sec. VI
  *
- * Conventions fixed where the paper is silent (each is listed in the design doc):
+ * Conventions fixed where the paper is silent:
  *   - unit-energy square QAM, PAM levels (2k-(P-1))*alpha per dimension,
  *     complex index q = k_re*P + k_im, Gray bits per dimension;
  *   - real-valued tree over the interleaved decomposition: real index 2j is
