@@ -12,8 +12,9 @@
 // kbest_levels); the new survivors copy their parent's path (4-byte words; the path
 // stride is an odd number of words so that threads reading their own paths
 // hit distinct banks) and append their child.  Complex tree (one level per
-// antenna, Q = P^2 children): thread t owns survivor t, and one bitonic sort
-// in shared memory orders the level's keys.
+// antenna, Q = P^2 children, cta_kbest_levels_complex): the same selection
+// over the S Q keys of a level (one bitonic sort in shared memory when K Q is
+// too large for register runs, kbest_levels_complex).
 //
 // Hybrid.  The master part enumerates every depth-d prefix (rows n-1..n-d),
 // keeps those inside the initial sphere and sorts them by partial distance;
@@ -407,6 +408,108 @@ __device__ int kbest_levels_complex(const KbCtx& c, int S, uint8_t** xcur, uint8
   return S;
 }
 
+// Complex-tree K-best level steps by a whole CTA (one level per antenna j:
+// real rows 2j+1 and 2j, Q = P^2 children): each survivor's interference of
+// both rows (one thread per survivor, as in kbest_levels_complex), then one
+// key (distance, parent rank * Q + q) per child, E per thread, sorted in
+// registers per warp and merged across warps as in cta_kbest_levels.
+template <int E>
+__device__ int cta_kbest_levels_complex(const KbCtx& c, int lq, const CtaRun& w, uint8_t** xcur, uint8_t** xnxt,
+                                        float** pcur, float** pnxt, const float* r2s, float Es, long long* nodes,
+                                        long long* peds, long long* flops) {
+  constexpr int R = 32 * E;
+  const int n = c.n, P = c.P, Q = P * P, K = c.K, pp = c.pp, tid = c.tid, T = c.T;
+  const int lane = tid & 31, warp = tid >> 5, W = T >> 5, wpp = pp >> 2;
+  int S = 1;
+  for (int j = n / 2 - 1; j >= 0 && S > 0; --j) {
+    const int r1 = 2 * j + 1, r0 = 2 * j;
+    const float bnd = prune_bound(*r2s, Es, n);
+    for (int t = tid; t < S; t += T) {
+      const uint8_t* xp = *xcur + (size_t)t * pp;
+      float c1 = c.yb[r1], c0 = c.yb[r0];
+      for (int jj = n - 1; jj > r1; --jj) {
+        const float a = (float)(2 * (int)xp[jj] - (P - 1)) * c.alpha;
+        c1 = fmaf(-c.Rc[col_off(jj) + r1], a, c1);
+        c0 = fmaf(-c.Rc[col_off(jj) + r0], a, c0);
+      }
+      w.cc[t] = c1;
+      w.cc[K + t] = c0;
+    }
+    __syncthreads();
+    const float r11 = c.Rc[col_off(r1) + r1], r01 = c.Rc[col_off(r1) + r0], r00 = c.Rc[col_off(r0) + r0];
+    uint64_t key[E];
+#pragma unroll
+    for (int r = 0; r < E; ++r) {
+      const int e = warp * R + r * 32 + lane;
+      const int t = e >> lq, q = e & (Q - 1);
+      key[r] = kInfKey;
+      if (t < S) {
+        const int kre = q / P, kim = q - kre * P;
+        const float aim = (float)(2 * kim - (P - 1)) * c.alpha, are = (float)(2 * kre - (P - 1)) * c.alpha;
+        const float d1 = fmaf(-r11, aim, w.cc[t]);
+        const float p1 = fmaf(d1, d1, (*pcur)[t]);
+        const float d0 = fmaf(-r00, are, fmaf(-r01, aim, w.cc[K + t]));
+        const float pd = fmaf(d0, d0, p1);
+        if (pd < bnd) key[r] = ((uint64_t)__float_as_uint(pd) << 32) | (unsigned)e;
+      }
+    }
+    run_sort<E>(key, lane);
+    for (int h = 1; h < W; h <<= 1) {
+      if ((warp & (2 * h - 1)) == h) {
+#pragma unroll
+        for (int r = 0; r < E; ++r) w.buf[warp * R + r * 32 + lane] = key[r];
+      }
+      __syncthreads();
+      if ((warp & (2 * h - 1)) == 0 && warp + h < W) {
+#pragma unroll
+        for (int r = 0; r < E; ++r) key[r] = kmin(key[r], w.buf[(warp + h) * R + (R - 1 - (r * 32 + lane))]);
+        run_merge<E>(key, lane);
+      }
+    }
+    if (warp == 0) {
+      int valid = 0;
+#pragma unroll
+      for (int r = 0; r < E; ++r) {
+        valid += __popc(__ballot_sync(0xffffffffu, key[r] != kInfKey));
+        if (r * 32 + lane < K) w.buf[r * 32 + lane] = key[r];
+      }
+      if (lane == 0) *w.cnt = valid;
+    }
+    __syncthreads();
+    const int kept = min(K, *w.cnt);
+    // new paths: rows 2j+1 (imaginary index) and 2j (real index) share a word
+    const int wj = r0 >> 2, sh = 8 * (r0 & 3);
+    for (int idx = tid; idx < kept * wpp; idx += T) {
+      const int s = idx / wpp, wd = idx - s * wpp;
+      const unsigned id = (unsigned)w.buf[s];
+      const int t = (int)(id >> lq), q = (int)(id & (unsigned)(Q - 1));
+      const int kre = q / P, kim = q - kre * P;
+      uint32_t word = reinterpret_cast<const uint32_t*>(*xcur + (size_t)t * pp)[wd];
+      if (wd == wj) word = (word & ~(0xffffu << sh)) | ((uint32_t)kre << sh) | ((uint32_t)kim << (sh + 8));
+      reinterpret_cast<uint32_t*>(*xnxt + (size_t)s * pp)[wd] = word;
+      if (wd == 0) {
+        const float aim = (float)(2 * kim - (P - 1)) * c.alpha, are = (float)(2 * kre - (P - 1)) * c.alpha;
+        const float d1 = fmaf(-r11, aim, w.cc[t]);
+        const float p1 = fmaf(d1, d1, (*pcur)[t]);
+        const float d0 = fmaf(-r00, are, fmaf(-r01, aim, w.cc[K + t]));
+        (*pnxt)[s] = fmaf(d0, d0, p1);
+      }
+    }
+    *nodes += S;
+    *peds += (long long)S * Q;
+    *flops += (long long)S * (4 * (n - 2 - r0) + 10 * Q);
+    __syncthreads();
+    uint8_t* tx = *xcur;
+    *xcur = *xnxt;
+    *xnxt = tx;
+    float* tp = *pcur;
+    *pcur = *pnxt;
+    *pnxt = tp;
+    S = kept;
+  }
+  return S;
+}
+
 // Stage R and ybar of vector v into shared memory and compute E and r2.
 __device__ void stage_vector(const SearchArgs& a, int v, const KbLayout& L, unsigned char* smem,
                              float* misc_f) {
@@ -599,8 +702,19 @@ __global__ void __launch_bounds__(1024) kbest_kernel(SearchArgs a, KbLayout L) {
       pnxt = reinterpret_cast<float*>(smem + L.off_pb);
       if (tid == 0) pcur[0] = 0.0f;
       __syncthreads();
-      if (a.flags & MDX_COMPLEX_TREE) {
+      if ((a.flags & MDX_COMPLEX_TREE) && L.E == 0) {
         S = kbest_levels_complex(c, 1, &xcur, &xnxt, &pcur, &pnxt, &misc_f[1], E, &nodes, &peds, &flops);
+      } else if (a.flags & MDX_COMPLEX_TREE) {
+        const CtaRun run{c.cc, keys, misc + 8};
+        if (L.E == 1)
+          S = cta_kbest_levels_complex<1>(c, L.lp, run, &xcur, &xnxt, &pcur, &pnxt, &misc_f[1], E, &nodes, &peds,
+                                          &flops);
+        else if (L.E == 2)
+          S = cta_kbest_levels_complex<2>(c, L.lp, run, &xcur, &xnxt, &pcur, &pnxt, &misc_f[1], E, &nodes, &peds,
+                                          &flops);
+        else
+          S = cta_kbest_levels_complex<4>(c, L.lp, run, &xcur, &xnxt, &pcur, &pnxt, &misc_f[1], E, &nodes, &peds,
+                                          &flops);
       } else if (L.E == 0) {
         S = kbest_levels(c, n - 1, 1, &xcur, &xnxt, &pcur, &pnxt, &misc_f[1], E, &nodes, &peds, &flops);
       } else {
@@ -1063,6 +1177,28 @@ void kb_geometry(KbLayout& L, int n, int K, int P) {
   L.init(n, K, P, T * E);
 }
 
+// Complex tree: the same with Q = P^2 children per survivor (lp holds log2 Q).
+void kb_geometry_complex(KbLayout& L, int n, int K, int P) {
+  const int Q = P * P, Kp = pow2ceil(K), C = Kp * Q;
+  int T = C / 4;
+  if (T < 32) T = 32;
+  if (T > 512) T = 512;
+  int E = 1;
+  while (T * E < C || 32 * E < Kp) E <<= 1;
+  L.lp = 0;
+  while ((1 << L.lp) < Q) ++L.lp;
+  L.G = 1;
+  if (E > 4) {
+    L.T = kb_threads(K, Q);
+    L.E = 0;
+    L.init(n, K, P, C < 2 ? 2 : C);
+    return;
+  }
+  L.T = T;
+  L.E = E;
+  L.init(n, K, P, T * E);
+}
+
 int kb_threads(int K, int P) {
   int C = pow2ceil(K * P);
   int T = C / 2;
@@ -1090,7 +1226,7 @@ cudaError_t launch_generic(const void* fn, const SearchArgs& a, const KbLayout& 
 size_t kbest_smem_bytes(int n, int K, int P, bool complex_tree) {
   KbLayout L;
   if (complex_tree) {
-    L.init(n, K, P, pow2ceil(K * P * P));
+    kb_geometry_complex(L, n, K, P);
   } else {
     kb_geometry(L, n, K, P);
   }
@@ -1101,10 +1237,9 @@ cudaError_t launch_kbest(const SearchArgs& a, int num_sms, cudaStream_t s) {
   if (a.batch <= 0) return cudaSuccess;
   KbLayout L;
   if (a.flags & MDX_COMPLEX_TREE) {
-    const int C = pow2ceil(a.K * a.P * a.P);
-    L.init(a.n, a.K, a.P, C < 2 ? 2 : C);
+    kb_geometry_complex(L, a.n, a.K, a.P);
     if (L.bytes > 227 * 1024) return cudaErrorInvalidConfiguration;
-    return launch_generic((const void*)kbest_kernel, a, L, kb_threads(a.K, a.P * a.P), num_sms, s);
+    return launch_generic((const void*)kbest_kernel, a, L, L.T, num_sms, s);
   }
   kb_geometry(L, a.n, a.K, a.P);
   if (L.bytes > 227 * 1024) return cudaErrorInvalidConfiguration;
