@@ -455,44 +455,53 @@ __device__ void qrd_panel(const QrdLayout& L, int k, int bw, double* Are, double
 }
 
 // One warp: columns c0..c0+7 of rows k..N8-1 updated by the panel's block
-// reflector, A_t <- A_t - V (Y^H A_t).
+// reflector, A_t <- A_t - V (Y^H A_t).  Each complex product takes three real
+// MMAs instead of four (Gauss): for W = Y^H A_t, with A1 = Yr^T Ar,
+// A2 = Yi^T Ai and A3 = (Yr - Yi)^T (Ar + Ai), Re W = A1 + A2 and
+// Im W = A3 - A1 + A2; for V W, with T1 = Vr Wr, T2 = Vi Wi and
+// T3 = (Vr + Vi)(Wr + Wi), Re = T1 - T2 and Im = T3 - T1 - T2.  An MMA holds
+// the FP64 unit about eight times as long as the FP64 addition that forms an
+// operand sum, so the trade saves FP64 time.
 __device__ void qrd_tile(const QrdLayout& L, int k, int c0, double* Are, double* Aim, const double* Vre,
                          const double* Vim, const double* Yre, const double* Yim, double* tre, double* tim,
                          int lane) {
   const int S = L.S, g = lane >> 2, q = lane & 3;
   const int R8 = L.N8 - k;
-  // W = Y^H A_t: A operand (Y^H)[i][rr] = conj(Y[rr][i]), B operand A_t[rr][c];
-  // even and odd k-steps accumulate separately (four independent chains)
-  double ar0 = 0.0, ar1 = 0.0, ai0 = 0.0, ai1 = 0.0, br0 = 0.0, br1 = 0.0, bi0 = 0.0, bi1 = 0.0;
+  // A operand (Y^H)[i][rr] -> Y[rr][i], B operand A_t[rr][c]; even and odd
+  // k-steps accumulate separately (six independent chains)
+  double p10 = 0.0, p11 = 0.0, p20 = 0.0, p21 = 0.0, p30 = 0.0, p31 = 0.0;
+  double q10 = 0.0, q11 = 0.0, q20 = 0.0, q21 = 0.0, q30 = 0.0, q31 = 0.0;
   const double* bre = Are + (size_t)(c0 + g) * S + k;
   const double* bim = Aim + (size_t)(c0 + g) * S + k;
   const double* yre = Yre + g * S;
   const double* yim = Yim + g * S;
-  int ks = 0;
-  for (; ks + 8 <= R8; ks += 8) {
+  for (int ks = 0; ks + 8 <= R8; ks += 8) {
     {
       const double vr = yre[ks + q], vi = yim[ks + q], xr = bre[ks + q], xi = bim[ks + q];
-      dmma(ar0, ar1, vr, xr);
-      dmma(ai0, ai1, vr, xi);
-      dmma(ar0, ar1, vi, xi);
-      dmma(ai0, ai1, ineg(vi), xr);
+      dmma(p10, p11, vr, xr);
+      dmma(p20, p21, vi, xi);
+      dmma(p30, p31, vr - vi, xr + xi);
     }
     {
       const double vr = yre[ks + 4 + q], vi = yim[ks + 4 + q], xr = bre[ks + 4 + q], xi = bim[ks + 4 + q];
-      dmma(br0, br1, vr, xr);
-      dmma(bi0, bi1, vr, xi);
-      dmma(br0, br1, vi, xi);
-      dmma(bi0, bi1, ineg(vi), xr);
+      dmma(q10, q11, vr, xr);
+      dmma(q20, q21, vi, xi);
+      dmma(q30, q31, vr - vi, xr + xi);
     }
   }
-  tre[(2 * q) * kTileStride + g] = ar0 + br0;
-  tre[(2 * q + 1) * kTileStride + g] = ar1 + br1;
-  tim[(2 * q) * kTileStride + g] = ai0 + bi0;
-  tim[(2 * q + 1) * kTileStride + g] = ai1 + bi1;
+  {
+    const double a10 = p10 + q10, a11 = p11 + q11, a20 = p20 + q20, a21 = p21 + q21;
+    const double a30 = p30 + q30, a31 = p31 + q31;
+    tre[(2 * q) * kTileStride + g] = a10 + a20;
+    tre[(2 * q + 1) * kTileStride + g] = a11 + a21;
+    tim[(2 * q) * kTileStride + g] = (a30 - a10) + a20;
+    tim[(2 * q + 1) * kTileStride + g] = (a31 - a11) + a21;
+  }
   __syncwarp();
   // A_t -= V W, row tiles of 8 (two at a time): A operand V[r][i], B operand W[i][n]
   const double w0r = tre[g * kTileStride + q], w0i = tim[g * kTileStride + q];
   const double w1r = tre[g * kTileStride + 4 + q], w1i = tim[g * kTileStride + 4 + q];
+  const double w0s = w0r + w0i, w1s = w1r + w1i;
   __syncwarp();
   for (int m0 = 0; m0 < R8; m0 += 16) {
     const bool two = m0 + 8 < R8;
@@ -506,31 +515,31 @@ __device__ void qrd_tile(const QrdLayout& L, int k, int c0, double* Are, double*
       di0 = pi0[8];
       di1 = pi0[S + 8];
     }
+    double t10 = 0.0, t11 = 0.0, t20 = 0.0, t21 = 0.0, u10 = 0.0, u11 = 0.0, u20 = 0.0, u21 = 0.0;
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
-      const double wr = h ? w1r : w0r, wi = h ? w1i : w0i;
+      const double wr = h ? w1r : w0r, wi = h ? w1i : w0i, ws = h ? w1s : w0s;
       const double vr = Vre[(4 * h + q) * S + m0 + g], vi = Vim[(4 * h + q) * S + m0 + g];
-      dmma(cr0, cr1, ineg(vr), wr);
-      dmma(ci0, ci1, ineg(vr), wi);
-      dmma(cr0, cr1, vi, wi);
-      dmma(ci0, ci1, ineg(vi), wr);
+      dmma(t10, t11, vr, wr);
+      dmma(t20, t21, vi, wi);
+      dmma(ci0, ci1, ineg(vr + vi), ws);
       if (two) {
         const double ur = Vre[(4 * h + q) * S + m0 + 8 + g], ui = Vim[(4 * h + q) * S + m0 + 8 + g];
-        dmma(dr0, dr1, ineg(ur), wr);
-        dmma(di0, di1, ineg(ur), wi);
-        dmma(dr0, dr1, ui, wi);
-        dmma(di0, di1, ineg(ui), wr);
+        dmma(u10, u11, ur, wr);
+        dmma(u20, u21, ui, wi);
+        dmma(di0, di1, ineg(ur + ui), ws);
       }
     }
-    pr0[0] = cr0;
-    pr0[S] = cr1;
-    pi0[0] = ci0;
-    pi0[S] = ci1;
+    // Re -= T1 - T2, Im -= T3 - T1 - T2 (the T3 part is already in ci / di)
+    pr0[0] = (cr0 - t10) + t20;
+    pr0[S] = (cr1 - t11) + t21;
+    pi0[0] = (ci0 + t10) + t20;
+    pi0[S] = (ci1 + t11) + t21;
     if (two) {
-      pr0[8] = dr0;
-      pr0[S + 8] = dr1;
-      pi0[8] = di0;
-      pi0[S + 8] = di1;
+      pr0[8] = (dr0 - u10) + u20;
+      pr0[S + 8] = (dr1 - u11) + u21;
+      pi0[8] = (di0 + u10) + u20;
+      pi0[S + 8] = (di1 + u11) + u21;
     }
   }
   __syncwarp();
