@@ -428,14 +428,16 @@ __device__ void qrd_panel(const QrdLayout& L, int k, int bw, double* Are, double
         yr[j] = tj * ar;
         yi[j] = tj * ai;
       }
-      // ---- apply H_j to the panel columns right of j
+      // ---- apply H_j to the panel columns right of j: a_c -= (tau_j v_j) w_c
+      {
+        const double tvr = tj * pr[j], tvi = tj * pi[j];
 #pragma unroll
-      for (int c = 0; c < 8; ++c) {
-        if (c > j && in_j) {
-          const double wr = t[2 * (c - 1)] * tj, wi = t[2 * (c - 1) + 1] * tj;
-          const double vr = pr[j], vv = pi[j];
-          pr[c] -= fma(vr, wr, -vv * wi);
-          pi[c] -= fma(vr, wi, vv * wr);
+        for (int c = 0; c < 8; ++c) {
+          if (c > j && in_j) {
+            const double wr = t[2 * (c - 1)], wi = t[2 * (c - 1) + 1];
+            pr[c] = fma(-tvr, wr, fma(tvi, wi, pr[c]));
+            pi[c] = fma(-tvr, wi, fma(-tvi, wr, pi[c]));
+          }
         }
       }
     }
