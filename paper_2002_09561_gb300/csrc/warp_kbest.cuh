@@ -31,13 +31,48 @@ __device__ __forceinline__ float row_interference(const float* Rc, const float* 
   float acc[M];
 #pragma unroll
   for (int m = 0; m < M; ++m) acc[m] = (s + G * m == 0) ? yb[i] : 0.0f;
-  constexpr int kUnroll = M <= 2 ? 4 : 1;  // loads in flight without growing the chains' registers
-#pragma unroll kUnroll
-  for (int j0 = n - 1; j0 > i; j0 -= 8) {
+  if (M <= 2) {
+    // one or two chains per lane: software-pipelined in batches of four steps,
+    // the next batch's loads and level conversions issued before this batch's
+    // FMAs.  A step past the chain's end is fmaf(-0, 0, acc) = acc exactly.
+    constexpr int B = 4;
+    float rb[B][M], ab[B][M];
+    auto fetch = [&](int j0, float (&r)[B][M], float (&av)[B][M]) {
 #pragma unroll
-    for (int m = 0; m < M; ++m) {
-      const int j = j0 - (s + G * m);
-      if (j > i) acc[m] = fmaf(-Rc[col_off(j) + i], (float)(2 * (int)xp[j] - (P - 1)) * alpha, acc[m]);
+      for (int b = 0; b < B; ++b)
+#pragma unroll
+        for (int m = 0; m < M; ++m) {
+          const int j = j0 - 8 * b - (s + G * m);
+          const bool ok = j > i;
+          r[b][m] = ok ? Rc[col_off(j) + i] : 0.0f;
+          av[b][m] = ok ? (float)(2 * (int)xp[j] - (P - 1)) * alpha : 0.0f;
+        }
+    };
+    int j0 = n - 1;
+    fetch(j0, rb, ab);
+    while (j0 > i) {
+      float rn[B][M], an[B][M];
+      fetch(j0 - 8 * B, rn, an);
+#pragma unroll
+      for (int b = 0; b < B; ++b)
+#pragma unroll
+        for (int m = 0; m < M; ++m) acc[m] = fmaf(-rb[b][m], ab[b][m], acc[m]);
+#pragma unroll
+      for (int b = 0; b < B; ++b)
+#pragma unroll
+        for (int m = 0; m < M; ++m) {
+          rb[b][m] = rn[b][m];
+          ab[b][m] = an[b][m];
+        }
+      j0 -= 8 * B;
+    }
+  } else {
+    for (int j0 = n - 1; j0 > i; j0 -= 8) {
+#pragma unroll
+      for (int m = 0; m < M; ++m) {
+        const int j = j0 - (s + G * m);
+        if (j > i) acc[m] = fmaf(-Rc[col_off(j) + i], (float)(2 * (int)xp[j] - (P - 1)) * alpha, acc[m]);
+      }
     }
   }
 #pragma unroll
