@@ -754,7 +754,7 @@ __global__ void __launch_bounds__(1024) kbest_kernel(SearchArgs a, KbLayout L) {
 // shared-memory lock), and one K-best workspace per warp.  During the master
 // phase the warp workspaces double as the prefix sort buffer.
 struct HyLayout {
-  int n, K, P, W, pp, ts, Cw;  // Cw: key capacity per warp
+  int n, K, P, W, Wk, pp, ts, Cw;  // W warps per CTA, Wk of them with a K-best workspace; Cw: key capacity per warp
   size_t off_R, off_yb, off_idx, off_cx, off_cp, off_misc, off_m, off_warp, warp_bytes, bytes;
   // the best prefix's run by the whole CTA (cta = 0: by warp 0 alone): G threads
   // per survivor, E keys per thread, lp = log2 P; buffers at off_warp + run_*
@@ -770,11 +770,12 @@ __host__ __device__ inline size_t hy_warp_bytes(int n, int K, int P) {
   return (b + 15) / 16 * 16;
 }
 
-__host__ __device__ inline void hy_layout(HyLayout& L, int n, int K, int P, int W, size_t sort_bytes) {
+__host__ __device__ inline void hy_layout(HyLayout& L, int n, int K, int P, int W, int Wk, size_t sort_bytes) {
   L.n = n;
   L.K = K;
   L.P = P;
   L.W = W;
+  L.Wk = Wk;
   L.pp = path_stride(n);
   L.ts = tri_stride32(n);
   L.Cw = round_up(K, 8);
@@ -796,9 +797,9 @@ __host__ __device__ inline void hy_layout(HyLayout& L, int n, int K, int P, int 
   o = (o + 15) / 16 * 16;
   L.off_warp = o;
   L.warp_bytes = hy_warp_bytes(n, K, P);
-  // the warp workspaces double as the master's prefix sort buffer and as the
-  // buffers of the CTA's run
-  size_t need = ((sort_bytes + W - 1) / W + 15) / 16 * 16;
+  // the warp workspaces double as the master's prefix sort buffer, as the
+  // buffers of the CTA's run and as the re-scoring partials
+  size_t need = ((sort_bytes + Wk - 1) / Wk + 15) / 16 * 16;
   const int T = 32 * W, Kp = pow2ceil(K);
   L.lp = 0;
   while ((1 << L.lp) < P) ++L.lp;
@@ -824,12 +825,13 @@ __host__ __device__ inline void hy_layout(HyLayout& L, int n, int K, int P, int 
     L.run_bytes = r;
   }
   if (L.cta) {
-    const size_t per = ((L.run_bytes + W - 1) / W + 15) / 16 * 16;
+    const size_t per = ((L.run_bytes + Wk - 1) / Wk + 15) / 16 * 16;
     if (need < per) need = per;
   }
-  if (need < sizeof(double) * 224) need = sizeof(double) * 224;  // re-scoring partials, one row block per warp
+  const size_t part = ((sizeof(double) * 224 * W + Wk - 1) / Wk + 15) / 16 * 16;  // one row block per CTA warp
+  if (need < part) need = part;
   if (L.warp_bytes < need) L.warp_bytes = need;
-  o += L.warp_bytes * W;
+  o += L.warp_bytes * Wk;
   L.bytes = o;
 }
 
@@ -1005,7 +1007,7 @@ __global__ void hybrid_kernel(SearchArgs a, HyLayout L) {
       }
       for (int phase = L.cta ? 1 : 0; phase < 2; ++phase) {
        if (phase == 1) __syncthreads();
-       if (phase == 1 || warp == 0) {
+       if ((phase == 1 && warp < L.Wk) || warp == 0) {
         for (;;) {
         int t = 0;
         if (lane == 0) t = atomicAdd(&misc[2], 1);
@@ -1246,18 +1248,26 @@ cudaError_t launch_kbest(const SearchArgs& a, int num_sms, cudaStream_t s) {
   return launch_generic((const void*)kbest_kernel, a, L, L.T, num_sms, s);
 }
 
+// Eight warps per CTA with as many K-best workspaces as fit (the best prefix
+// runs on the whole CTA, the other prefixes on the warps with a workspace);
+// fewer warps only when not even one workspace fits beside eight warps' needs.
+bool hy_fit(HyLayout& L, int n, int K, int P, size_t sort_bytes) {
+  for (int W = 8; W >= 1; --W)
+    for (int Wk = W; Wk >= 1; --Wk) {
+      hy_layout(L, n, K, P, W, Wk, sort_bytes);
+      if (L.bytes <= 227 * 1024) return true;
+    }
+  return false;
+}
+
 cudaError_t launch_hybrid(const SearchArgs& a, int num_sms, cudaStream_t s) {
   if (a.batch <= 0) return cudaSuccess;
   int np = 1;
   for (int l = 0; l < a.depth; ++l) np *= a.P;
   const size_t sort_bytes = sizeof(uint64_t) * pow2ceil(np < 2 ? 2 : np);
   HyLayout L;
-  int W = 8;
-  for (; W >= 1; --W) {
-    hy_layout(L, a.n, a.K, a.P, W, sort_bytes);
-    if (L.bytes <= 227 * 1024) break;
-  }
-  if (W < 1) return cudaErrorInvalidConfiguration;
+  if (!hy_fit(L, a.n, a.K, a.P, sort_bytes)) return cudaErrorInvalidConfiguration;
+  const int W = L.W;
   const void* fn = (const void*)hybrid_kernel;
   cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.bytes);
   if (e != cudaSuccess) return e;
@@ -1276,11 +1286,7 @@ size_t hybrid_smem_bytes(int n, int K, int P, int depth) {
   for (int l = 0; l < depth; ++l) np *= P;
   const size_t sort_bytes = sizeof(uint64_t) * pow2ceil(np < 2 ? 2 : np);
   HyLayout L;
-  for (int W = 8; W >= 1; --W) {
-    hy_layout(L, n, K, P, W, sort_bytes);
-    if (L.bytes <= 227 * 1024) return L.bytes;
-  }
-  return (size_t)-1;
+  return hy_fit(L, n, K, P, sort_bytes) ? L.bytes : (size_t)-1;
 }
 
 }  // namespace mdx
