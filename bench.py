@@ -77,10 +77,10 @@ METRIC = "decoded vectors/s at matched BER (16x16 16QAM, 100x100 64QAM), learned
 # DRAM bytes (read + write) of the dominant kernel per vector, from one ncu
 # capture of the same kernel on a smaller run of the same workload (traffic
 # grows with the number of vectors); None where no capture of the current
-# kernel exists.  Captures: sd_kernel, 20,000 vectors: 154.1 MB read + 5.4 MB
-# written; hybrid_kernel, 2,000 vectors: 513.6 MB read + 3.8 MB written.
-TRAFFIC_PER_VECTOR = {"16x16-16qam-sd-learned": (154.095616e6 + 5.353216e6) / 20000,
-                      "100x100-64qam-hybrid32-learned": (513.629952e6 + 3.825664e6) / 2000}
+# kernel exists.  Captures: sd_kernel, 20,000 vectors: 154.2 MB read + 4.8 MB
+# written; hybrid_kernel, 2,000 vectors: 517.5 MB read + 4.1 MB written.
+TRAFFIC_PER_VECTOR = {"16x16-16qam-sd-learned": (154.186752e6 + 4.764160e6) / 20000,
+                      "100x100-64qam-hybrid32-learned": (517.457664e6 + 4.140800e6) / 2000}
 FP32_LANES_PER_SM = 128  # FP32 FMA lanes per SM (4 sub-partitions x 32)
 
 
