@@ -155,8 +155,9 @@ __device__ int cta_kbest_levels(const float* Rc, const float* yb, int n, int P, 
       // levels whose children fit in one warp: warp 0 alone, no CTA barrier
       if (warp == 0) {
         int steps = 0;
+        // nothing else changes the radius during a CTA's run
+        const float b = prune_bound(__uint_as_float(*(volatile const unsigned int*)r2bits), Es, n);
         while (i >= 0 && S > 0 && S * P <= 32) {
-          const float b = prune_bound(__uint_as_float(*(volatile const unsigned int*)r2bits), Es, n);
           const int kept = warp_level_small<SE>(Rc, yb, n, P, K, pp, alpha, i, b, S, *xcur, *xnxt, *pcur, *pnxt, lane);
           *nodes += S;
           *flops += (long long)S * (2 * (n - 1 - i) + 4 * P);

@@ -199,6 +199,18 @@ def test_hybrid_survivor_widths(env, N, qam, K, d, snr):
     _compare(gpu, ref, KB_GAP, label=f"hybrid {N}x{N} {qam}-QAM K={K} d={d}")
 
 
+def test_hybrid_100x100_64qam_k128_two_workspaces(env):
+    """K = 128 at 100x100: only two K-best workspaces fit beside R, so the
+    best prefix runs on the whole CTA and the others on two of its eight warps."""
+    w = wl.generate(72, 8, 100, 100, 64, 28.0)
+    gpu = _run(env, "hybrid", w, 64, K=128, depth=4, radius="paper")
+    ref = oracle.detect_batch("hybrid", w["H"], w["y"], w["noise_var"], 64, K=128, depth=4, radius="paper")
+    same = (gpu[0] == ref["sym"]).all(axis=1)
+    assert same.mean() >= 7 / 8
+    rel = np.abs(gpu[1] - ref["metric"]) / ref["metric"]
+    assert rel[same].max() < MET_RTOL
+
+
 def test_hybrid_100x100_64qam_sample(env):
     w = wl.generate(71, 6, 100, 100, 64, 28.0)
     gpu = _run(env, "hybrid", w, 64, K=32, depth=4, radius="paper")
