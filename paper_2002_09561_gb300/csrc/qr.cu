@@ -1,11 +1,13 @@
 // Batched FP64 QR preprocessing (Sec. III-B): H = QR with a real positive
 // diagonal and ybar = Q^H y, by complex Householder reflections applied to the
-// augmented matrix [H | y] held in shared memory.  One CTA per matrix; the
-// CTA's lanes are split into column workers of LPC lanes each (LPC = 16 for
-// n_rx <= 16, else 32): worker 0 forms the reflector of column k, then every
-// worker applies it to its share of the remaining columns.  The complex R is
-// written out in the real interleaved form (entry r_ab -> [[Re,-Im],[Im,Re]])
-// that the tree search uses.
+// augmented matrix [H | y].  Three forms: up to 32 receive antennas, several
+// matrices per warp held in registers (qr_small_kernel, below); beyond that one
+// CTA per matrix in shared memory, either with column workers of 32 lanes
+// (qr_kernel: worker 0 forms the reflector of column k, then every worker
+// applies it to its share of the remaining columns) or, from 48 transmit
+// antennas, blocked with FP64 MMA trailing updates (qr_dmma_kernel).  The
+// complex R is written out in the real interleaved form (entry r_ab ->
+// [[Re,-Im],[Im,Re]]) that the tree search uses.
 #include "mdx_internal.cuh"
 
 namespace mdx {
@@ -631,23 +633,25 @@ __global__ void __launch_bounds__(kQrdWarps * 32, 1)
 }
 
 // ---------------------------------------------------------------------------
-// Small systems (n_rx <= 16): the same reflectors, column by column in the
+// Small systems (n_rx <= 32): the same reflectors, column by column in the
 // left-looking order (column j receives reflectors 0..j-1, then forms its own),
-// for 16 matrices per warp with two lanes per matrix: lane 2m + h holds rows
-// r = 2q + h (q < 8) of matrix m's current column in registers.  An FP64
+// for 32 / L matrices per warp with L lanes per matrix (L = 2 for n_rx <= 16,
+// 4 for n_rx <= 32): lane L m + h holds rows r = L q + h (q < 8) of matrix
+// m's current column in registers.  An FP64
 // instruction occupies its scheduler's FP64 unit for about 70 cycles however
 // many lanes it serves, so here every lane does useful FMAs and a reflector
 // costs one two-lane reduction, where one CTA per matrix spends most of its
 // FP64 instructions on cross-lane sums and idle rows.  The reflectors v_k
-// (rows k..N-1) and tau_k live in shared memory, entry-major with the 16
+// (rows k..N-1) and tau_k live in shared memory, entry-major with the warp's
 // matrices innermost (consecutive lanes read consecutive 16-byte entries);
 // the phases of R's rows stay in the registers of the lanes owning them.
-constexpr int kQsMats = 16;  // matrices per warp
-constexpr int kQsSlots = 8;  // rows per lane (n_rx <= 16)
+constexpr int kQsSlots = 8;  // rows per lane (n_rx <= 8 L)
 
 __host__ __device__ inline int qs_vo(int k, int N) { return k * N - k * (k - 1) / 2; }  // first entry of v_k
+__host__ __device__ inline int qs_lanes(int N) { return N <= 16 ? 2 : 4; }
 __host__ __device__ inline size_t qs_smem(int N, int M) {
-  return sizeof(double2) * kQsMats * (size_t)qs_vo(M, N) + sizeof(double) * kQsMats * (size_t)M;
+  const int mats = 32 / qs_lanes(N);
+  return sizeof(double2) * mats * (size_t)qs_vo(M, N) + sizeof(double) * mats * (size_t)M;
 }
 
 // One R entry z = R_kc (complex, after the phase fix) in the real interleaved
@@ -666,12 +670,14 @@ __device__ __forceinline__ void qs_put(const QrDst& out, int n, int k, int c, do
   }
 }
 
-// Factorises the [H | y] of this lane pair (act: the pair has a matrix).
+// Factorises the [H | y] of this lane group (act: the group has a matrix).
 // Hb: row-major N x M complex, yb: N complex.  Every lane of the warp calls
 // this with the same N, M (shuffles inside).
+template <int L>
 __device__ void qr_small_pair(int N, int M, bool act, const double2* __restrict__ Hb,
                               const double2* __restrict__ yv, const QrDst& out, double2* V, double* Tau) {
-  const int lane = threadIdx.x & 31, m = lane >> 1, h = lane & 1;
+  constexpr int kQsMats = 32 / L;
+  const int lane = threadIdx.x & 31, m = lane / L, h = lane % L;
   const int n = 2 * M;
   double2 a[kQsSlots], ph[kQsSlots];
 #pragma unroll
@@ -680,34 +686,37 @@ __device__ void qr_small_pair(int N, int M, bool act, const double2* __restrict_
   for (int j = 0; j <= M; ++j) {
 #pragma unroll
     for (int q = 0; q < kQsSlots; ++q) {
-      const int r = 2 * q + h;
+      const int r = L * q + h;
       a[q] = make_double2(0.0, 0.0);
       if (act && r < N) a[q] = (j < M) ? Hb[(size_t)r * M + j] : yv[r];
     }
     // reflectors 0 .. j-1: a <- a - v_k tau_k (v_k^H a) over rows k..N-1
     const int kend = j < M ? j : M;
     for (int k = 0; k < kend; ++k) {
-      const double2* vk = V + (size_t)(qs_vo(k, N) - k) * kQsMats + m;  // entry r at vk[r * 16]
+      const double2* vk = V + (size_t)(qs_vo(k, N) - k) * kQsMats + m;  // entry r at vk[r * kQsMats]
       double wr = 0.0, wi = 0.0;
 #pragma unroll
       for (int q = 0; q < kQsSlots; ++q) {
-        const int r = 2 * q + h;
-        if (2 * q + 1 < k || 2 * q >= N) continue;  // neither lane of the pair has this row
+        const int r = L * q + h;
+        if (L * q + L - 1 < k || L * q >= N) continue;  // no lane of the group has this row
         if (r >= k && r < N) {
           const double2 v = vk[(size_t)r * kQsMats];
           wr = fma(v.x, a[q].x, fma(v.y, a[q].y, wr));
           wi = fma(v.x, a[q].y, fma(-v.y, a[q].x, wi));
         }
       }
-      wr += __shfl_xor_sync(0xffffffffu, wr, 1);
-      wi += __shfl_xor_sync(0xffffffffu, wi, 1);
+#pragma unroll
+      for (int o = 1; o < L; o <<= 1) {
+        wr += __shfl_xor_sync(0xffffffffu, wr, o);
+        wi += __shfl_xor_sync(0xffffffffu, wi, o);
+      }
       const double tk = Tau[k * kQsMats + m];
       wr *= tk;
       wi *= tk;
 #pragma unroll
       for (int q = 0; q < kQsSlots; ++q) {
-        const int r = 2 * q + h;
-        if (2 * q + 1 < k || 2 * q >= N) continue;
+        const int r = L * q + h;
+        if (L * q + L - 1 < k || L * q >= N) continue;
         if (r >= k && r < N) {
           const double2 v = vk[(size_t)r * kQsMats];
           a[q].x = fma(-v.x, wr, fma(v.y, wi, a[q].x));
@@ -719,7 +728,7 @@ __device__ void qr_small_pair(int N, int M, bool act, const double2* __restrict_
       // column j of R above the diagonal: rows k < j, final now, phase-fixed
 #pragma unroll
       for (int q = 0; q < kQsSlots; ++q) {
-        const int r = 2 * q + h;
+        const int r = L * q + h;
         if (act && r < j) {
           const double re = a[q].x * ph[q].x + a[q].y * ph[q].y, im = a[q].y * ph[q].x - a[q].x * ph[q].y;
           qs_put(out, n, r, j, re, im);
@@ -730,14 +739,15 @@ __device__ void qr_small_pair(int N, int M, bool act, const double2* __restrict_
       double2 x0 = make_double2(0.0, 0.0);
 #pragma unroll
       for (int q = 0; q < kQsSlots; ++q) {
-        const int r = 2 * q + h;
+        const int r = L * q + h;
         if (r >= j && r < N) s = fma(a[q].x, a[q].x, fma(a[q].y, a[q].y, s));
         if (r == j) x0 = a[q];
       }
-      s += __shfl_xor_sync(0xffffffffu, s, 1);
-      const int h0 = j & 1;
-      x0.x = __shfl_sync(0xffffffffu, x0.x, (lane & ~1) | h0);
-      x0.y = __shfl_sync(0xffffffffu, x0.y, (lane & ~1) | h0);
+#pragma unroll
+      for (int o = 1; o < L; o <<= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+      const int h0 = j % L;
+      x0.x = __shfl_sync(0xffffffffu, x0.x, (lane & ~(L - 1)) | h0);
+      x0.y = __shfl_sync(0xffffffffu, x0.y, (lane & ~(L - 1)) | h0);
       double sigma = 0.0, tj = 0.0;
       double2 phr = make_double2(1.0, 0.0), al = make_double2(0.0, 0.0);
       if (s > 0.0) {
@@ -761,7 +771,7 @@ __device__ void qr_small_pair(int N, int M, bool act, const double2* __restrict_
       double2* vj = V + (size_t)(qs_vo(j, N) - j) * kQsMats + m;
 #pragma unroll
       for (int q = 0; q < kQsSlots; ++q) {
-        const int r = 2 * q + h;
+        const int r = L * q + h;
         if (r >= j && r < N) vj[(size_t)r * kQsMats] = (r == j) ? make_double2(x0.x - al.x, x0.y - al.y) : a[q];
         if (r == j) ph[q] = phr;
       }
@@ -771,7 +781,7 @@ __device__ void qr_small_pair(int N, int M, bool act, const double2* __restrict_
       // ybar = Q^H y: rows k < M of the y column, phase-fixed
 #pragma unroll
       for (int q = 0; q < kQsSlots; ++q) {
-        const int r = 2 * q + h;
+        const int r = L * q + h;
         if (act && r < M) {
           const double re = a[q].x * ph[q].x + a[q].y * ph[q].y, im = a[q].y * ph[q].x - a[q].x * ph[q].y;
           if (out.yb64) {
@@ -793,19 +803,21 @@ __device__ void qr_small_pair(int N, int M, bool act, const double2* __restrict_
   }
   if (act) {
     if (out.Rdense)
-      for (int t = h; t < n * n; t += 2)
+      for (int t = h; t < n * n; t += L)
         if (t / n > t % n) out.Rdense[t] = 0.0;
     if (h == 0 && out.singular) *out.singular = sing;
   }
 }
 
+template <int L>
 __global__ void __launch_bounds__(32) qr_small_kernel(int batch, int N, int M, const double* __restrict__ H,
                                                       const double* __restrict__ y, QrOut out) {
+  constexpr int kQsMats = 32 / L;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   double2* V = reinterpret_cast<double2*>(smem_raw);
   double* Tau = reinterpret_cast<double*>(V + (size_t)kQsMats * qs_vo(M, N));
   const int lane = threadIdx.x & 31;
-  const int b = blockIdx.x * kQsMats + (lane >> 1);
+  const int b = blockIdx.x * kQsMats + lane / L;
   const bool act = b < batch;
   const int n = 2 * M;
   const int bb = act ? b : 0;
@@ -817,27 +829,29 @@ __global__ void __launch_bounds__(32) qr_small_kernel(int batch, int N, int M, c
   d.Rdense = out.Rdense ? out.Rdense + (size_t)bb * n * n : nullptr;
   d.ybdense = out.ybdense ? out.ybdense + (size_t)bb * n : nullptr;
   d.singular = out.singular ? out.singular + bb : nullptr;
-  qr_small_pair(N, M, act, reinterpret_cast<const double2*>(H) + (size_t)bb * N * M,
+  qr_small_pair<L>(N, M, act, reinterpret_cast<const double2*>(H) + (size_t)bb * N * M,
                 reinterpret_cast<const double2*>(y) + (size_t)bb * N, d, V, Tau);
 }
 
 // Uneven batches: the listed requests (all N x M) at their own offsets.
+template <int L>
 __global__ void __launch_bounds__(32) qr_small_gather_kernel(int count, const int* __restrict__ ids,
                                                              const MixedReq* __restrict__ reqs,
                                                              const double* __restrict__ H,
                                                              const double* __restrict__ y, int N, int M,
                                                              QrOut out) {
+  constexpr int kQsMats = 32 / L;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   double2* V = reinterpret_cast<double2*>(smem_raw);
   double* Tau = reinterpret_cast<double*>(V + (size_t)kQsMats * qs_vo(M, N));
   const int lane = threadIdx.x & 31;
-  const int i = blockIdx.x * kQsMats + (lane >> 1);
+  const int i = blockIdx.x * kQsMats + lane / L;
   const bool act = i < count;
   const MixedReq q = reqs[ids[act ? i : 0]];
   const int r = ids[act ? i : 0];
   QrDst d{out.R64 + q.r_off64, out.yb64 + q.y_off64, out.R32 + q.r_off, out.yb32 + q.y_off, nullptr, nullptr,
           out.singular + r};
-  qr_small_pair(N, M, act, reinterpret_cast<const double2*>(H + q.h_off),
+  qr_small_pair<L>(N, M, act, reinterpret_cast<const double2*>(H + q.h_off),
                 reinterpret_cast<const double2*>(y + q.yin_off), d, V, Tau);
 }
 
@@ -900,10 +914,15 @@ cudaError_t launch_qr_gather(int count, int n_rx, int n_tx, const int* ids, cons
     qr_dmma_gather_kernel<<<count, kQrdWarps * 32, sm, s>>>(count, ids, reqs, H, y, out);
     return cudaGetLastError();
   }
-  if (n_rx <= 16) {
+  if (n_rx <= 32) {
     const size_t sm = qs_smem(n_rx, n_tx);
-    cudaFuncSetAttribute(qr_small_gather_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    qr_small_gather_kernel<<<(count + kQsMats - 1) / kQsMats, 32, sm, s>>>(count, ids, reqs, H, y, n_rx, n_tx, out);
+    if (n_rx <= 16) {
+      cudaFuncSetAttribute(qr_small_gather_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+      qr_small_gather_kernel<2><<<(count + 15) / 16, 32, sm, s>>>(count, ids, reqs, H, y, n_rx, n_tx, out);
+    } else {
+      cudaFuncSetAttribute(qr_small_gather_kernel<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+      qr_small_gather_kernel<4><<<(count + 7) / 8, 32, sm, s>>>(count, ids, reqs, H, y, n_rx, n_tx, out);
+    }
     return cudaGetLastError();
   }
   const size_t smem = qr_smem(n_rx, n_tx);
@@ -924,11 +943,16 @@ cudaError_t launch_qr(int batch, int n_rx, int n_tx, const double* H, const doub
     qr_dmma_kernel<<<batch, kQrdWarps * 32, sm, s>>>(batch, n_rx, n_tx, H, y, out);
     return cudaGetLastError();
   }
-  if (n_rx <= 16) {
-    // 16 matrices per warp, two lanes per matrix
+  if (n_rx <= 32) {
+    // 16 matrices per warp with two lanes each (n_rx <= 16), else 8 with four
     const size_t sm = qs_smem(n_rx, n_tx);
-    cudaFuncSetAttribute(qr_small_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    qr_small_kernel<<<(batch + kQsMats - 1) / kQsMats, 32, sm, s>>>(batch, n_rx, n_tx, H, y, out);
+    if (n_rx <= 16) {
+      cudaFuncSetAttribute(qr_small_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+      qr_small_kernel<2><<<(batch + 15) / 16, 32, sm, s>>>(batch, n_rx, n_tx, H, y, out);
+    } else {
+      cudaFuncSetAttribute(qr_small_kernel<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+      qr_small_kernel<4><<<(batch + 7) / 8, 32, sm, s>>>(batch, n_rx, n_tx, H, y, out);
+    }
     return cudaGetLastError();
   }
   const size_t smem = qr_smem(n_rx, n_tx);

@@ -71,6 +71,7 @@ def _compare(gpu, ref, gap_tol, max_mismatch=0.01, label=""):
 
 
 @pytest.mark.parametrize("N,M,B", [(4, 4, 64), (16, 16, 256), (12, 8, 33), (15, 13, 17), (16, 1, 3), (7, 7, 50),
+                                   (32, 32, 20), (24, 20, 9), (17, 17, 11),
                                    (40, 24, 9), (64, 48, 5), (70, 64, 7), (100, 100, 3), (1, 1, 5)])
 def test_qr_matches_oracle(env, N, M, B):
     torch, mdx, ctx = env
