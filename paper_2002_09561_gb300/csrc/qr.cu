@@ -223,7 +223,7 @@ __device__ void qr_one(int N, int M, const double2* __restrict__ Hb, const doubl
 // rounded up to 8), zero-padded to N8 rows and C8 = round_up(M + 1, 8)
 // columns, so the MMA tiles need no masks; the padding stays zero.
 
-constexpr int kQrdWarps = 8;
+constexpr int kQrdWarps = 8;  // per CTA where one matrix fills the SM's shared memory, else 4 (two CTAs per SM)
 constexpr int kPanelWarps = 4;
 constexpr int kTileStride = 12;  // doubles per column of a warp's 8 x 8 tile
 
@@ -231,7 +231,7 @@ struct QrdLayout {
   int N8, C8, S;
   size_t off_are, off_aim, off_vre, off_vim, off_yre, off_yim, off_tile, off_red, off_alpha, off_tau, off_sing,
       bytes;
-  __host__ __device__ void init(int N, int M) {
+  __host__ __device__ void init(int N, int M, int warps) {
     N8 = round_up(N, 8);
     C8 = round_up(M + 1, 8);
     S = N8 + 4;
@@ -247,7 +247,7 @@ struct QrdLayout {
     off_vim = take(sizeof(double) * 8 * (size_t)S);
     off_yre = take(sizeof(double) * 8 * (size_t)S);
     off_yim = take(sizeof(double) * 8 * (size_t)S);
-    off_tile = take(sizeof(double) * 2 * 8 * kTileStride * kQrdWarps);
+    off_tile = take(sizeof(double) * 2 * 8 * kTileStride * warps);
     off_red = take(sizeof(double) * (8 + 2 * 16 * kPanelWarps));
     off_alpha = take(sizeof(double2) * (size_t)M);
     off_tau = take(sizeof(double) * (size_t)M);
@@ -549,12 +549,13 @@ __device__ void qrd_tile(const QrdLayout& L, int k, int c0, double* Are, double*
   __syncwarp();
 }
 
-// Factorises one [H | y] with the calling CTA (kQrdWarps warps).
+// Factorises one [H | y] with the calling CTA (4 or 8 warps; warps 0..3 factor
+// the panels, all of them update the trailing columns).
 __device__ void qr_dmma_one(int N, int M, const double2* __restrict__ Hb, const double2* __restrict__ yb,
                             const QrDst& out) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   QrdLayout L;
-  L.init(N, M);
+  L.init(N, M, (int)(blockDim.x >> 5));
   double* Are = reinterpret_cast<double*>(smem_raw + L.off_are);
   double* Aim = reinterpret_cast<double*>(smem_raw + L.off_aim);
   double* Vre = reinterpret_cast<double*>(smem_raw + L.off_vre);
@@ -602,7 +603,8 @@ __device__ void qr_dmma_one(int N, int M, const double2* __restrict__ Hb, const 
   if (out.singular && tid == 0) *out.singular = *sing;
 }
 
-__global__ void __launch_bounds__(kQrdWarps * 32, 1)
+template <int WQ>
+__global__ void __launch_bounds__(WQ * 32, WQ == kPanelWarps ? 2 : 1)
     qr_dmma_kernel(int batch, int N, int M, const double* __restrict__ H, const double* __restrict__ y,
                    QrOut out) {
   const int b = blockIdx.x;
@@ -620,7 +622,8 @@ __global__ void __launch_bounds__(kQrdWarps * 32, 1)
               reinterpret_cast<const double2*>(y) + (size_t)b * N, d);
 }
 
-__global__ void __launch_bounds__(kQrdWarps * 32, 1)
+template <int WQ>
+__global__ void __launch_bounds__(WQ * 32, WQ == kPanelWarps ? 2 : 1)
     qr_dmma_gather_kernel(int count, const int* __restrict__ ids, const MixedReq* __restrict__ reqs,
                           const double* __restrict__ H, const double* __restrict__ y, QrOut out) {
   if ((int)blockIdx.x >= count) return;
@@ -860,12 +863,19 @@ __global__ void __launch_bounds__(32) qr_small_gather_kernel(int count, const in
 #define MDX_QRD_MIN_TX 48
 #endif
 constexpr int kQrdMinTx = MDX_QRD_MIN_TX;
-size_t qrd_smem(int n_rx, int n_tx) {
+size_t qrd_smem(int n_rx, int n_tx, int warps) {
   QrdLayout L;
-  L.init(n_rx, n_tx);
+  L.init(n_rx, n_tx, warps);
   return L.bytes;
 }
-bool use_qrd(int n_rx, int n_tx) { return n_tx >= kQrdMinTx && n_rx <= 128 && qrd_smem(n_rx, n_tx) <= 227 * 1024; }
+bool use_qrd(int n_rx, int n_tx) {
+  return n_tx >= kQrdMinTx && n_rx <= 128 && qrd_smem(n_rx, n_tx, kQrdWarps) <= 227 * 1024;
+}
+// Four warps per CTA when two such CTAs fit in one SM's shared memory: one
+// matrix's panel then overlaps the other's trailing update.
+int qrd_warps(int n_rx, int n_tx) {
+  return 2 * qrd_smem(n_rx, n_tx, kPanelWarps) <= 227 * 1024 ? kPanelWarps : kQrdWarps;
+}
 
 template <int LPC>
 __global__ void qr_kernel(int batch, int N, int M, const double* __restrict__ H,
@@ -909,9 +919,15 @@ cudaError_t launch_qr_gather(int count, int n_rx, int n_tx, const int* ids, cons
                              const double* H, const double* y, QrOut out, cudaStream_t s) {
   if (count <= 0) return cudaSuccess;
   if (use_qrd(n_rx, n_tx)) {
-    const size_t sm = qrd_smem(n_rx, n_tx);
-    cudaFuncSetAttribute(qr_dmma_gather_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    qr_dmma_gather_kernel<<<count, kQrdWarps * 32, sm, s>>>(count, ids, reqs, H, y, out);
+    const int wq = qrd_warps(n_rx, n_tx);
+    const size_t sm = qrd_smem(n_rx, n_tx, wq);
+    if (wq == kPanelWarps) {
+      cudaFuncSetAttribute(qr_dmma_gather_kernel<kPanelWarps>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+      qr_dmma_gather_kernel<kPanelWarps><<<count, wq * 32, sm, s>>>(count, ids, reqs, H, y, out);
+    } else {
+      cudaFuncSetAttribute(qr_dmma_gather_kernel<kQrdWarps>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+      qr_dmma_gather_kernel<kQrdWarps><<<count, wq * 32, sm, s>>>(count, ids, reqs, H, y, out);
+    }
     return cudaGetLastError();
   }
   if (n_rx <= 32) {
@@ -938,9 +954,15 @@ cudaError_t launch_qr(int batch, int n_rx, int n_tx, const double* H, const doub
                       cudaStream_t s) {
   if (batch <= 0) return cudaSuccess;
   if (use_qrd(n_rx, n_tx)) {
-    const size_t sm = qrd_smem(n_rx, n_tx);
-    cudaFuncSetAttribute(qr_dmma_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    qr_dmma_kernel<<<batch, kQrdWarps * 32, sm, s>>>(batch, n_rx, n_tx, H, y, out);
+    const int wq = qrd_warps(n_rx, n_tx);
+    const size_t sm = qrd_smem(n_rx, n_tx, wq);
+    if (wq == kPanelWarps) {
+      cudaFuncSetAttribute(qr_dmma_kernel<kPanelWarps>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+      qr_dmma_kernel<kPanelWarps><<<batch, wq * 32, sm, s>>>(batch, n_rx, n_tx, H, y, out);
+    } else {
+      cudaFuncSetAttribute(qr_dmma_kernel<kQrdWarps>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+      qr_dmma_kernel<kQrdWarps><<<batch, wq * 32, sm, s>>>(batch, n_rx, n_tx, H, y, out);
+    }
     return cudaGetLastError();
   }
   if (n_rx <= 32) {
