@@ -21,7 +21,8 @@
 // the CTA then finishes them best-first, each by a K-best run over the
 // remaining rows under the current radius (a run stops as soon as all its
 // survivors leave the sphere), and shrinks the radius with the run's best
-// leaf.  Prefixes are taken while their own partial distance is inside the
+// leaf: the best prefix on the whole CTA (cta_kbest_levels), the others one
+// per warp (warp_kbest) on the warps that hold a K-best workspace.  Prefixes are taken while their own partial distance is inside the
 // sphere; the first one outside ends the vector, since all later ones are
 // farther.  The answer is the best K-best leaf over the prefixes inside the
 // initial sphere, whatever the order, because a radius above the answer only
@@ -114,19 +115,22 @@ struct KbCtx {
 
 // ---------------------------------------------------------------------------
 // K-best level steps by a whole CTA (T = 32 W threads), for one run from one
-// node.  Per level: survivor t's interference (row_interference, G threads per
-// survivor, the same bits as a warp's single-lane chains), then one key per
-// child e = t P + k held in registers (E per thread, warp w holding the 32 E
-// elements from 32 E w).  A key orders the children as the tournament of
+// node; the radius must not change during the run.  Per level: survivor t's
+// interference (row_interference, G threads per survivor, the same bits as a
+// warp's single-lane chains), then one key per child e = t P + k held in
+// registers (E per thread, warp w holding the 32 E elements from 32 E w).
+// With SE (the hybrid) a key orders the children as the tournament of
 // warp_kbest emits them: its distance field is the running maximum of the
 // partial distances along the survivor's Schnorr-Euchner order (a stream ends
 // at its first child outside the bound, and a child leaves its stream only
-// after the ones before it), then parent rank, Schnorr-Euchner rank, child.
-// Each warp sorts its keys in registers (bitonic: shuffles below stride 32,
-// in-thread exchanges above); the warps' sorted runs are then merged pairwise
-// through shared memory, keeping the 32 E smallest at each step (elementwise
-// minimum against the partner's reversed run, then a bitonic merge), so that
-// warp 0 ends with the level's survivors.
+// after the ones before it), then parent rank, Schnorr-Euchner rank, child;
+// without SE (detect_kbest) it is (distance, parent rank, child).  Each warp
+// sorts its keys in registers (bitonic: shuffles below stride 32, in-thread
+// exchanges above); the warps' sorted runs are then merged pairwise through
+// shared memory, keeping the 32 E smallest at each step (elementwise minimum
+// against the partner's reversed run, then a bitonic merge), so that warp 0
+// ends with the level's survivors.  Levels whose S P children fit in 32 lanes
+// run on warp 0 alone (warp_level_small) while the other warps wait.
 struct CtaRun {
   float* cc;      // [Kp] interference per survivor
   uint64_t* buf;  // [W][32 E] merge runs; [0, K) the level's survivor keys
