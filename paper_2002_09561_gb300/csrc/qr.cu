@@ -247,7 +247,8 @@ struct QrdLayout {
     off_vim = take(sizeof(double) * 8 * (size_t)S);
     off_yre = take(sizeof(double) * 8 * (size_t)S);
     off_yim = take(sizeof(double) * 8 * (size_t)S);
-    off_tile = take(sizeof(double) * 2 * 8 * kTileStride * warps);
+    off_tile = take(sizeof(double) * 2 * 8 * kTileStride * (C8 / 8));  // W of every trailing tile
+    (void)warps;
     off_red = take(sizeof(double) * (8 + 2 * 16 * kPanelWarps));
     off_alpha = take(sizeof(double2) * (size_t)M);
     off_tau = take(sizeof(double) * (size_t)M);
@@ -466,9 +467,8 @@ __device__ void qrd_panel(const QrdLayout& L, int k, int bw, double* Are, double
 // T3 = (Vr + Vi)(Wr + Wi), Re = T1 - T2 and Im = T3 - T1 - T2.  An MMA holds
 // the FP64 unit about eight times as long as the FP64 addition that forms an
 // operand sum, so the trade saves FP64 time.
-__device__ void qrd_tile(const QrdLayout& L, int k, int c0, double* Are, double* Aim, const double* Vre,
-                         const double* Vim, const double* Yre, const double* Yim, double* tre, double* tim,
-                         int lane) {
+__device__ void qrd_w(const QrdLayout& L, int k, int c0, const double* Are, const double* Aim, const double* Yre,
+                      const double* Yim, double* tre, double* tim, int lane) {
   const int S = L.S, g = lane >> 2, q = lane & 3;
   const int R8 = L.N8 - k;
   // A operand (Y^H)[i][rr] -> Y[rr][i], B operand A_t[rr][c]; even and odd
@@ -501,13 +501,19 @@ __device__ void qrd_tile(const QrdLayout& L, int k, int c0, double* Are, double*
     tim[(2 * q) * kTileStride + g] = (a30 - a10) + a20;
     tim[(2 * q + 1) * kTileStride + g] = (a31 - a11) + a21;
   }
-  __syncwarp();
-  // A_t -= V W, row tiles of 8 (two at a time): A operand V[r][i], B operand W[i][n]
+}
+
+// A_t -= V W for rows k + m0 .. k + m0 + 15 of the tile at column c0 (W from
+// qrd_w in tre / tim).
+__device__ void qrd_update(const QrdLayout& L, int k, int c0, int m0, double* Are, double* Aim, const double* Vre,
+                           const double* Vim, const double* tre, const double* tim, int lane) {
+  const int S = L.S, g = lane >> 2, q = lane & 3;
+  const int R8 = L.N8 - k;
+  // A operand V[r][i], B operand W[i][n]; two row tiles of 8
   const double w0r = tre[g * kTileStride + q], w0i = tim[g * kTileStride + q];
   const double w1r = tre[g * kTileStride + 4 + q], w1i = tim[g * kTileStride + 4 + q];
   const double w0s = w0r + w0i, w1s = w1r + w1i;
-  __syncwarp();
-  for (int m0 = 0; m0 < R8; m0 += 16) {
+  {
     const bool two = m0 + 8 < R8;
     double* pr0 = Are + (size_t)(c0 + 2 * q) * S + k + m0 + g;
     double* pi0 = Aim + (size_t)(c0 + 2 * q) * S + k + m0 + g;
@@ -546,8 +552,8 @@ __device__ void qrd_tile(const QrdLayout& L, int k, int c0, double* Are, double*
       pi0[S + 8] = (di1 + u11) + u21;
     }
   }
-  __syncwarp();
 }
+
 
 // Factorises one [H | y] with the calling CTA (4 or 8 warps; warps 0..3 factor
 // the panels, all of them update the trailing columns).
@@ -567,8 +573,7 @@ __device__ void qr_dmma_one(int N, int M, const double2* __restrict__ Hb, const 
   double* tau = reinterpret_cast<double*>(smem_raw + L.off_tau);
   int* sing = reinterpret_cast<int*>(smem_raw + L.off_sing);
   const int tid = threadIdx.x, nthr = blockDim.x, lane = tid & 31, warp = tid >> 5;
-  double* tre = reinterpret_cast<double*>(smem_raw + L.off_tile) + (size_t)warp * 2 * 8 * kTileStride;
-  double* tim = tre + 8 * kTileStride;
+  double* tiles = reinterpret_cast<double*>(smem_raw + L.off_tile);
 
   const int plane = L.C8 * L.S;
   for (int t = tid; t < plane; t += nthr) {
@@ -593,9 +598,20 @@ __device__ void qr_dmma_one(int N, int M, const double2* __restrict__ Hb, const 
     const int bw = min(8, M - k);
     if (warp < kPanelWarps) qrd_panel(L, k, bw, Are, Aim, Vre, Vim, Yre, Yim, red, alpha, tau, sing, warp, lane);
     __syncthreads();
-    const int ntiles = (M + 1 - (k + 8) + 7) / 8;  // columns k+8 .. M, 8 per task
-    for (int t = warp; t < ntiles; t += nthr / 32)
-      qrd_tile(L, k, k + 8 + 8 * t, Are, Aim, Vre, Vim, Yre, Yim, tre, tim, lane);
+    // W_t = Y^H A_t for every tile of 8 columns (k+8 .. M), then A_t -= V W_t
+    // in units of (tile, 16 rows) spread over all warps (a panel's tile count
+    // is rarely a multiple of the four schedulers)
+    const int ntiles = (M + 1 - (k + 8) + 7) / 8;
+    const int nw = nthr / 32, nrb = (L.N8 - k + 15) / 16;
+    for (int t = warp; t < ntiles; t += nw)
+      qrd_w(L, k, k + 8 + 8 * t, Are, Aim, Yre, Yim, tiles + (size_t)t * 2 * 8 * kTileStride,
+            tiles + (size_t)t * 2 * 8 * kTileStride + 8 * kTileStride, lane);
+    __syncthreads();
+    for (int u = warp; u < ntiles * nrb; u += nw) {
+      const int t = u / nrb, rb = u - t * nrb;
+      const double* tw = tiles + (size_t)t * 2 * 8 * kTileStride;
+      qrd_update(L, k, k + 8 + 8 * t, 16 * rb, Are, Aim, Vre, Vim, tw, tw + 8 * kTileStride, lane);
+    }
     __syncthreads();
   }
   qr_writeout(M, [&](int c, int r) { return make_double2(Are[(size_t)c * L.S + r], Aim[(size_t)c * L.S + r]); },
