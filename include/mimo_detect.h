@@ -318,8 +318,10 @@ mdx_status mdx_mlp_error(mdx_ctx* ctx, int* err_out);
  * scratch (QR outputs, flags, work counter) in one static device array of
  * MDX_NOALLOC_SCRATCH_BYTES that the library reserves on every GPU it is
  * loaded on until the process exits.
- *   - Device pointers only (MDX_HOST_BUFFERS and MDX_LEARNED_RADIUS are
- *     rejected with MDX_EUNSUPPORTED); arguments as for detect_kbest.
+ *   - Device pointers only; arguments as for detect_kbest.  The flags
+ *     detect_kbest rejects (MDX_LEARNED_RADIUS, MDX_LEARNED_ORDER,
+ *     MDX_ORDER_NATURAL) and MDX_HOST_BUFFERS return MDX_EUNSUPPORTED, as do
+ *     K and sizes whose shared memory detect_kbest would refuse.
  *   - A batch whose scratch exceeds the array returns MDX_EUNSUPPORTED
  *     (about 6.7 KB per vector at 16x16, 243 KB at 100x100).
  *   - All calls share the array and it keeps the last call's contents; the
@@ -327,7 +329,9 @@ mdx_status mdx_mlp_error(mdx_ctx* ctx, int* err_out);
  *     overlaps on the GPU (other streams, other host threads) race:
  *     serialise them on one stream.
  *   - The first call on each device looks up the array's address with that
- *     device current; make that first call before any stream capture.
+ *     device current; make that first call before any stream capture.  The
+ *     address is kept until the process exits: resetting the device
+ *     (cudaDeviceReset) between calls is not supported.
  * Errors are reported by the return value only (there is no context). */
 #define MDX_NOALLOC_SCRATCH_BYTES (16u << 20)
 mdx_status detect_kbest_noalloc(const mdx_params* p, int batch, const double* H, const double* y,
@@ -346,6 +350,21 @@ mdx_status detect_kbest_noalloc(const mdx_params* p, int batch, const double* H,
  * the detection path; enable = 0 turns it off. */
 mdx_status mdx_profile(mdx_ctx* ctx, int enable);
 mdx_status mdx_profile_read(mdx_ctx* ctx, double* ms_out);
+
+/* Arithmetic-throughput probes for roofline denominators (not part of the
+ * detection path; the paper has none).  Runs three short kernels on
+ * `device` (about 40 ms in all, on `stream`, synchronously) filling every SM:
+ *   out[0] = FP32 FMA throughput, TFLOP/s (8 independent FFMA chains per
+ *            thread; the unit of the tree searches' partial distances),
+ *   out[1] = FP64 FMA throughput, TFLOP/s (8 DFMA chains per thread; the
+ *            QR's panel),
+ *   out[2] = FP64 mma.sync m8n8k4 throughput, TFLOP/s, with the A and B
+ *            operand values changed before every MMA (the QR's trailing
+ *            updates),
+ *   out[3] = milliseconds the three timed launches took.
+ * An FMA counts as 2 flops.  Allocates and frees a small device buffer.
+ * Returns MDX_EINVAL for a bad device or NULL out, MDX_ECUDA on a CUDA error. */
+mdx_status mdx_measure_peaks(int device, double* out, void* stream);
 
 #ifdef __cplusplus
 }

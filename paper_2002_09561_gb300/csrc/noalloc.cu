@@ -18,7 +18,9 @@
 //     other's results; serialise them on one stream;
 //   - the first call on each device looks up the array's device address
 //     (cudaGetSymbolAddress) with that device current; make that first call
-//     before any stream capture begins.
+//     before any stream capture begins.  The address is kept for the life of
+//     the process, so a device reset (cudaDeviceReset) between calls is not
+//     supported: it unloads the module and the kept address goes stale.
 #include <math.h>
 
 #include <mutex>
@@ -63,16 +65,6 @@ bool on_device(const void* p, int device) {
   return at.type == cudaMemoryTypeManaged || (at.type == cudaMemoryTypeDevice && at.device == device);
 }
 
-size_t kb_smem_bytes(int n, int K, int P) {
-  int w = round_up(n, 4) / 4;
-  if ((w & 1) == 0) ++w;
-  const size_t pp = 4 * (size_t)w;
-  const size_t o = sizeof(uint64_t) * pow2ceil(K * P) + sizeof(float) * tri_stride32(n) +
-                   sizeof(float) * round_up(n, 4) + 2 * sizeof(float) * round_up(K, 4) + sizeof(float) * 8 +
-                   64 + pp * (2 * (size_t)K + 8);
-  return (o + 15) / 16 * 16;
-}
-
 }  // namespace
 
 extern "C" mdx_status detect_kbest_noalloc(const mdx_params* p, int batch, const double* H,
@@ -87,13 +79,17 @@ extern "C" mdx_status detect_kbest_noalloc(const mdx_params* p, int batch, const
   if (p->K < 1 || p->K > MDX_MAX_K) return MDX_EINVAL;
   const double r0 = p->init_radius_sq;
   if (isnan(r0) || r0 == 0.0) return MDX_EINVAL;
-  if (p->flags & (MDX_HOST_BUFFERS | MDX_LEARNED_RADIUS)) return MDX_EUNSUPPORTED;
+  // the flags detect_kbest itself rejects, plus host buffers (which need the
+  // context's staging buffers)
+  if (p->flags & (MDX_HOST_BUFFERS | MDX_LEARNED_RADIUS | MDX_LEARNED_ORDER | MDX_ORDER_NATURAL))
+    return MDX_EUNSUPPORTED;
   const int radius_mode = isinf(r0) ? (r0 > 0 ? RADIUS_NONE : RADIUS_PAPER) : (r0 < 0 ? RADIUS_PAPER : RADIUS_VALUE);
   if (radius_mode == RADIUS_PAPER && !noise_var) return MDX_EINVAL;
   if (!H || !y || !sym_out || !metric_out || !vstatus) return MDX_EINVAL;
   if ((reinterpret_cast<uintptr_t>(H) & 15u) || (reinterpret_cast<uintptr_t>(y) & 15u)) return MDX_EINVAL;
   const int n = 2 * M;
-  if (kb_smem_bytes(n, p->K, P) > 227 * 1024) return MDX_EUNSUPPORTED;
+  // the same shared-memory check as detect_kbest, before anything is enqueued
+  if (kbest_smem_bytes(n, p->K, P, (p->flags & MDX_COMPLEX_TREE) != 0) > 227 * 1024) return MDX_EUNSUPPORTED;
 
   // scratch layout: R64 | yb64 | R32 | yb32 | singular | work counter
   const size_t B = (size_t)batch;

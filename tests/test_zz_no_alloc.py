@@ -75,6 +75,31 @@ def test_noalloc_matches_detect_kbest_on_consecutive_calls(env):
         _same(torch, got, ref)
 
 
+def test_noalloc_matches_detect_kbest_blocked_qr_and_complex_tree(env):
+    """The 100x100 systems take the blocked FP64 QR (and its scratch nearly
+    fills the array: about 243 KB per vector, so 60 vectors); the complex
+    tree takes the K-best kernel's complex level steps.  Two calls in a row
+    each, against detect_kbest."""
+    torch, mdx, _ = env
+    big = mdx.Context(0, max_batch=64, max_n_rx=100, max_n_tx=100)
+    try:
+        for seed in (111, 112):
+            H, y, nv = _inputs(torch, seed, 60, 100, 100, 64, 28.0)
+            params = mdx.make_params(100, 100, 64, K=32)
+            st, got = _noalloc(torch, mdx, params, H, y, nv)
+            assert st == mdx.MDX_OK, st
+            _same(torch, got, mdx.detect("kbest", big, params, H, y, nv))
+    finally:
+        big.close()
+    _, _, ctx = env
+    for seed in (113, 114):
+        H, y, nv = _inputs(torch, seed, 200, 8, 8, 16, 12.0)
+        params = mdx.make_params(8, 8, 16, K=16, flags=mdx.MDX_COMPLEX_TREE)
+        st, got = _noalloc(torch, mdx, params, H, y, nv)
+        assert st == mdx.MDX_OK, st
+        _same(torch, got, mdx.detect("kbest", ctx, params, H, y, nv))
+
+
 def test_noalloc_rejects_batches_beyond_its_scratch(env):
     torch, mdx, ctx = env
     per_vector = 8 * (528 + 32) + 4 * (528 + 32) + 4  # 16x16: R and ybar in FP64 and FP32, flag
@@ -92,9 +117,21 @@ def test_noalloc_rejects_batches_beyond_its_scratch(env):
     _same(torch, got, mdx.detect("kbest", ctx, params, H, y, nv))
 
 
-def test_noalloc_rejects_host_buffers(env):
+def test_noalloc_rejects_host_buffers_and_the_flags_detect_kbest_rejects(env):
     torch, mdx, ctx = env
     H, y, nv = _inputs(torch, 8, 4, 4, 4, 4, 10.0)
-    params = mdx.make_params(4, 4, 4, K=4, flags=mdx.MDX_HOST_BUFFERS)
+    for flag in (mdx.MDX_HOST_BUFFERS, mdx.MDX_LEARNED_RADIUS, mdx.MDX_LEARNED_ORDER, mdx.MDX_ORDER_NATURAL):
+        params = mdx.make_params(4, 4, 4, K=4, flags=flag)
+        st, _ = _noalloc(torch, mdx, params, H, y, nv)
+        assert st == mdx.MDX_EUNSUPPORTED, flag
+        if flag != mdx.MDX_HOST_BUFFERS:
+            with pytest.raises(mdx.MdxError) as e:
+                mdx.detect("kbest", ctx, params, H, y, nv)
+            assert e.value.status == mdx.MDX_EUNSUPPORTED
+    # a size whose shared memory detect_kbest refuses (complex tree at 100x100
+    # 64-QAM, K = 256: 16,384 keys of 8 bytes beside R and the paths) is
+    # refused here too, before any launch
+    H, y, nv = _inputs(torch, 9, 4, 100, 100, 64, 20.0)
+    params = mdx.make_params(100, 100, 64, K=256, flags=mdx.MDX_COMPLEX_TREE)
     st, _ = _noalloc(torch, mdx, params, H, y, nv)
     assert st == mdx.MDX_EUNSUPPORTED
