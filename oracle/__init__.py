@@ -7,9 +7,15 @@ arithmetic lives in oracle.c (plain C, double precision, each function
 citing the passage of the paper it writes out); this module only builds
 that library and marshals numpy arrays into it.
 
-Parity unpinned: none of the functions here; every one has a pin in
-tests/test_oracle.py (brute force, closed forms, library routines, the
-paper's printed counts and its ML symbol-error curve).
+Every function here has a pin in tests/test_oracle.py or
+tests/test_oracle_gaps.py (brute force, closed forms, library routines, the
+paper's printed counts, an independent restatement of the K-best gaps).
+Parity unpinned (SNR convention): the noise variance sigma^2 = 10^(-SNR/10)
+per complex entry, which the input generator applies and the oracle's paper
+radius r^2 = N M sigma^2 reads, is the reading of the paper's radius
+formula; the paper's ML error-rate curves match it only in shape (a
+constant, unexplained 5.5 dB offset), so the convention itself is not
+pinned.
 """
 
 from __future__ import annotations

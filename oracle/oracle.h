@@ -27,7 +27,13 @@
  *     Re(s_j), 2j+1 is Im(s_j); complex entry h becomes [[Re,-Im],[Im,Re]];
  *   - rows are expanded top row first (i = n-1 ... 0), survival is PED < r^2;
  *   - ties in child order go to the lower PAM index; K-best ties go to
- *     (PED, parent rank, child index).
+ *     (PED, parent rank, child index);
+ *   - noise variance sigma^2 per complex receive entry, read from the
+ *     paper's radius formula r^2 = N M 10^(-SNR/10) (Sec. III-B) as
+ *     sigma^2 = 10^(-SNR/10) for unit-energy symbols.  Parity unpinned (SNR
+ *     convention): the paper's ML error-rate curves (Sec. VII-B) agree with
+ *     it in shape only, 5.5 dB apart; the functions below take sigma^2 (or
+ *     r^2) as an input and are pinned independently of it.
  */
 #ifndef MIMO_ORACLE_H
 #define MIMO_ORACLE_H
