@@ -73,14 +73,20 @@ WORKLOADS = {
                       snr=[6.0, 30.0], vectors=50_000, detector="mixed", radius="paper (SD) / none (K-best)",
                       K=64, depth=0, budget=20_000),
 }
+DEFAULT_WORKLOAD = "16x16-16qam-sd-learned"
 METRIC = "decoded vectors/s at matched BER (16x16 16QAM, 100x100 64QAM), learned vs plain"
 # DRAM bytes (read + write) of the dominant kernel per vector, from one ncu
 # capture of the same kernel on a smaller run of the same workload (traffic
-# grows with the number of vectors); None where no capture of the current
-# kernel exists.  Captures: sd_kernel, 20,000 vectors: 154.2 MB read + 4.8 MB
-# written; hybrid_kernel, 2,000 vectors: 517.5 MB read + 4.1 MB written.
-TRAFFIC_PER_VECTOR = {"16x16-16qam-sd-learned": (154.186752e6 + 4.764160e6) / 20000,
-                      "100x100-64qam-hybrid32-learned": (517.457664e6 + 4.140800e6) / 2000}
+# grows with the number of vectors), with the capture it comes from.  A kernel
+# changed since its capture has no entry here until it is captured again.
+TRAFFIC_PER_VECTOR = {
+    "16x16-16qam-sd-learned": ((154.186752e6 + 4.764160e6) / 20000,
+                               "ncu capture of sd_kernel, 20,000 vectors of the learned 16x16 sweep "
+                               "(profiles/sd_kernel_16x16_16qam_sweep_20k.md), scaled by vectors"),
+    "100x100-64qam-hybrid32-learned": ((517.457664e6 + 4.140800e6) / 2000,
+                                       "ncu capture of hybrid_kernel, 2,000 vectors of the learned 100x100 "
+                                       "workload (profiles/hybrid_kernel_100x100_64qam_2k.md), scaled by vectors"),
+}
 FP32_LANES_PER_SM = 128  # FP32 FMA lanes per SM (4 sub-partitions x 32)
 
 
@@ -90,7 +96,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="mdx", choices=["mdx", "reference"])
-    ap.add_argument("--workload", default="16x16-16qam-sd-learned", choices=sorted(WORKLOADS))
+    ap.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=sorted(WORKLOADS))
     ap.add_argument("--no-plain", action="store_true", help="skip the plain-radius comparison arm")
     ap.add_argument("--vectors", type=int, default=0, help="override vectors per step (per GPU)")
     ap.add_argument("--snr", type=str, default="", help="comma-separated SNR points (override)")
@@ -99,6 +105,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="target CPU-baseline duration")
     ap.add_argument("--no-autotune", action="store_true", help="uneven batch: keep the default tuning")
+    ap.add_argument("--no-hybrid", action="store_true",
+                    help="default workload: skip the 100x100 64-QAM hybrid record")
     return ap.parse_args()
 
 
@@ -212,7 +220,7 @@ def cpu_baseline_mixed(w, seed, target_s):
     a rotating start) until target_s seconds have been spent."""
     import oracle
 
-    cores = oracle.max_threads()
+    cores = host_cores()
     d, reqs = mixed_table(w, seed, w["vectors"])
     done = 0
     t0 = time.perf_counter()
@@ -228,53 +236,175 @@ def cpu_baseline_mixed(w, seed, target_s):
                       f"on {cores} threads"}
 
 
-def cpu_baseline(w, seed, target_s, start_offset):
-    """The FP64 oracle on the host cores over a bounded sample of the same
-    workload: vectors taken round-robin over the SNR points, in chunks, until
-    target_s seconds have been spent."""
+# The oracle's CPU baseline and error check run on a FIXED sample of the
+# workload: its first PER_POINT[workload] vectors of every SNR point (vector b
+# is at point b mod len(snr), so the sample is the first per_point * len(snr)
+# vectors of the seed), the same vectors in both arms of the benchmark.
+ORACLE_PER_POINT = {"16x16": 64, "100x100": 16}
+ORACLE_PER_POINT_1CORE = {"16x16": 8, "100x100": 2}
+
+
+def _size_key(w):
+    return "100x100" if w["n"] > 32 else "16x16"
+
+
+def oracle_sample(w, seed, per_point):
+    return generate(w, seed, per_point * len(w["snr"]), start=0)
+
+
+_HOST_CORES = []
+
+
+def host_cores():
+    """The oracle's OpenMP thread count before any single-core run changed it."""
+    import oracle
+
+    if not _HOST_CORES:
+        _HOST_CORES.append(oracle.max_threads())
+    return _HOST_CORES[0]
+
+
+def oracle_detect(w, d, nthreads=0, want_gap=False):
+    import oracle
+
+    nthreads = nthreads or host_cores()
+    algo = w["detector"] + ("_complex" if w.get("complex") else "")
+    if algo == "linear":
+        r = oracle.detect_linear("mmse" if w.get("mmse") else "zf", d["H"], d["y"], d["noise_var"], w["qam"])
+        r["gap"] = r["margin"]
+        return r
+    return oracle.detect_batch(algo, d["H"], d["y"], d["noise_var"], w["qam"], radius=w["radius"],
+                               K=max(w["K"], 1), depth=w["depth"], order="natural" if w.get("natural") else "se",
+                               want_gap=want_gap, nthreads=nthreads)
+
+
+def cpu_baseline(w, seed):
+    """The FP64 oracle as it stands, on the host cores, over the fixed sample
+    (all cores), and over a smaller fixed sample on one core."""
     import oracle
 
     if w.get("mixed"):
-        return cpu_baseline_mixed(w, seed, target_s)
-    cores = oracle.max_threads()
-    algo = w["detector"] + ("_complex" if w.get("complex") else "")
-    if algo == "linear":
-        cores = 1  # numpy, one thread
-    done = 0
+        return cpu_baseline_mixed(w, seed, 15.0)
+    key = _size_key(w)
+    cores = 1 if w["detector"] == "linear" else host_cores()
+    d = oracle_sample(w, seed, ORACLE_PER_POINT[key])
     t0 = time.perf_counter()
-    chunk = max(cores, 16)
-    pos = start_offset
-    while time.perf_counter() - t0 < target_s and done < w["vectors"]:
-        d = generate(w, seed, chunk, start=pos)
-        if algo == "linear":
-            oracle.detect_linear("mmse" if w.get("mmse") else "zf", d["H"], d["y"], d["noise_var"], w["qam"])
-        else:
-            oracle.detect_batch(algo, d["H"], d["y"], d["noise_var"], w["qam"], radius=w["radius"],
-                                K=max(w["K"], 1), depth=w["depth"],
-                                order="natural" if w.get("natural") else "se")
-        done += chunk
-        pos += chunk
+    ref = oracle_detect(w, d)
     dt = time.perf_counter() - t0
-    return {"value": done / dt, "unit": "vectors/s", "cores": cores, "kind": "oracle",
-            "sample": f"{done} vectors of the same workload ({w['n']}x{w['n']} {w['qam']}-QAM "
-                      f"{algo}, SNR points round-robin) in {dt:.1f} s on {cores} threads"}
+    d1 = oracle_sample(w, seed, ORACLE_PER_POINT_1CORE[key])
+    t1 = time.perf_counter()
+    oracle_detect(w, d1)
+    dt1c = time.perf_counter() - t1
+    t1 = time.perf_counter()
+    oracle_detect(w, d1, nthreads=1)
+    dt1 = time.perf_counter() - t1
+    B = len(d["noise_var"])
+    algo = w["detector"] + ("_complex" if w.get("complex") else "")
+    return {"value": B / dt, "unit": "vectors/s", "cores": cores, "kind": "oracle",
+            "sample": f"fixed: the first {ORACLE_PER_POINT[key]} vectors of each of the {len(w['snr'])} SNR points "
+                      f"({B} vectors, seed {seed}; {w['n']}x{w['n']} {w['qam']}-QAM {algo}, "
+                      f"radius {w['radius'] if w['radius'] == 'paper' else 'none'}) in {dt:.2f} s on {cores} threads",
+            "single_core": {"value": len(d1["noise_var"]) / dt1, "unit": "vectors/s", "cores": 1,
+                            "all_cores_same_sample": len(d1["noise_var"]) / dt1c,
+                            "sample": f"the first {ORACLE_PER_POINT_1CORE[key]} vectors of each SNR point "
+                                      f"({len(d1['noise_var'])} vectors) in {dt1:.2f} s on one thread "
+                                      f"({dt1c:.2f} s on {cores})"}}, d, ref
+
+
+def gray_bit_errors(a, b, qam):
+    """Bit errors per vector between complex indices a and b (Gray code per
+    PAM dimension of q = k_re P + k_im)."""
+    P = int(round(qam ** 0.5))
+    ones = np.array([bin(v).count("1") for v in range(256)], dtype=np.int64)
+    a = a.astype(np.int64)
+    b = b.astype(np.int64)
+    g = lambda k: k ^ (k >> 1)  # noqa: E731
+    x = ones[g(a // P) ^ g(b // P)] + ones[g(a % P) ^ g(b % P)]
+    return x.sum(axis=1)
+
+
+def per_snr(w, outs, truth):
+    """Per SNR point: BER, SER, mean / p99 visited nodes, radius-doubling and
+    budget rates (vector b is at point b mod len(snr))."""
+    sym, vst, st = outs
+    B = sym.shape[0]
+    pts = np.arange(B) % len(w["snr"])
+    be = gray_bit_errors(sym, truth, w["qam"])
+    se = (sym != truth).sum(axis=1)
+    bits_per_vec = 2 * w["n"] * int(round(math.log2(int(round(w["qam"] ** 0.5)))))
+    rows = []
+    for i, s in enumerate(w["snr"]):
+        m = pts == i
+        nodes = st[m, 0].astype(np.float64)
+        rows.append({"snr_db": s, "vectors": int(m.sum()), "ber": float(be[m].sum() / (m.sum() * bits_per_vec)),
+                     "ser": float(se[m].sum() / (m.sum() * w["n"])), "mean_nodes": float(nodes.mean()),
+                     "p99_nodes": float(np.percentile(nodes, 99)),
+                     "radius_doubling_rate": float((vst[m] == 1).mean()),
+                     "budget_rate": float((vst[m] == 2).mean())})
+    return rows
+
+
+def oracle_check(w, d, ref_gap, gpu_sym, gpu_met, seed):
+    """The GPU's answers on the oracle's fixed sample against the oracle's:
+    mismatches outside near-ties (SD: best/second-best gap < 1e-6; K-best,
+    hybrid: a K / K+1 cut or final gap < 1e-5), near-tie fraction, largest
+    relative metric error where the indices agree, and BER of both per SNR
+    point."""
+    tol = 1e-6 if w["detector"] == "sd" else (1e-8 if w["detector"] == "linear" else 1e-5)
+    B = len(d["noise_var"])
+    same = (gpu_sym[:B] == ref_gap["sym"]).all(axis=1)
+    near = ref_gap["gap"] < tol
+    rel = np.abs(gpu_met[:B] - ref_gap["metric"]) / np.maximum(ref_gap["metric"], 1e-300)
+    pts = np.arange(B) % len(w["snr"])
+    bits_per_vec = 2 * w["n"] * int(round(math.log2(int(round(w["qam"] ** 0.5)))))
+    gb = gray_bit_errors(gpu_sym[:B], d["sym"], w["qam"])
+    ob = gray_bit_errors(ref_gap["sym"], d["sym"], w["qam"])
+    return {"vectors": int(B), "sample": f"the oracle's fixed sample (seed {seed})",
+            "identical": int(same.sum()), "mismatches_outside_near_ties": int((~same & ~near).sum()),
+            "differing_near_ties": int((~same & near).sum()), "near_tie_fraction": float(near.mean()),
+            "near_tie_rule": f"gap < {tol:g} relative",
+            "max_rel_metric_error": float(rel[same].max()) if same.any() else None,
+            "ber_per_snr": [{"snr_db": s, "gpu": float(gb[pts == i].sum() / ((pts == i).sum() * bits_per_vec)),
+                             "oracle": float(ob[pts == i].sum() / ((pts == i).sum() * bits_per_vec))}
+                            for i, s in enumerate(w["snr"])]}
 
 
 def run_reference(args, w, rank, world):
+    """The oracle arm: every step detects the fixed sample on all host cores
+    (the same vectors the GPU arm's cpu_baseline times)."""
     if rank != 0:
         return
+    import oracle
+
     steps, warm = args.steps, args.warmup
-    target = max(2.0, min(args.cpu_seconds, 60.0 / max(1, steps + warm)))
-    for _ in range(warm):
-        cpu_baseline(w, args.seed, target / 4, 0)
-    vals = []
-    t0 = time.perf_counter()
-    for k in range(steps):
-        vals.append(cpu_baseline(w, args.seed, target, 0))
-    wall = time.perf_counter() - t0
-    value = float(np.mean([v["value"] for v in vals]))
-    base = dict(vals[-1])
-    base["value"] = value
+    if w.get("mixed"):
+        target = max(2.0, min(args.cpu_seconds, 60.0 / max(1, steps + warm)))
+        for _ in range(warm):
+            cpu_baseline_mixed(w, args.seed, target / 4)
+        vals = []
+        t0 = time.perf_counter()
+        for _ in range(steps):
+            vals.append(cpu_baseline_mixed(w, args.seed, target))
+        wall = time.perf_counter() - t0
+        value = float(np.mean([v["value"] for v in vals]))
+        base = dict(vals[-1])
+        base["value"] = value
+    else:
+        key = _size_key(w)
+        d = oracle_sample(w, args.seed, ORACLE_PER_POINT[key])
+        B = len(d["noise_var"])
+        warm_d = oracle_sample(w, args.seed, 1)
+        for _ in range(warm):
+            oracle_detect(w, warm_d)
+        t0 = time.perf_counter()
+        for _ in range(steps):
+            oracle_detect(w, d)
+        wall = time.perf_counter() - t0
+        value = B * steps / wall
+        cores = 1 if w["detector"] == "linear" else host_cores()
+        base = {"value": value, "unit": "vectors/s", "cores": cores, "kind": "oracle",
+                "sample": f"fixed: the first {ORACLE_PER_POINT[key]} vectors of each of the {len(w['snr'])} SNR "
+                          f"points ({B} vectors, seed {args.seed}) per step, {steps} steps on {cores} threads"}
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": base["unit"], "n_gpus": world,
             "steps": steps, "warmup": warm, "ms_per_step": 1e3 * wall / steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
@@ -352,6 +482,7 @@ def main():
     nv = torch.from_numpy(data["noise_var"]).to(dev)
     truth = torch.from_numpy(data["sym"]).to(dev)
     ctx = mdx.Context(local, max_batch=B, max_n_rx=n, max_n_tx=n)
+    probe = mdx.measure_peaks(local)
     learned = bool(w.get("learned"))
     model_meta = None
     if learned:
@@ -362,90 +493,70 @@ def main():
     if learned:
         # the ordering head exists for models with full features (detect_sd)
         flags = mdx.MDX_LEARNED_RADIUS | (mdx.MDX_LEARNED_ORDER if w["detector"] == "sd" else 0)
+    base_flags = 0
     if w.get("complex"):
-        flags |= mdx.MDX_COMPLEX_TREE
+        base_flags |= mdx.MDX_COMPLEX_TREE
     if w.get("natural"):
-        flags |= mdx.MDX_ORDER_NATURAL
+        base_flags |= mdx.MDX_ORDER_NATURAL
     if w.get("mmse"):
-        flags |= mdx.MDX_LINEAR_MMSE
+        base_flags |= mdx.MDX_LINEAR_MMSE
+    flags |= base_flags
     params = mdx.make_params(n, n, qam, radius=w["radius"], K=max(w["K"], 1), depth=w["depth"], flags=flags)
     algo = w["detector"]
     out = mdx._outputs(B, n, dev, True)
     stream = torch.cuda.current_stream(dev)
+    arm = Arm(torch, mdx, replicas, ctx, algo, H, y, nv, truth, qam, stream, dist, dev, local)
 
-    def timed(prm, outs, steps, warm):
-        def step():
-            mdx.detect(algo, ctx, prm, H, y, nv, stream=stream, out=outs)
-            return mdx.count_errors(ctx, outs[0], truth, qam, stream=stream)
-
-        for _ in range(warm):
-            step()
-        torch.cuda.synchronize(dev)
-        if dist is not None:
-            dist.barrier()
-        torch.cuda.synchronize(dev)
-        sampler = ClockSampler(local)
-        sampler.start()
-        ctx.profile(True)
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        errs = None
-        for _ in range(steps):
-            errs = step()
-        e1.record(stream)
-        torch.cuda.synchronize(dev)
-        if dist is not None:
-            dist.barrier()
-        torch.cuda.synchronize(dev)
-        sampler.stop()
-        el = e0.elapsed_time(e1)
-        prof = ctx.profile_read()
-        ctx.profile(False)
-        el = replicas.max_over_ranks(el, dist, dev)
-        return el, prof, errs, sampler
-
-    ms, (qr_ms, search_ms, calls), errs, sampler = timed(params, out, args.steps, args.warmup)
+    ms, (qr_ms, search_ms, calls), errs, sampler = arm.time(params, out, args.steps, args.warmup)
     value = B * world * args.steps / (ms / 1e3)
-    plain = None
+    host = lambda o: (o[0].cpu().numpy(), o[2].cpu().numpy(), o[3].cpu().numpy())  # noqa: E731
+    main_host = host(out)
+    bits_vec = 2 * n * int(round(math.log2(int(round(qam ** 0.5)))))
+    plain = babai = None
+    plain_qr = None
     if learned and not args.no_plain:
         pparams = mdx.make_params(n, n, qam, radius=w["radius"], K=max(w["K"], 1), depth=w["depth"],
-                                  flags=mdx.MDX_COMPLEX_TREE if w.get("complex") else 0)
+                                  flags=base_flags)
         pout = mdx._outputs(B, n, dev, True)
-        pms, _, perrs, _ = timed(pparams, pout, args.steps, 1)
-        same = bool(torch.equal(pout[0], out[0]))
-        pst = pout[3].cpu().numpy()
+        pms, pprof, perrs, _ = arm.time(pparams, pout, args.steps, 1)
+        plain_qr = pprof
+        ph = host(pout)
         plain = {"value": B * world * args.steps / (pms / 1e3), "unit": "vectors/s", "ms_per_step": pms / args.steps,
-                 "initial_radius": "r^2 = N M sigma^2", "mean_nodes": float(pst[:, 0].mean()),
-                 "identical_decisions": same,
-                 "ber": int(perrs[0]) / (B * n * 2 * int(round(math.log2(int(round(qam ** 0.5)))))),
-                 "speedup_learned": (B * world * args.steps / (ms / 1e3)) / (B * world * args.steps / (pms / 1e3))}
+                 "initial_radius": "r^2 = N M sigma^2", "mean_nodes": float(ph[2][:, 0].mean()),
+                 "identical_decisions": bool(torch.equal(pout[0], out[0])),
+                 "ber": int(perrs[0]) / (B * bits_vec), "speedup_learned": pms / ms,
+                 "search_ms_per_launch": pprof[1] / max(pprof[2], 1), "per_snr": per_snr(w, ph, data["sym"])}
+        if algo == "sd":
+            # the Babai-radius control: no initial radius, so the first leaf the
+            # Schnorr-Euchner descent reaches (the Babai / ZF-SIC point) sets r^2
+            bsteps = max(1, min(args.steps, 5))
+            bparams = mdx.make_params(n, n, qam, radius=math.inf, flags=base_flags)
+            bout = mdx._outputs(B, n, dev, True)
+            bms, bprof, berrs, _ = arm.time(bparams, bout, bsteps, 1)
+            bh = host(bout)
+            babai = {"value": B * world * bsteps / (bms / 1e3), "unit": "vectors/s", "ms_per_step": bms / bsteps,
+                     "steps": bsteps, "initial_radius": "none (the Babai point reached by the first descent sets it)",
+                     "mean_nodes": float(bh[2][:, 0].mean()),
+                     "identical_decisions": bool(torch.equal(bout[0], out[0])),
+                     "ber": int(berrs[0]) / (B * bits_vec), "speedup_learned": (bms / bsteps) / (ms / args.steps),
+                     "search_ms_per_launch": bprof[1] / max(bprof[2], 1), "per_snr": per_snr(w, bh, data["sym"])}
 
-    stats = out[3].cpu().numpy()
-    vst = out[2].cpu().numpy()
-    P = int(round(qam ** 0.5))
-    # whole-job counters (one sum-reduction over the ranks)
+    stats = main_host[2]
+    vst = main_host[1]
     tot = replicas.sum_counters({"bit_errors": int(errs[0]), "symbol_errors": int(errs[1]),
                                  "budget_exceeded": int((vst == 2).sum()), "radius_doublings": int((vst == 1).sum()),
                                  "nodes": int(stats[:, 0].sum())}, dist, dev)
     bit_err, sym_err = tot["bit_errors"], tot["symbol_errors"]
-    bits = B * world * n * 2 * int(round(math.log2(P)))
+    bits = B * world * bits_vec
 
     # dominant kernel: the tree search; algorithmic FP32 flops per launch from the
     # kernel's own count, sum over branched nodes at row i of 2(n-1-i) + 4P
-    peaks = load_peaks()
-    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
     sms = torch.cuda.get_device_properties(dev).multi_processor_count
-    peak = sms * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
-    flops = float(stats[:, 4].sum())
-    per_launch_s = (search_ms / max(calls, 1)) / 1e3
-    achieved = flops / per_launch_s / 1e12 if per_launch_s > 0 else 0.0
-    tpv = TRAFFIC_PER_VECTOR.get(args.workload)
-    roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-            "traffic": tpv * B if tpv else None, "traffic_unit": "bytes per launch (ncu capture, scaled by vectors)",
-            "kernel": f"{algo} search", "search_ms_per_launch": 1e3 * per_launch_s,
-            "qr_ms_per_launch": qr_ms / max(calls, 1),
-            "peak_source": f"derived: {sms} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 x {sm_max:.0f} MHz"}
+    roof = search_roofline(args.workload, algo, stats, search_ms, calls, qr_ms, sms, probe, B)
+    # the FP64 QR (timed in the arm without the network, whose QR interval is
+    # the QR kernel and a 4-byte counter reset)
+    qprof = plain_qr if plain_qr is not None else ((qr_ms, search_ms, calls) if not learned else None)
+    qr_roof = qr_roofline(n, n, B, qprof, sms, probe) if qprof else None
 
     e2e = None
     if not args.no_e2e:
@@ -468,9 +579,19 @@ def main():
                "h2d_bytes_per_step": int(hH.nbytes + hy.nbytes + hnv.nbytes),
                "d2h_bytes_per_step": int(hsym.nbytes + hmet.nbytes + hvst.nbytes)}
 
-    cpu = None
+    cpu = check = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cpu = cpu_baseline(w, args.seed, args.cpu_seconds, 0)
+        cpu, d_s, _ = cpu_baseline(w, args.seed)
+        ref = oracle_detect(w, d_s, want_gap=True)
+        check = oracle_check(w, d_s, ref, main_host[0], out[1].cpu().numpy(), args.seed)
+
+    hybrid = None
+    if args.workload == DEFAULT_WORKLOAD and not args.no_hybrid:
+        ctx.close()
+        ctx = None
+        del H, y, nv, truth, out
+        torch.cuda.empty_cache()
+        hybrid = hybrid_record(args, rank, world, local, dev, dist, torch, mdx, replicas, probe)
 
     if rank == 0:
         cfg = config_of(args, w, world)
@@ -482,15 +603,164 @@ def main():
                 "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f32 search, f64 QR and re-scoring",
                 "data": "synthetic (seeded Rayleigh channels, uniform QAM symbols, AWGN)",
-                "config": cfg, "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
-                "gpu_launches": (8 if learned else 3) * args.steps, "clocks": sampler.summary(), "plain": plain,
+                "config": cfg, "roofline": roof, "qr_roofline": qr_roof, "cpu_baseline": cpu, "e2e": e2e,
+                "gpu_launches": (8 if learned else 3) * args.steps, "clocks": sampler.summary(),
+                "measured_peaks": probe, "oracle_check": check, "plain": plain, "babai": babai,
                 "quality": {"ber": bit_err / bits, "ser": sym_err / (B * world * n),
                             "budget_exceeded": tot["budget_exceeded"], "radius_doublings": tot["radius_doublings"],
-                            "mean_nodes": tot["nodes"] / (B * world), "max_nodes_rank0": int(stats[:, 0].max())}}
+                            "mean_nodes": tot["nodes"] / (B * world), "max_nodes_rank0": int(stats[:, 0].max()),
+                            "per_snr_rank0": per_snr(w, main_host, data["sym"])},
+                "hybrid_100x100": hybrid}
         print(json.dumps(line), flush=True)
-    ctx.close()
+    if ctx is not None:
+        ctx.close()
     if dist is not None:
         dist.destroy_process_group()
+
+
+class Arm:
+    """Times one detector configuration: W untimed calls, then K calls (each
+    a detection plus the batch's bit/symbol error count) between CUDA events
+    on the launching stream, bracketed by barriers and synchronizations; the
+    elapsed time is the maximum over ranks.  The library's own events give
+    the QR and search kernels' share."""
+
+    def __init__(self, torch, mdx, replicas, ctx, algo, H, y, nv, truth, qam, stream, dist, dev, local):
+        self.torch, self.mdx, self.replicas, self.ctx, self.algo = torch, mdx, replicas, ctx, algo
+        self.H, self.y, self.nv, self.truth, self.qam = H, y, nv, truth, qam
+        self.stream, self.dist, self.dev, self.local = stream, dist, dev, local
+
+    def time(self, prm, outs, steps, warm):
+        torch, mdx = self.torch, self.mdx
+
+        def step():
+            mdx.detect(self.algo, self.ctx, prm, self.H, self.y, self.nv, stream=self.stream, out=outs)
+            return mdx.count_errors(self.ctx, outs[0], self.truth, self.qam, stream=self.stream)
+
+        for _ in range(warm):
+            step()
+        torch.cuda.synchronize(self.dev)
+        if self.dist is not None:
+            self.dist.barrier()
+        torch.cuda.synchronize(self.dev)
+        sampler = ClockSampler(self.local)
+        sampler.start()
+        self.ctx.profile(True)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(self.stream)
+        errs = None
+        for _ in range(steps):
+            errs = step()
+        e1.record(self.stream)
+        torch.cuda.synchronize(self.dev)
+        if self.dist is not None:
+            self.dist.barrier()
+        torch.cuda.synchronize(self.dev)
+        sampler.stop()
+        el = e0.elapsed_time(e1)
+        prof = self.ctx.profile_read()
+        self.ctx.profile(False)
+        el = self.replicas.max_over_ranks(el, self.dist, self.dev)
+        return el, prof, errs.cpu().numpy(), sampler
+
+
+def search_roofline(workload, algo, stats, search_ms, calls, qr_ms, sms, probe, B):
+    """FP32 roofline of the search kernel: algorithmic flops (the kernel's own
+    count, sum over branched nodes at row i of 2(n-1-i) + 4P) per launch over
+    the launch's CUDA-event duration, against the derived FP32 peak (SMs x
+    128 lanes x 2 x the maximum SM clock) and beside the probe's measured
+    FFMA rate."""
+    peaks = load_peaks()
+    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
+    peak = sms * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
+    flops = float(stats[:, 4].sum())
+    per_launch_s = (search_ms / max(calls, 1)) / 1e3
+    achieved = flops / per_launch_s / 1e12 if per_launch_s > 0 else 0.0
+    tpv = TRAFFIC_PER_VECTOR.get(workload)
+    nodes = float(stats[:, 0].sum())
+    return {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+            "measured_fma_peak": probe["fp32_fma_tflops"], "frac_of_measured": achieved / probe["fp32_fma_tflops"],
+            "traffic": tpv[0] * B if tpv else None,
+            "traffic_unit": "bytes per launch (dram read + write)" if tpv else None,
+            "traffic_source": tpv[1] if tpv else "no capture of the current kernel",
+            "kernel": f"{algo} search", "search_ms_per_launch": 1e3 * per_launch_s,
+            "qr_ms_per_launch": qr_ms / max(calls, 1),
+            "nodes_per_s": nodes / per_launch_s if per_launch_s > 0 else None,
+            "nodes_per_s_per_sm": nodes / per_launch_s / sms if per_launch_s > 0 else None,
+            "peak_source": f"derived: {sms} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 x {sm_max:.0f} MHz"}
+
+
+def qr_roofline(n_rx, n_tx, B, prof, sms, probe):
+    """FP64 roofline of the QR: 8 (N M^2 - M^3 / 3) real flops per complex
+    Householder QR of an N x M matrix, over the QR interval's CUDA-event
+    duration, against the derived FP64 peak (SMs x 2 FP64 FMA lanes x 2 x the
+    maximum SM clock) and the probe's measured FP64 FMA and MMA rates."""
+    qr_ms, _, calls = prof
+    peaks = load_peaks()
+    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
+    peak = sms * 2 * 2 * sm_max * 1e6 / 1e12
+    N, M = float(n_rx), float(n_tx)
+    flops = 8.0 * (N * M * M - M ** 3 / 3.0) * B
+    s = (qr_ms / max(calls, 1)) / 1e3
+    achieved = flops / s / 1e12 if s > 0 else 0.0
+    meas = max(probe["fp64_fma_tflops"], probe["fp64_mma_tflops"])
+    return {"bound": "fp64", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+            "measured_fp64_peak": meas, "frac_of_measured": achieved / meas, "ms_per_launch": 1e3 * s,
+            "flops_per_matrix": flops / B, "matrices": B,
+            "peak_source": f"derived: {sms} SMs x 2 FP64 FMA lanes x 2 x {sm_max:.0f} MHz; measured = the larger "
+                           "of the FP64 FMA and m8n8k4 MMA probes",
+            "interval": "QR kernel and the 4-byte work-counter reset"}
+
+
+def hybrid_record(args, rank, world, local, dev, dist, torch, mdx, replicas, probe):
+    """The metric's second configuration: 100x100 64-QAM hybrid (depth 4,
+    K = 32) at 20/24/28/32 dB, 10,000 vectors per step, learned radius
+    against the paper radius; each arm's throughput, decisions, BER, nodes,
+    per-SNR figures, the search kernel's FP32 fraction, the QR's FP64
+    fraction, and the oracle on a fixed sample beside it."""
+    from paper_2002_09561_gb300 import train
+
+    w = dict(WORKLOADS["100x100-64qam-hybrid32-learned"])
+    B, n, qam = w["vectors"], w["n"], w["qam"]
+    start, _ = replicas.shard(rank, world, B)
+    data = generate(w, args.seed, B, start=start)
+    H = torch.from_numpy(data["H"]).to(dev)
+    y = torch.from_numpy(data["y"]).to(dev)
+    nv = torch.from_numpy(data["noise_var"]).to(dev)
+    truth = torch.from_numpy(data["sym"]).to(dev)
+    ctx = mdx.Context(local, max_batch=B, max_n_rx=n, max_n_tx=n)
+    meta = train.load_model(ctx, n, qam)
+    stream = torch.cuda.current_stream(dev)
+    arm = Arm(torch, mdx, replicas, ctx, "hybrid", H, y, nv, truth, qam, stream, dist, dev, local)
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    bits_vec = 2 * n * int(round(math.log2(int(round(qam ** 0.5)))))
+    rec = {"workload": "100x100-64qam-hybrid32", "vectors_per_step_per_gpu": B, "snr_db": w["snr"], "K": w["K"],
+           "hybrid_depth": w["depth"], "model": {k: meta.get(k) for k in ("traces", "snr_db", "epochs", "seed")}}
+    outs = {}
+    for name, fl, warm in (("learned", mdx.MDX_LEARNED_RADIUS, args.warmup), ("plain", 0, 1)):
+        prm = mdx.make_params(n, n, qam, radius="paper", K=w["K"], depth=w["depth"], flags=fl)
+        o = mdx._outputs(B, n, dev, True)
+        ms, prof, errs, sampler = arm.time(prm, o, args.steps, warm)
+        hh = (o[0].cpu().numpy(), o[2].cpu().numpy(), o[3].cpu().numpy())
+        outs[name] = (o, hh)
+        r = {"value": B * world * args.steps / (ms / 1e3), "unit": "vectors/s", "ms_per_step": ms / args.steps,
+             "ber": int(errs[0]) / (B * bits_vec), "mean_nodes": float(hh[2][:, 0].mean()),
+             "roofline": search_roofline("100x100-64qam-hybrid32-" + name, "hybrid", hh[2], prof[1], prof[2], prof[0],
+                                         sms, probe, B),
+             "clocks": sampler.summary(), "per_snr": per_snr(w, hh, data["sym"])}
+        if name == "plain":
+            r["qr_roofline"] = qr_roofline(n, n, B, prof, sms, probe)
+        rec[name] = r
+    rec["identical_decisions"] = bool(torch.equal(outs["learned"][0][0], outs["plain"][0][0]))
+    rec["speedup_learned"] = rec["learned"]["value"] / rec["plain"]["value"]
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu, d_s, ref = cpu_baseline(w, args.seed)
+        rec["cpu_baseline"] = cpu
+        rec["oracle_check"] = oracle_check(w, d_s, ref, outs["learned"][1][0], outs["learned"][0][1].cpu().numpy(),
+                                           args.seed)
+    ctx.close()
+    return rec
 
 
 def main_mixed(args, w, rank, world, local, dev, dist, torch, mdx):

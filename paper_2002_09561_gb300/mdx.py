@@ -33,7 +33,8 @@ EXPORTS = ["mdx_create", "mdx_destroy", "mdx_strerror", "mdx_last_error", "mdx_w
            "mdx_qr", "detect_sd", "detect_kbest", "detect_hybrid", "mdx_count_errors",
            "mdx_profile", "mdx_profile_read", "detect_kbest_noalloc", "mdx_mlp_param_count",
            "mdx_mlp_dims", "mdx_mlp_init", "mdx_mlp_set_params", "mdx_mlp_get_params", "mdx_mlp_predict",
-           "mdx_mlp_train_step", "mdx_mlp_error", "detect_mixed", "mdx_autotune_mixed", "detect_linear"]
+           "mdx_mlp_train_step", "mdx_mlp_error", "detect_mixed", "mdx_autotune_mixed", "detect_linear",
+           "mdx_measure_peaks"]
 NOALLOC_SCRATCH_BYTES = 16 << 20
 STATS = 5  # per-vector stats: nodes, peds, restarts, rescored, algorithmic FP32 flops
 
@@ -124,6 +125,8 @@ def lib():
             L.mdx_profile.restype = i
             L.mdx_profile_read.argtypes = [vp, vp]
             L.mdx_profile_read.restype = i
+            L.mdx_measure_peaks.argtypes = [i, vp, vp]
+            L.mdx_measure_peaks.restype = i
             _lib = L
     return _lib
 
@@ -431,3 +434,16 @@ def mlp_error(ctx: Context) -> int:
     e = ctypes.c_int()
     ctx.check(lib().mdx_mlp_error(ctx.handle, ctypes.byref(e)), "mdx_mlp_error")
     return e.value
+
+
+def measure_peaks(device: int = 0, stream=None):
+    """FP32 FMA, FP64 FMA and FP64 m8n8k4 MMA throughput of `device`
+    (TFLOP/s, mdx_measure_peaks)."""
+    import numpy as np
+
+    out = np.zeros(4)
+    st = lib().mdx_measure_peaks(int(device), ctypes.c_void_p(out.ctypes.data), _stream(stream))
+    if st != MDX_OK:
+        raise MdxError(st, "mdx_measure_peaks")
+    return {"fp32_fma_tflops": float(out[0]), "fp64_fma_tflops": float(out[1]),
+            "fp64_mma_tflops": float(out[2]), "probe_ms": float(out[3])}
