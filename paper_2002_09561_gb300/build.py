@@ -19,7 +19,7 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libmdx.so")
-SOURCES = ["api.cu", "qr.cu", "sd.cu", "kbest.cu", "mixed.cu", "linear.cu", "noalloc.cu", "mlp.cu", "peaks.cu"]
+SOURCES = ["api.cu", "qr.cu", "sd.cu", "sd_group.cu", "kbest.cu", "mixed.cu", "linear.cu", "noalloc.cu", "mlp.cu", "peaks.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", INCLUDE, "-I", CSRC]
 

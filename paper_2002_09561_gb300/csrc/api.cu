@@ -29,6 +29,7 @@ struct mdx_ctx {
   void* sd_shared = nullptr;
   void* sd_queue = nullptr;
   unsigned char* sd_vstate = nullptr;
+  int* sd_order = nullptr;
   unsigned long long sd_epoch = 0;
   // learned radius model (mdx_mlp_init), null until created
   mdx::MlpState* mlp = nullptr;
@@ -139,7 +140,7 @@ void free_all(mdx_ctx* c) {
       if (c->prof_ev[i][k]) cudaEventDestroy(c->prof_ev[i][k]);
   void* ptrs[] = {c->R64, c->yb64, c->R32,  c->yb32, c->singular, c->counter,  c->counts,
                   c->sH,  c->sy,   c->snv,  c->ssym, c->ssym2,    c->smet,     c->svst,
-                  c->sstats, c->sd_shared, c->sd_queue, c->sd_vstate};
+                  c->sstats, c->sd_shared, c->sd_queue, c->sd_vstate, c->sd_order};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (c->mx_graph) cudaGraphExecDestroy(c->mx_graph);
@@ -355,7 +356,7 @@ mdx_status run_detect(int algo, mdx_ctx* c, const mdx_params* p, int batch, cons
     e = launch_mixed(m, c->mx_W, 0, c->num_sms, s);
   } else if (algo == ALGO_SD) {
     if (ev) cudaEventRecord(ev[1], s);
-    SdWorkspace w{c->sd_shared, c->sd_queue, kSdQueueSlots, c->sd_vstate, ++c->sd_epoch};
+    SdWorkspace w{c->sd_shared, c->sd_queue, kSdQueueSlots, c->sd_vstate, ++c->sd_epoch, c->sd_order};
     e = launch_sd(a, w, c->num_sms, s);
   }
   else if (algo == ALGO_KBEST) {
@@ -913,6 +914,7 @@ mdx_status mdx_create(mdx_ctx** out, int device, int max_batch, int max_n_rx, in
   chk(alloc(c, reinterpret_cast<unsigned char**>(&c->sd_shared), sd_shared_bytes()));
   chk(alloc(c, reinterpret_cast<unsigned char**>(&c->sd_queue), sd_task_bytes() * kSdQueueSlots));
   chk(alloc(c, &c->sd_vstate, B * sd_vec_state_bytes(n)));
+  chk(alloc(c, &c->sd_order, sd_order_ints(max_batch)));
   if (e != cudaSuccess) {
     cudaGetLastError();
     free_all(c);

@@ -135,7 +135,9 @@ struct SdWorkspace {
   unsigned int qcap;     // power of two
   unsigned char* vstate; // batch x sd_vec_state_bytes(n)
   unsigned long long epoch;  // distinct per launch on this workspace
+  int* order;            // batch ints + sd_order_scratch_ints(): the fresh-vector order
 };
+size_t sd_order_ints(int max_batch);
 size_t sd_shared_bytes();
 size_t sd_error_offset();
 size_t sd_counters_offset();

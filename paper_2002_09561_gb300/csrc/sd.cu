@@ -3,10 +3,14 @@
 // (Sec. IV-C, Eq. inc) and dynamic subtree splitting between warps (the
 // load balancing of the paper's parallel SD, Sec. V-C, recast for a GPU).
 //
+// This warp-per-task kernel serves n > 32 (more than 16 transmit antennas);
+// smaller systems take the group kernel of sd_group.cu, which runs the same
+// search with four vectors per warp.
+//
 // Unit of work: a task = one tree node (rows n-1..L+1 fixed, row L to
 // expand) of one vector, explored depth-first by one warp.  A vector starts
 // as its root task.  Warps take work in this order: a queued task, else a
-// fresh vector, else they wait (idle).  While any warp is idle, a busy warp
+// fresh vector (heaviest first, see launch_sd), else they wait (idle).  While any warp is idle, a busy warp
 // checks every kSplitEvery nodes and donates all untried children of its
 // top-most open level whose next child is inside the sphere as new tasks,
 // marking that level exhausted.  The only
@@ -39,144 +43,11 @@
 // launch's error word and the warp moves on; an idle warp that waits too
 // long simply exits (the busy warps drain the queue themselves before they
 // finish).
-#include "mdx_internal.cuh"
+#include "sd_common.cuh"
 
 namespace mdx {
 
-// Global state of one SD launch (zeroed before the launch).
-struct SdShared {
-  unsigned int vec_next;
-  unsigned int q_head;
-  unsigned int q_tail;
-  int outstanding;  // tasks queued or running (root tasks included)
-  int idle;         // warps waiting for work
-  int error;        // a bounded wait expired
-  // event counters (read back by mdx_profile_read)
-  unsigned int split_checks;   // periodic checks that saw idle warps
-  unsigned int splits;         // checks that donated at least one task
-  unsigned int donated;        // tasks donated
-  unsigned int no_level;       // checks that found no level to split
-  int pad[6];
-};
-
 namespace {
-
-constexpr int kWarpsMax = 4;     // warps per CTA
-constexpr int kCand = 8;         // leaf candidates kept per vector
-constexpr int kSplitEvery = 128; // nodes between split / radius checks
-constexpr int kTaskPath = 224;   // path bytes in a task record (n <= 224)
-constexpr int kMinSplitLevel = 3; // donate only children with at least 3 rows below
-constexpr int kSplitMinNodes = 512; // a task donates only after searching this many nodes
-
-struct SdTask {
-  unsigned long long seq;  // (epoch << 32) | (slot index + 1) once written
-  int v;
-  int level;  // row to expand; rows level+1..n-1 fixed in x[]
-  float ped;
-  int pad;
-  uint8_t x[kTaskPath];
-};
-static_assert(sizeof(SdTask) == 248, "task record layout");
-
-// Per-vector state in global memory.
-struct SdVec {
-  unsigned int r2bits;  // FP32 r^2 bits (non-negative floats order like uints)
-  int pending;          // unfinished tasks of this vector
-  int lock;             // candidate-list lock
-  int ncand;
-  unsigned long long nodes, peds, flops;
-  int restarts;
-  int budget_hit;
-  float E;
-  float r2_start;  // radius of the current pass (for doubling)
-  float cand_ped[kCand];
-  // followed by kCand paths of path_pad(n) bytes
-};
-
-__host__ __device__ inline int path_pad(int n) { return round_up(n, 16); }
-__host__ __device__ inline size_t vec_state_bytes(int n) {
-  return round_up((int)(sizeof(SdVec) + (size_t)kCand * path_pad(n)), 16);
-}
-
-__host__ __device__ inline size_t sd_warp_bytes(int n) {
-  const size_t b = sizeof(float) * (2 * (size_t)tri_stride32(n) + 5 * (size_t)n) +
-                   sizeof(int) * (size_t)n + (size_t)path_pad(n);
-  return (b + 15) / 16 * 16;
-}
-
-struct SdArgs {
-  SearchArgs a;
-  SdShared* sh;
-  SdTask* queue;
-  unsigned int qcap;  // power of two
-  unsigned char* vstate;
-  size_t vstride;
-  unsigned long long epoch;
-};
-
-__device__ __forceinline__ SdVec* vec_of(const SdArgs& g, int v) {
-  return reinterpret_cast<SdVec*>(g.vstate + (size_t)v * g.vstride);
-}
-__device__ __forceinline__ uint8_t* cand_path(SdVec* vs, int q, int n) {
-  return reinterpret_cast<uint8_t*>(vs + 1) + (size_t)q * path_pad(n);
-}
-
-// Claim a queued task (lane 0); returns the slot index or -1 if the queue is empty.
-__device__ long long queue_pop(const SdArgs& g) {
-  volatile unsigned int* head = &g.sh->q_head;
-  volatile unsigned int* tail = &g.sh->q_tail;
-  for (int tries = 0; tries < 64; ++tries) {
-    const unsigned int h = *head;
-    if (h >= *tail) return -1;
-    if (atomicCAS(&g.sh->q_head, h, h + 1) == h) return (long long)h;
-  }
-  return -1;
-}
-
-// Reserve cnt consecutive slots (lane 0); -1 if the ring has no room.  The
-// head is read before the tail: the head never passes a tail read after it,
-// so tail - head cannot underflow.
-__device__ long long queue_reserve(const SdArgs& g, int cnt) {
-  for (int tries = 0; tries < 4096; ++tries) {
-    const unsigned int h = *(volatile unsigned int*)&g.sh->q_head;
-    const unsigned int t = *(volatile unsigned int*)&g.sh->q_tail;
-    if (t - h + (unsigned)cnt > g.qcap) return -1;
-    if (atomicCAS(&g.sh->q_tail, t, t + (unsigned)cnt) == t) return (long long)t;
-    __nanosleep(16);
-  }
-  return -1;
-}
-
-// A slot used before in this launch (index >= qcap) may be written only
-// after the consumer of its previous occupant has copied it out and marked
-// it free ((epoch << 32) | 0).  Lane 0; false if that never happened.
-__device__ bool slot_writable(const SdArgs& g, SdTask* t, unsigned long long idx) {
-  if (idx < g.qcap) return true;
-  const unsigned long long freed = g.epoch << 32;
-  for (int it = 0; it < (1 << 22); ++it) {
-    if (*(volatile unsigned long long*)&t->seq == freed) {
-      __threadfence();
-      return true;
-    }
-    __nanosleep(32);
-  }
-  return false;
-}
-
-__device__ __forceinline__ bool lock_acquire(int* lk) {
-  for (int it = 0; it < (1 << 22); ++it) {
-    if (atomicCAS(lk, 0, 1) == 0) {
-      __threadfence();
-      return true;
-    }
-    __nanosleep(64);
-  }
-  return false;
-}
-__device__ __forceinline__ void lock_release(int* lk) {
-  __threadfence();
-  atomicExch(lk, 0);
-}
 
 // Blocks per SM the register allocation is made for: for n <= 32 the shared
 // memory allows up to eight 4-warp blocks; six (80 registers, no spills)
@@ -252,7 +123,10 @@ __global__ void __launch_bounds__(kWarpsMax * 32, ROWS == 1 ? MDX_SD_MIN_BLOCKS_
           continue;
         }
       } else {
-        if (lane == 0) v = (int)atomicAdd(&g.sh->vec_next, 1u);
+        if (lane == 0) {
+          v = (int)atomicAdd(&g.sh->vec_next, 1u);
+          if (v < a.batch && g.order) v = g.order[v];
+        }
         v = __shfl_sync(0xffffffffu, v, 0);
         if (v < a.batch) {
           fresh = true;
@@ -746,6 +620,47 @@ __global__ void __launch_bounds__(kWarpsMax * 32, ROWS == 1 ? MDX_SD_MIN_BLOCKS_
 
 #undef SD_FOLD
 
+// Fresh vectors are taken heaviest first (longest-processing-time order),
+// so that the searches that take longest start early and their subtrees can
+// be split while the light vectors still keep every worker busy.  The cost
+// proxy is the noise variance (the search grows steeply as the SNR falls),
+// bucketed at a quarter octave: a counting sort by histogram, exclusive scan
+// and scatter.  The order inside a bucket is arbitrary; answers do not depend
+// on it.
+constexpr int kOrderBuckets = 1024;
+
+__device__ __forceinline__ int order_bucket(double nv) {
+  // -log2(sigma^2) * 4, offset: ascending buckets = descending noise variance
+  const float b = floorf(-log2f((float)nv) * 4.0f) + (float)(kOrderBuckets / 2);
+  return (int)fminf(fmaxf(b, 0.0f), (float)(kOrderBuckets - 1));
+}
+
+__global__ void sd_order_hist(int batch, const double* __restrict__ nv, unsigned int* cnt) {
+  const int v = blockIdx.x * blockDim.x + threadIdx.x;
+  if (v < batch) atomicAdd(&cnt[order_bucket(nv[v])], 1u);
+}
+
+// exclusive scan of the kOrderBuckets counts into cnt[kOrderBuckets + b]
+__global__ void __launch_bounds__(kOrderBuckets) sd_order_scan(unsigned int* cnt) {
+  __shared__ unsigned int s[kOrderBuckets];
+  const int t = threadIdx.x;
+  const unsigned int mine = cnt[t];
+  s[t] = mine;
+  __syncthreads();
+  for (int o = 1; o < kOrderBuckets; o <<= 1) {
+    const unsigned int add = t >= o ? s[t - o] : 0u;
+    __syncthreads();
+    s[t] += add;
+    __syncthreads();
+  }
+  cnt[kOrderBuckets + t] = s[t] - mine;
+}
+
+__global__ void sd_order_scatter(int batch, const double* __restrict__ nv, unsigned int* cnt, int* order) {
+  const int v = blockIdx.x * blockDim.x + threadIdx.x;
+  if (v < batch) order[atomicAdd(&cnt[kOrderBuckets + order_bucket(nv[v])], 1u)] = v;
+}
+
 template <int ROWS>
 cudaError_t launch_rows(const SdArgs& g, int num_sms, cudaStream_t s) {
   // as many warps per CTA (up to kWarpsMax) as fit in 200 KB of shared memory
@@ -768,6 +683,7 @@ cudaError_t launch_rows(const SdArgs& g, int num_sms, cudaStream_t s) {
 }  // namespace
 
 size_t sd_vec_state_bytes(int n) { return vec_state_bytes(n); }
+size_t sd_order_ints(int max_batch) { return (size_t)max_batch + 2 * kOrderBuckets; }
 size_t sd_task_bytes() { return sizeof(SdTask); }
 size_t sd_shared_bytes() { return sizeof(SdShared); }
 size_t sd_error_offset() { return offsetof(SdShared, error); }
@@ -784,9 +700,23 @@ cudaError_t launch_sd(const SearchArgs& a, const SdWorkspace& w, int num_sms, cu
   g.vstate = w.vstate;
   g.vstride = vec_state_bytes(a.n);
   g.epoch = w.epoch;
+  g.order = nullptr;
   cudaError_t e = cudaMemsetAsync(w.shared, 0, sizeof(SdShared), s);
   if (e != cudaSuccess) return e;
-  if (a.n <= 32) return launch_rows<1>(g, num_sms, s);
+  if (a.noise_var && w.order && a.batch > 1) {
+    int* order = w.order;
+    unsigned int* cnt = reinterpret_cast<unsigned int*>(order + a.batch);
+    e = cudaMemsetAsync(cnt, 0, sizeof(unsigned int) * kOrderBuckets, s);
+    if (e != cudaSuccess) return e;
+    const int blocks = (a.batch + 255) / 256;
+    sd_order_hist<<<blocks, 256, 0, s>>>(a.batch, a.noise_var, cnt);
+    sd_order_scan<<<1, kOrderBuckets, 0, s>>>(cnt);
+    sd_order_scatter<<<blocks, 256, 0, s>>>(a.batch, a.noise_var, cnt, order);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    g.order = order;
+  }
+  if (a.n <= 32) return launch_sd_group(g, num_sms, s);
   if (a.n <= 64) return launch_rows<2>(g, num_sms, s);
   if (a.n <= 128) return launch_rows<4>(g, num_sms, s);
   return launch_rows<7>(g, num_sms, s);
