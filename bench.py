@@ -80,9 +80,9 @@ METRIC = "decoded vectors/s at matched BER (16x16 16QAM, 100x100 64QAM), learned
 # grows with the number of vectors), with the capture it comes from.  A kernel
 # changed since its capture has no entry here until it is captured again.
 TRAFFIC_PER_VECTOR = {
-    "16x16-16qam-sd-learned": ((154.186752e6 + 4.764160e6) / 20000,
-                               "ncu capture of sd_kernel, 20,000 vectors of the learned 16x16 sweep "
-                               "(profiles/sd_kernel_16x16_16qam_sweep_20k.md), scaled by vectors"),
+    "16x16-16qam-sd-learned": ((227.213312e6 + 6.532864e6) / 30000,
+                               "ncu capture of sd_group_kernel, 30,000 vectors of the learned 16x16 sweep "
+                               "(profiles/sd_group_kernel_16x16_16qam_sweep_30k.md), scaled by vectors"),
     "100x100-64qam-hybrid32-learned": ((517.457664e6 + 4.140800e6) / 2000,
                                        "ncu capture of hybrid_kernel, 2,000 vectors of the learned 100x100 "
                                        "workload (profiles/hybrid_kernel_100x100_64qam_2k.md), scaled by vectors"),
@@ -604,7 +604,7 @@ def main():
                 "scaling": "weak", "vs_baseline": None, "dtype": "f32 search, f64 QR and re-scoring",
                 "data": "synthetic (seeded Rayleigh channels, uniform QAM symbols, AWGN)",
                 "config": cfg, "roofline": roof, "qr_roofline": qr_roof, "cpu_baseline": cpu, "e2e": e2e,
-                "gpu_launches": (8 if learned else 3) * args.steps, "clocks": sampler.summary(),
+                "gpu_launches": launches_per_call(algo, learned, n) * args.steps, "clocks": sampler.summary(),
                 "measured_peaks": probe, "oracle_check": check, "plain": plain, "babai": babai,
                 "quality": {"ber": bit_err / bits, "ser": sym_err / (B * world * n),
                             "budget_exceeded": tot["budget_exceeded"], "radius_doublings": tot["radius_doublings"],
@@ -616,6 +616,16 @@ def main():
         ctx.close()
     if dist is not None:
         dist.destroy_process_group()
+
+
+def launches_per_call(algo, learned, n):
+    """Kernels of one timed step: the QR, the network (features, three GEMMs,
+    radius) when learned, the sphere decoder's heaviest-first ordering (three
+    kernels) for detect_sd, the search, and the error count."""
+    k = 3 + (5 if learned else 0)
+    if algo == "sd":
+        k += 3
+    return k
 
 
 class Arm:
