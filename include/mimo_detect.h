@@ -74,7 +74,7 @@ typedef enum {
 enum {
   MDX_V_OK = 0,              /* searched to completion */
   MDX_V_EMPTY_RETRIED = 1,   /* the initial sphere held no leaf; the radius was doubled
-                                (r^2 <- 4 r^2) until one did; the answer is still exact
+                                (r^2 <- 2 r^2) until one did; the answer is still exact
                                 for detect_sd */
   MDX_V_BUDGET_EXCEEDED = 2, /* node_budget ran out; best leaf found so far (or the
                                 first leaf reached) is returned */

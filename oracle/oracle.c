@@ -334,7 +334,7 @@ int orc_sd(int n, int P, const double* R, const double* ybar, const double* leve
     sd_visit(&s, n - 1, 0.0);
     if (s.found || s.budget_hit) break;
     /* empty sphere: double the radius and search again */
-    r2 *= 4.0;
+    r2 *= 2.0; /* empty sphere: double the radius r^2 (Sec. III-B names r^2 the radius) */
     st->restarts++;
     status = ORC_V_EMPTY_RETRIED;
     if (!(r2 < 1e300)) break;
@@ -455,7 +455,7 @@ int orc_kbest(int n, int P, const double* R, const double* ybar, const double* l
     int S = kbest_run(n, P, R, ybar, levels, K, r2, n - 1, prefix, 0.0, cur, nxt, pc, pn, cand,
                       k_out, &ped, &gap, st);
     if (S > 0) break;
-    r2 *= 4.0; /* empty sphere: double the radius */
+    r2 *= 2.0; /* empty sphere: double the radius r^2 */
     st->restarts++;
     status = ORC_V_EMPTY_RETRIED;
     if (!(r2 < 1e300)) {
@@ -561,7 +561,7 @@ int orc_hybrid(int n, int P, const double* R, const double* ybar, const double* 
     if (d == 0) hybrid_handoff(&s, n - 1, 0.0);
     else hybrid_visit(&s, n - 1, 0.0);
     if (s.found) break;
-    r2 *= 4.0;
+    r2 *= 2.0; /* empty sphere: double the radius r^2 (Sec. III-B names r^2 the radius) */
     st->restarts++;
     status = ORC_V_EMPTY_RETRIED;
     if (!(r2 < 1e300)) break;
@@ -664,7 +664,7 @@ int orc_sd_complex(int n, int P, const double* R, const double* ybar, const doub
     s.st = st;
     sdc_visit(&s, n / 2 - 1, 0.0);
     if (s.found || s.budget_hit) break;
-    r2 *= 4.0; /* empty sphere: double the radius and search again */
+    r2 *= 2.0; /* empty sphere: double the radius r^2 and search again */
     st->restarts++;
     status = ORC_V_EMPTY_RETRIED;
     if (!(r2 < 1e300)) break;
@@ -756,7 +756,7 @@ int orc_kbest_complex(int n, int P, const double* R, const double* ybar, const d
     gap = 1.0;
     const int S = kbest_run_complex(n, P, R, ybar, levels, K, r2, cur, nxt, pc, pn, cand, k_out, &ped, &gap, st);
     if (S > 0) break;
-    r2 *= 4.0; /* empty sphere: double the radius */
+    r2 *= 2.0; /* empty sphere: double the radius r^2 */
     st->restarts++;
     status = ORC_V_EMPTY_RETRIED;
     if (!(r2 < 1e300)) {

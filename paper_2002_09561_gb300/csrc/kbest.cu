@@ -741,7 +741,7 @@ __global__ void __launch_bounds__(1024) kbest_kernel(SearchArgs a, KbLayout L) {
       }
       if (S > 0 || !(misc_f[1] < INFINITY) || restarts >= 64) break;
       __syncthreads();
-      if (tid == 0) misc_f[1] *= 4.0f;  // empty sphere: double the radius
+      if (tid == 0) misc_f[1] *= 2.0f;  // empty sphere: double the radius r^2
       ++restarts;
       __syncthreads();
     }
@@ -1139,7 +1139,7 @@ __global__ void hybrid_kernel(SearchArgs a, HyLayout L) {
       const float r2now = __uint_as_float((unsigned)misc[5]);
       if (nc > 0 || misc[8] || !(r2now < INFINITY) || restarts >= 64) break;
       // empty sphere: double the radius and run master and workers again
-      if (tid == 0) misc[5] = (int)__float_as_uint(4.0f * r2now);
+      if (tid == 0) misc[5] = (int)__float_as_uint(2.0f * r2now);
       ++restarts;
       __syncthreads();
     }

@@ -270,8 +270,8 @@ __device__ void sd_request(const MixedArgs& g, const MixedReq& q, int r, const f
       flops += 2 * (n - 1 - i) + 4 * P;
     }
     if (ncand == 0 && !bh && r2_start < INFINITY && restarts < 64) {
-      // empty sphere: r^2 <- 4 r^2 and search again
-      r2_start *= 4.0f;
+      // empty sphere: r^2 <- 2 r^2 and search again
+      r2_start *= 2.0f;
       r2 = r2_start;
       ++restarts;
       continue;
@@ -432,7 +432,7 @@ __device__ void sdc_request(const MixedArgs& g, const MixedReq& q, int r, const 
       flops += 4 * (n - 2 - 2 * j) + 10 * Q;
     }
     if (ncand == 0 && !bh && r2_start < INFINITY && restarts < 64) {
-      r2_start *= 4.0f;  // empty sphere: r^2 <- 4 r^2 and search again
+      r2_start *= 2.0f;  // empty sphere: r^2 <- 2 r^2 and search again
       r2 = r2_start;
       ++restarts;
       continue;
@@ -474,7 +474,7 @@ __device__ void kb_request(const MixedArgs& g, const MixedReq& q, int r, const f
                         &flops);
     __syncwarp();
     if (S > 0 || !(r2 < INFINITY) || restarts >= 64) break;
-    r2 *= 4.0f;  // every survivor left the sphere: r^2 <- 4 r^2
+    r2 *= 2.0f;  // every survivor left the sphere: r^2 <- 2 r^2
     ++restarts;
   }
   const int nc = S < kCandMax ? S : kCandMax;

@@ -530,11 +530,11 @@ __global__ void __launch_bounds__(kWarpsMax * 32, ROWS == 1 ? MDX_SD_MIN_BLOCKS_
       const float r2s = __shfl_sync(0xffffffffu, lane == 0 ? vv->r2_start : 0.0f, 0);
       const int rs = __shfl_sync(0xffffffffu, lane == 0 ? vv->restarts : 0, 0);
       if (nc == 0 && !bh && r2s < INFINITY && rs < 64) {
-        // empty sphere: double the radius (r^2 <- 4 r^2) and search the root
+        // empty sphere: double the radius (r^2 <- 2 r^2) and search the root
         // again; this warp takes the new root itself (outstanding stays: the
         // new root replaces this task)
         if (lane == 0) {
-          const float nr2 = 4.0f * r2s;
+          const float nr2 = 2.0f * r2s;
           vs->r2_start = nr2;
           vs->r2bits = __float_as_uint(nr2);
           vs->restarts += 1;

@@ -53,7 +53,7 @@
 // then on the vector's radius is shared through atomicMin on its FP32 bits,
 // its tasks merge their candidates into the vector's list under its lock,
 // and the task that finishes last re-scores that list.  An empty sphere
-// doubles the radius (r^2 <- 4 r^2) and searches the root again.
+// doubles the radius (r^2 <- 2 r^2) and searches the root again.
 //
 // Waiting.  A group with a ticket looks at its slot every 16 passes while
 // its warp has busy groups; a warp whose groups all wait polls the slots
@@ -266,9 +266,9 @@ __global__ void __launch_bounds__(group_warps<G>() * 32, MDX_SDG_MIN_BLOCKS) sd_
           SdVec* vs = vec_of(g, v);
           if (solo) {
             if (ncl == 0 && !budget_hit && r2_start < INFINITY && restarts < 64) {
-              // empty sphere: r^2 <- 4 r^2 and the root again
+              // empty sphere: r^2 <- 2 r^2 and the root again
               restart = true;
-              r2_start *= 4.0f;
+              r2_start *= 2.0f;
               ++restarts;
               if (gl == 0) {
                 vs->r2_start = r2_start;
@@ -337,11 +337,11 @@ __global__ void __launch_bounds__(group_warps<G>() * 32, MDX_SDG_MIN_BLOCKS) sd_
             nodes = peds = flops = 0;
             if (last) {
               if (gnc == 0 && !bh && r2s < INFINITY && rs < 64) {
-                // empty sphere over all tasks: the root again with r^2 <- 4 r^2,
+                // empty sphere over all tasks: the root again with r^2 <- 2 r^2,
                 // as a single task of this group (outstanding unchanged); the
                 // counts so far are in vs
                 restart = true;
-                r2_start = 4.0f * r2s;
+                r2_start = 2.0f * r2s;
                 restarts = rs + 1;
                 if (gl == 0) {
                   vs->r2_start = r2_start;

@@ -84,7 +84,7 @@ def np_kbest(R, yb, lev, K, r2):
         x, d = kb.run(r2, kb.n - 1, np.zeros(kb.n, dtype=int), gaps)
         if x is not None:
             return x, d, min(gaps, default=1.0)
-        r2 *= 4.0
+        r2 *= 2.0
 
 
 def np_kbest_complex(R, yb, lev, K, r2):
@@ -117,7 +117,7 @@ def np_kbest_complex(R, yb, lev, K, r2):
             if len(surv) > 1:
                 gaps.append(_rel_gap(last[0], last[1]))
             return surv[0], last[0], min(gaps, default=1.0)
-        r2 *= 4.0
+        r2 *= 2.0
 
 
 def np_hybrid(R, yb, lev, K, d, r2):
@@ -150,7 +150,7 @@ def np_hybrid(R, yb, lev, K, d, r2):
         visit(n - 1, np.zeros(n, dtype=int))
         if st["best"] is not None:
             return st["best"], st["r2"], min(st["gaps"], default=1.0)
-        r2 *= 4.0
+        r2 *= 2.0
 
 
 CASES_KB = [(3, 16, 4, "inf", 6.0), (4, 4, 3, "inf", 2.0), (3, 64, 5, "paper", 14.0), (2, 16, 2, "paper", 0.0),
