@@ -202,24 +202,20 @@ def test_hybrid_survivor_widths(env, N, qam, K, d, snr):
 
 def test_hybrid_100x100_64qam_k128_two_workspaces(env):
     """K = 128 at 100x100: only two K-best workspaces fit beside R, so the
-    best prefix runs on the whole CTA and the others on two of its eight warps."""
+    best prefix runs on the whole CTA and the others on two of its eight
+    warps.  (The benchmark's configurations, 40 vectors per SNR point, are in
+    test_gpu_headline.py; this is the quick form.)"""
     w = wl.generate(72, 8, 100, 100, 64, 28.0)
     gpu = _run(env, "hybrid", w, 64, K=128, depth=4, radius="paper")
     ref = oracle.detect_batch("hybrid", w["H"], w["y"], w["noise_var"], 64, K=128, depth=4, radius="paper")
-    same = (gpu[0] == ref["sym"]).all(axis=1)
-    assert same.mean() >= 7 / 8
-    rel = np.abs(gpu[1] - ref["metric"]) / ref["metric"]
-    assert rel[same].max() < MET_RTOL
+    _compare(gpu, ref, KB_GAP, max_mismatch=0.25, label="hybrid 100x100 64-QAM K=128 28 dB")
 
 
 def test_hybrid_100x100_64qam_sample(env):
     w = wl.generate(71, 6, 100, 100, 64, 28.0)
     gpu = _run(env, "hybrid", w, 64, K=32, depth=4, radius="paper")
     ref = oracle.detect_batch("hybrid", w["H"], w["y"], w["noise_var"], 64, K=32, depth=4, radius="paper")
-    same = (gpu[0] == ref["sym"]).all(axis=1)
-    assert same.mean() >= 5 / 6
-    rel = np.abs(gpu[1] - ref["metric"]) / ref["metric"]
-    assert rel[same].max() < MET_RTOL
+    _compare(gpu, ref, KB_GAP, max_mismatch=0.25, label="hybrid 100x100 64-QAM K=32 28 dB")
 
 
 # ------------------------------------------------------------------------ errors and I/O
