@@ -692,8 +692,12 @@ __global__ void __launch_bounds__(group_warps<G>() * 32, MDX_SDG_MIN_BLOCKS) sd_
     // One child of the current level, in Schnorr-Euchner order: its partial
     // distance, then pop (none left inside the sphere), a leaf (slow path),
     // or descend.  Everything the step may need from shared memory is loaded
-    // first, independently of the child chosen.
-    if (mode == 1) {
+    // first, independently of the child chosen.  The step has no branch: the
+    // groups of a warp that pop, descend, or have no task run the same
+    // instructions under their own predicates (a branch would serialise the
+    // outcomes and stall on its resolution every pass).
+    {
+      const bool busy = mode == 1;
       const int ip = min(i + 1, n - 1), im = max(i - 1, 0);
       const int ci = col_off(i);
       float rcv[RPL], zinv[RPL];
@@ -706,60 +710,52 @@ __global__ void __launch_bounds__(group_warps<G>() * 32, MDX_SDG_MIN_BLOCKS) sd_
       const float2 curp = CUR(ip);
       const float2 lrn = LR(im);
       const bool has_lo = flo >= 0.0f, has_hi = fhi < Pf;
-      const bool has = has_lo || has_hi;
+      const bool has = busy && (has_lo || has_hi);
       const bool take_lo = has_lo && (!has_hi || fabsf(u - flo) <= fabsf(fhi - u));
       const float kf = take_lo ? flo : fhi;
-      flo = take_lo ? flo - 1.0f : flo;
+      flo = (has && take_lo) ? flo - 1.0f : flo;
       fhi = (has && !take_lo) ? fhi + 1.0f : fhi;
       const float av = fmaf(kf, 2.0f, -(Pf - 1.0f)) * alpha;  // (2k - (P - 1)) alpha
       const float d = fmaf(-rii, av, c);
       const float ped = fmaf(d, d, ped_par);
       p32 += has ? 1 : 0;
       const bool ok = has && ped < bnd;
-      const bool desc = ok && i > 0 && n32 < left32;
-      if (ok && i > 0 && n32 >= left32) budget_hit = true;
-      ev_done = (!ok && i == top) || (ok && i > 0 && n32 >= left32);
+      const bool deep = ok && i > 0;
+      const bool desc = deep && n32 < left32;
+      const bool bstop = deep && n32 >= left32;
+      budget_hit = budget_hit || bstop;
+      ev_done = busy && ((!ok && i == top) || bstop);
       ev_leaf = ok && i == 0;
       leaf_ped = ped;
       leaf_k = (int)kf;
-      const bool pop = !ok && i != top;
+      const bool pop = busy && !ok && i != top;
       float cn = 0.0f;
       const int cm = col_off(im);
 #pragma unroll
       for (int t = 0; t < RPL; ++t) {
         const int r = gl + G * t;
-        if (desc && r < i) {
-          const float z = fmaf(-rcv[t], av, zinv[t]);
-          ZW(cm + r) = z;
-          if (r == i - 1) cn = z;
-        }
+        const float z = fmaf(-rcv[t], av, zinv[t]);
+        if (desc && r < i) ZW(cm + r) = z;
+        cn = (r == i - 1) ? z : cn;
       }
       if (desc) {
         ST(i) = make_float4(ped_par, c, u, rii);
         CUR(i) = make_float2(flo, fhi);
         XS(i) = (uint8_t)(int)kf;
       }
-      const float cnew = __shfl_sync(gmask, cn, lead + ((i - 1) & (G - 1)));
-      if (desc) {
-        i = im;
-        ped_par = ped;
-        c = cnew;
-        rii = lrn.x;
-        u = fmaf(cnew, lrn.y, uoff);
-        flo = fminf(fmaxf(ceilf(u - 0.5f), 0.0f), Pf - 1.0f);
-        fhi = flo + 1.0f;
-        ++n32;
-        lsum += im;
-        ++task_nodes;
-      } else if (pop) {
-        i = ip;
-        ped_par = stp.x;
-        c = stp.y;
-        u = stp.z;
-        rii = stp.w;
-        flo = curp.x;
-        fhi = curp.y;
-      }
+      const float cnew = __shfl_sync(full, cn, lead + ((i - 1) & (G - 1)));
+      const float unew = fmaf(cnew, lrn.y, uoff);
+      const float flonew = fminf(fmaxf(ceilf(unew - 0.5f), 0.0f), Pf - 1.0f);
+      i = desc ? im : (pop ? ip : i);
+      ped_par = desc ? ped : (pop ? stp.x : ped_par);
+      c = desc ? cnew : (pop ? stp.y : c);
+      u = desc ? unew : (pop ? stp.z : u);
+      rii = desc ? lrn.x : (pop ? stp.w : rii);
+      flo = desc ? flonew : (pop ? curp.x : flo);
+      fhi = desc ? flonew + 1.0f : (pop ? curp.y : fhi);
+      n32 += desc ? 1 : 0;
+      lsum += desc ? im : 0;
+      task_nodes += desc ? 1 : 0;
     }
 
     // ===================================================== periodic check
