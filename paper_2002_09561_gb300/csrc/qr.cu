@@ -53,7 +53,7 @@ __device__ void qr_writeout(int M, GetA getA, double2* alpha, double* tau, const
   const int nb = M * (M + 1) / 2;  // complex entries (a, c) with a <= c
   for (int t = tid; t < nb; t += nthr) {
     // unrank t -> (a, c), a <= c, column-major over c
-    int c = (int)((sqrt(8.0 * t + 1.0) - 1.0) * 0.5);
+    int c = (int)((sqrtf(8.0f * (float)t + 1.0f) - 1.0f) * 0.5f);  // exact after the corrections below
     while (c * (c + 1) / 2 > t) --c;
     while ((c + 1) * (c + 2) / 2 <= t) ++c;
     const int a = t - c * (c + 1) / 2;
@@ -225,13 +225,17 @@ __device__ void qr_one(int N, int M, const double2* __restrict__ Hb, const doubl
 
 constexpr int kQrdWarps = 8;  // per CTA where one matrix fills the SM's shared memory, else 4 (two CTAs per SM)
 constexpr int kPanelWarps = 4;
-constexpr int kTileStride = 12;  // doubles per column of a warp's 8 x 8 tile
+constexpr int kTileStride = 12;                     // doubles per column of a warp's 8 x 8 tile
+constexpr int kTileDoubles = 2 * 8 * kTileStride;  // one W tile: real plane, then imaginary plane
 
+// Shared memory of one matrix: A = [H | y] as real and imaginary planes; two
+// Y = V T buffers (the panel being applied and the one being factored); the
+// W tiles of the trailing update; panel reduction scratch; alpha, tau.  V is
+// not stored separately: below the diagonal of its panel columns A holds it.
 struct QrdLayout {
   int N8, C8, S;
-  size_t off_are, off_aim, off_vre, off_vim, off_yre, off_yim, off_tile, off_red, off_alpha, off_tau, off_sing,
-      bytes;
-  __host__ __device__ void init(int N, int M, int warps) {
+  size_t off_are, off_aim, off_y[2], off_tile, off_red, off_alpha, off_tau, off_sing, bytes;
+  __host__ __device__ void init(int N, int M) {
     N8 = round_up(N, 8);
     C8 = round_up(M + 1, 8);
     S = N8 + 4;
@@ -243,12 +247,9 @@ struct QrdLayout {
     };
     off_are = take(sizeof(double) * (size_t)C8 * S);
     off_aim = take(sizeof(double) * (size_t)C8 * S);
-    off_vre = take(sizeof(double) * 8 * (size_t)S);
-    off_vim = take(sizeof(double) * 8 * (size_t)S);
-    off_yre = take(sizeof(double) * 8 * (size_t)S);
-    off_yim = take(sizeof(double) * 8 * (size_t)S);
-    off_tile = take(sizeof(double) * 2 * 8 * kTileStride * (C8 / 8));  // W of every trailing tile
-    (void)warps;
+    off_y[0] = take(sizeof(double) * 16 * (size_t)S);  // Y re: 8 columns of stride S, then Y im
+    off_y[1] = take(sizeof(double) * 16 * (size_t)S);
+    off_tile = take(sizeof(double) * kTileDoubles * (C8 / 8));
     off_red = take(sizeof(double) * (8 + 2 * 16 * kPanelWarps));
     off_alpha = take(sizeof(double2) * (size_t)M);
     off_tau = take(sizeof(double) * (size_t)M);
@@ -276,26 +277,39 @@ __device__ __forceinline__ double wsum(double v) {
 }
 
 __device__ __forceinline__ void panel_sync() { asm volatile("bar.sync 1, %0;" ::"n"(kPanelWarps * 32)); }
+__device__ __forceinline__ void update_sync(int threads) { asm volatile("bar.sync 2, %0;" ::"r"(threads)); }
 
-// 1 / sqrt(x) for a positive normal x: a single-precision estimate refined by
-// two Newton-Raphson steps y <- y (3 - x y^2) / 2 (quadratic convergence from
-// about 2^-22 relative error to the double rounding level).
-__device__ __forceinline__ double rsqrt_nr(double x) {
-  if (!(x > 1e-30 && x < 1e30)) return 1.0 / sqrt(x);
-  double y = (double)rsqrtf((float)x);
-  const double hx = 0.5 * x;
-  y = y * fma(-hx * y, y, 1.5);
-  y = y * fma(-hx * y, y, 1.5);
-  return y;
+// Conversions between a positive normal double in [1e-30, 1e30] and a float
+// estimate of it, done on the integer pipe (rebias the exponent, keep the top
+// 23 fraction bits): an FP64 conversion would occupy the FP64 unit.
+__device__ __forceinline__ float f32_estimate(double x) {
+  const unsigned hi = (unsigned)__double2hiint(x), lo = (unsigned)__double2loint(x);
+  const unsigned e = ((hi >> 20) & 0x7ffu) - 1023u + 127u;
+  return __uint_as_float((e << 23) | ((hi & 0xfffffu) << 3) | (lo >> 29));
 }
-// 1 / d for a positive normal d: single-precision estimate, two Newton-Raphson
-// steps y <- y (2 - d y).
-__device__ __forceinline__ double rcp_nr(double d) {
+__device__ __forceinline__ double f64_of(float f) {
+  const unsigned b = __float_as_uint(f);
+  const unsigned e = ((b >> 23) & 0xffu) - 127u + 1023u;
+  return __hiloint2double((int)((e << 20) | ((b & 0x7fffffu) >> 3)), (int)((b & 7u) << 29));
+}
+
+// 1 / sqrt(x) for a positive x: a single-precision estimate y0 (relative
+// error below 2^-21) refined by one third-order step of the binomial series
+// (1 - e)^(-1/2) = 1 + e/2 + 3e^2/8 + O(e^3), e = 1 - x y0^2 (error below
+// 2^-60 before rounding).
+__device__ __forceinline__ double rsqrt64(double x) {
+  if (!(x > 1e-30 && x < 1e30)) return 1.0 / sqrt(x);
+  const double y = f64_of(rsqrtf(f32_estimate(x)));
+  const double e = fma(-(x * y), y, 1.0);
+  return fma(y, e * fma(0.375, e, 0.5), y);
+}
+// 1 / d for a positive d: single-precision estimate refined by one
+// third-order step of 1 / (1 - e) = 1 + e + e^2 + O(e^3), e = 1 - d y0.
+__device__ __forceinline__ double rcp64(double d) {
   if (!(d > 1e-30 && d < 1e30)) return 1.0 / d;
-  double y = (double)(1.0f / (float)d);
-  y = y * fma(-d, y, 2.0);
-  y = y * fma(-d, y, 2.0);
-  return y;
+  const double y = f64_of(__frcp_rn(f32_estimate(d)));
+  const double e = fma(-d, y, 1.0);
+  return fma(y, fma(e, e, e), y);
 }
 
 // Sum of 16 per-lane values over the warp, scattered: on return lane l holds
@@ -332,15 +346,27 @@ __device__ __forceinline__ double reduce_scatter16(double (&v)[16], int lane) {
   return a1 + __shfl_xor_sync(0xffffffffu, a1, 1);
 }
 
+// Sum of the first nlw of four per-warp partials p[0], p[stride], ...
+__device__ __forceinline__ double sum_live(const double* p, int stride, int nlw) {
+  if (nlw == 2) return p[0] + p[stride];
+  if (nlw == 3) return (p[0] + p[stride]) + p[2 * stride];
+  return (p[0] + p[stride]) + (p[2 * stride] + p[3 * stride]);
+}
+
 // Factors the panel of columns k..k+7 (bw of them are reflector columns) with
-// warps 0..3, lane = row k + 32 warp + lane.  Writes the panel back, V (rows
-// relative to k, zero above each reflector's first row) and Y = V T.
-__device__ void qrd_panel(const QrdLayout& L, int k, int bw, double* Are, double* Aim, double* Vre, double* Vim,
-                          double* Yre, double* Yim, double* red, double2* alpha, double* tau, int* sing, int warp,
-                          int lane) {
+// warps 0..3, lane = row k + 32 warp + lane.  Writes the panel back (R above
+// the diagonal, the reflectors' first entries on it and V below it) and
+// Y = V T into Yb.  Warps without rows in the panel (32 warp >= N8 - k) skip
+// every FP64 instruction; with one live warp the panel needs no shared-memory
+// exchange at all.
+__device__ void qrd_panel(const QrdLayout& L, int k, int bw, double* Are, double* Aim, double* Yb, double* red,
+                          double2* alpha, double* tau, int* sing, int warp, int lane) {
   const int S = L.S;
   const int rr = 32 * warp + lane, r = k + rr;
   const bool live = r < L.N8;
+  const int nlw = min(kPanelWarps, (L.N8 - k + 31) / 32);  // warps with rows in the panel
+  const bool wlive = warp < nlw;
+  if (nlw == 1 && !wlive) return;  // warp 0 factors the panel alone, without barriers
   double pr[8], pi[8], yr[8], yi[8];
 #pragma unroll
   for (int j = 0; j < 8; ++j) {
@@ -356,31 +382,38 @@ __device__ void qrd_panel(const QrdLayout& L, int k, int bw, double* Are, double
     if (j < bw) {
       const bool in_j = rr >= j;  // row in the support of v_j
       // ---- norm of the column's rows j.. and x0
-      double s = in_j ? fma(pr[j], pr[j], pi[j] * pi[j]) : 0.0;
-      s = wsum(s);
-      if (lane == 0) rn[warp] = s;
-      if (rr == j) {
-        rn[4] = pr[j];
-        rn[5] = pi[j];
-      }
-      panel_sync();
-      s = (rn[0] + rn[1]) + (rn[2] + rn[3]);
-      const double x0r = rn[4], x0i = rn[5];
-      double alr = 0.0, ali = 0.0, tj = 0.0;
-      if (s > 0.0) {
-        const double rs = rsqrt_nr(s);
-        const double sigma = s * rs;
-        const double q = fma(x0r, x0r, x0i * x0i);
-        double phr = 1.0, phi = 0.0, ax0 = 0.0;
-        if (q > 0.0) {
-          const double rq = rsqrt_nr(q);
-          ax0 = q * rq;
-          phr = x0r * rq;
-          phi = x0i * rq;
+      double s = 0.0, x0r, x0i;
+      if (wlive) s = wsum(in_j ? fma(pr[j], pr[j], pi[j] * pi[j]) : 0.0);
+      if (nlw == 1) {
+        x0r = __shfl_sync(0xffffffffu, pr[j], j);
+        x0i = __shfl_sync(0xffffffffu, pi[j], j);
+      } else {
+        if (lane == 0) rn[warp] = s;
+        if (rr == j) {
+          rn[4] = pr[j];
+          rn[5] = pi[j];
         }
-        alr = -phr * sigma;
-        ali = -phi * sigma;
-        tj = rcp_nr(sigma * (sigma + ax0));
+        panel_sync();
+        if (wlive) s = sum_live(rn, 1, nlw);
+        x0r = rn[4];
+        x0i = rn[5];
+      }
+      // ---- alpha_j = -e^{i arg x0} sigma, tau_j = 1 / (sigma (sigma + |x0|)),
+      // sigma = sqrt(s); with t = 1 / sqrt(s q), q = |x0|^2: sigma / |x0| = s t
+      // and |x0| / sigma = q t, so alpha = -x0 s t and tau = 1 / (s (1 + q t))
+      double alr = 0.0, ali = 0.0, tj = 0.0;
+      if (wlive && s > 0.0) {
+        const double q = fma(x0r, x0r, x0i * x0i);
+        if (q > 0.0) {
+          const double t = rsqrt64(s * q);
+          const double st = s * t;
+          alr = -(x0r * st);
+          ali = -(x0i * st);
+          tj = rcp64(s * fma(q, t, 1.0));
+        } else {
+          alr = -(s * rsqrt64(s));
+          tj = rcp64(s);
+        }
       }
       if (rr == j) {
         pr[j] = x0r - alr;
@@ -392,94 +425,98 @@ __device__ void qrd_panel(const QrdLayout& L, int k, int bw, double* Are, double
         if (!(s > 0.0)) *sing = 1;
       }
       // ---- slot m < j: z_m = v_m^H v_j; slot m >= j: w_{m+1} = v_j^H a_{m+1}
-      double v[16];
+      double tot = 0.0;
+      if (wlive) {
+        double v[16];
 #pragma unroll
-      for (int m = 0; m < 7; ++m) {
-        const int c = (m < j) ? m : m + 1;
-        double dr, di;
-        if (m < j) {  // conj(v_m) v_j
-          dr = fma(pr[c], pr[j], pi[c] * pi[j]);
-          di = fma(pr[c], pi[j], -pi[c] * pr[j]);
-        } else {  // conj(v_j) a_c
-          dr = fma(pr[j], pr[c], pi[j] * pi[c]);
-          di = fma(pr[j], pi[c], -pi[j] * pr[c]);
-        }
-        v[2 * m] = in_j ? dr : 0.0;
-        v[2 * m + 1] = in_j ? di : 0.0;
-      }
-      v[14] = 0.0;
-      v[15] = 0.0;
-      const double part = reduce_scatter16(v, lane);
-      if ((lane & 1) == 0) rd[warp * 16 + (lane >> 1)] = part;
-      panel_sync();
-      const int vi = (lane >> 1) & 15;
-      const double tot = (rd[vi] + rd[16 + vi]) + (rd[32 + vi] + rd[48 + vi]);
-      double t[14];
-#pragma unroll
-      for (int m = 0; m < 14; ++m) t[m] = __shfl_sync(0xffffffffu, tot, 2 * m);
-      // ---- Y_j = tau_j (v_j - sum_{l<j} Y_l z_l)
-      {
-        double ar = in_j ? pr[j] : 0.0, ai = in_j ? pi[j] : 0.0;
-#pragma unroll
-        for (int l = 0; l < 8; ++l) {
-          if (l < j) {
-            const double zr = t[2 * l], zi = t[2 * l + 1];
-            ar = fma(-yr[l], zr, fma(yi[l], zi, ar));
-            ai = fma(-yr[l], zi, fma(-yi[l], zr, ai));
+        for (int m = 0; m < 7; ++m) {
+          const int c = (m < j) ? m : m + 1;
+          double dr, di;
+          if (m < j) {  // conj(v_m) v_j
+            dr = fma(pr[c], pr[j], pi[c] * pi[j]);
+            di = fma(pr[c], pi[j], -pi[c] * pr[j]);
+          } else {  // conj(v_j) a_c
+            dr = fma(pr[j], pr[c], pi[j] * pi[c]);
+            di = fma(pr[j], pi[c], -pi[j] * pr[c]);
           }
+          v[2 * m] = in_j ? dr : 0.0;
+          v[2 * m + 1] = in_j ? di : 0.0;
         }
-        yr[j] = tj * ar;
-        yi[j] = tj * ai;
+        v[14] = 0.0;
+        v[15] = 0.0;
+        tot = reduce_scatter16(v, lane);
       }
-      // ---- apply H_j to the panel columns right of j: a_c -= (tau_j v_j) w_c
-      {
-        const double tvr = tj * pr[j], tvi = tj * pi[j];
+      if (nlw > 1) {
+        if ((lane & 1) == 0) rd[warp * 16 + (lane >> 1)] = tot;
+        panel_sync();
+        if (wlive) tot = sum_live(rd + ((lane >> 1) & 15), 16, nlw);
+      }
+      if (wlive) {
+        double t[14];
 #pragma unroll
-        for (int c = 0; c < 8; ++c) {
-          if (c > j && in_j) {
-            const double wr = t[2 * (c - 1)], wi = t[2 * (c - 1) + 1];
-            pr[c] = fma(-tvr, wr, fma(tvi, wi, pr[c]));
-            pi[c] = fma(-tvr, wi, fma(-tvi, wr, pi[c]));
+        for (int m = 0; m < 14; ++m) t[m] = __shfl_sync(0xffffffffu, tot, 2 * m);
+        // ---- Y_j = tau_j (v_j - sum_{l<j} Y_l z_l)
+        {
+          double ar = in_j ? pr[j] : 0.0, ai = in_j ? pi[j] : 0.0;
+#pragma unroll
+          for (int l = 0; l < 8; ++l) {
+            if (l < j) {
+              const double zr = t[2 * l], zi = t[2 * l + 1];
+              ar = fma(-yr[l], zr, fma(yi[l], zi, ar));
+              ai = fma(-yr[l], zi, fma(-yi[l], zr, ai));
+            }
+          }
+          yr[j] = tj * ar;
+          yi[j] = tj * ai;
+        }
+        // ---- apply H_j to the panel columns right of j: a_c -= (tau_j v_j) w_c
+        {
+          const double tvr = tj * pr[j], tvi = tj * pi[j];
+#pragma unroll
+          for (int c = 0; c < 8; ++c) {
+            if (c > j && in_j) {
+              const double wr = t[2 * (c - 1)], wi = t[2 * (c - 1) + 1];
+              pr[c] = fma(-tvr, wr, fma(tvi, wi, pr[c]));
+              pi[c] = fma(-tvr, wi, fma(-tvi, wr, pi[c]));
+            }
           }
         }
       }
     }
   }
   if (live) {
+    double* Yre = Yb;
+    double* Yim = Yb + 8 * S;
 #pragma unroll
     for (int j = 0; j < 8; ++j) {
       Are[(size_t)(k + j) * S + r] = pr[j];
       Aim[(size_t)(k + j) * S + r] = pi[j];
-      const bool in_v = (j < bw) && rr >= j;
-      Vre[j * S + rr] = in_v ? pr[j] : 0.0;
-      Vim[j * S + rr] = in_v ? pi[j] : 0.0;
       Yre[j * S + rr] = (j < bw) ? yr[j] : 0.0;
       Yim[j * S + rr] = (j < bw) ? yi[j] : 0.0;
     }
   }
 }
 
-// One warp: columns c0..c0+7 of rows k..N8-1 updated by the panel's block
-// reflector, A_t <- A_t - V (Y^H A_t).  Each complex product takes three real
-// MMAs instead of four (Gauss): for W = Y^H A_t, with A1 = Yr^T Ar,
-// A2 = Yi^T Ai and A3 = (Yr - Yi)^T (Ar + Ai), Re W = A1 + A2 and
-// Im W = A3 - A1 + A2; for V W, with T1 = Vr Wr, T2 = Vi Wi and
-// T3 = (Vr + Vi)(Wr + Wi), Re = T1 - T2 and Im = T3 - T1 - T2.  An MMA holds
-// the FP64 unit about eight times as long as the FP64 addition that forms an
-// operand sum, so the trade saves FP64 time.
-__device__ void qrd_w(const QrdLayout& L, int k, int c0, const double* Are, const double* Aim, const double* Yre,
-                      const double* Yim, double* tre, double* tim, int lane) {
+// One warp: W = Y^H A_t for the tile of columns c0..c0+7 over rows k..N8-1,
+// summed over the 8-row blocks blk0, blk0 + bstep, ... (bstep > 1 leaves a
+// partial sum).  Each complex product takes three real MMAs instead of four
+// (Gauss): with A1 = Yr^T Ar, A2 = Yi^T Ai and A3 = (Yr - Yi)^T (Ar + Ai),
+// Re W = A1 + A2 and Im W = A3 - A1 + A2.  An MMA holds the FP64 unit about
+// eight times as long as the FP64 addition that forms an operand sum, so the
+// trade saves FP64 time.
+__device__ void qrd_w(const QrdLayout& L, int k, int c0, const double* Are, const double* Aim, const double* Yb,
+                      double* tile, int blk0, int bstep, int lane) {
   const int S = L.S, g = lane >> 2, q = lane & 3;
   const int R8 = L.N8 - k;
-  // A operand (Y^H)[i][rr] -> Y[rr][i], B operand A_t[rr][c]; even and odd
-  // k-steps accumulate separately (six independent chains)
+  // A operand (Y^H)[i][rr] -> Y[rr][i], B operand A_t[rr][c]; the two halves
+  // of each block accumulate separately (six independent chains)
   double p10 = 0.0, p11 = 0.0, p20 = 0.0, p21 = 0.0, p30 = 0.0, p31 = 0.0;
   double q10 = 0.0, q11 = 0.0, q20 = 0.0, q21 = 0.0, q30 = 0.0, q31 = 0.0;
   const double* bre = Are + (size_t)(c0 + g) * S + k;
   const double* bim = Aim + (size_t)(c0 + g) * S + k;
-  const double* yre = Yre + g * S;
-  const double* yim = Yim + g * S;
-  for (int ks = 0; ks + 8 <= R8; ks += 8) {
+  const double* yre = Yb + g * S;
+  const double* yim = Yb + 8 * S + g * S;
+  for (int ks = 8 * blk0; ks + 8 <= R8; ks += 8 * bstep) {
     {
       const double vr = yre[ks + q], vi = yim[ks + q], xr = bre[ks + q], xi = bim[ks + q];
       dmma(p10, p11, vr, xr);
@@ -494,6 +531,8 @@ __device__ void qrd_w(const QrdLayout& L, int k, int c0, const double* Are, cons
     }
   }
   {
+    double* tre = tile;
+    double* tim = tile + 8 * kTileStride;
     const double a10 = p10 + q10, a11 = p11 + q11, a20 = p20 + q20, a21 = p21 + q21;
     const double a30 = p30 + q30, a31 = p31 + q31;
     tre[(2 * q) * kTileStride + g] = a10 + a20;
@@ -504,11 +543,16 @@ __device__ void qrd_w(const QrdLayout& L, int k, int c0, const double* Are, cons
 }
 
 // A_t -= V W for rows k + m0 .. k + m0 + 15 of the tile at column c0 (W from
-// qrd_w in tre / tim).
-__device__ void qrd_update(const QrdLayout& L, int k, int c0, int m0, double* Are, double* Aim, const double* Vre,
-                           const double* Vim, const double* tre, const double* tim, int lane) {
+// qrd_w in tile).  V is read from the panel's columns of A: entry (row rr,
+// reflector i) is A[k + rr][k + i] for rr >= i and zero above (the updates
+// only ever follow full panels of 8 reflectors).  For V W, with T1 = Vr Wr,
+// T2 = Vi Wi and T3 = (Vr + Vi)(Wr + Wi): Re = T1 - T2, Im = T3 - T1 - T2.
+__device__ void qrd_update(const QrdLayout& L, int k, int c0, int m0, double* Are, double* Aim, const double* tile,
+                           int lane) {
   const int S = L.S, g = lane >> 2, q = lane & 3;
   const int R8 = L.N8 - k;
+  const double* tre = tile;
+  const double* tim = tile + 8 * kTileStride;
   // A operand V[r][i], B operand W[i][n]; two row tiles of 8
   const double w0r = tre[g * kTileStride + q], w0i = tim[g * kTileStride + q];
   const double w1r = tre[g * kTileStride + 4 + q], w1i = tim[g * kTileStride + 4 + q];
@@ -529,12 +573,15 @@ __device__ void qrd_update(const QrdLayout& L, int k, int c0, int m0, double* Ar
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
       const double wr = h ? w1r : w0r, wi = h ? w1i : w0i, ws = h ? w1s : w0s;
-      const double vr = Vre[(4 * h + q) * S + m0 + g], vi = Vim[(4 * h + q) * S + m0 + g];
+      const int i = 4 * h + q;
+      const size_t vo = (size_t)(k + i) * S + k + m0 + g;
+      const bool up = m0 + g >= i;  // below or on the diagonal of reflector i
+      const double vr = up ? Are[vo] : 0.0, vi = up ? Aim[vo] : 0.0;
       dmma(t10, t11, vr, wr);
       dmma(t20, t21, vi, wi);
       dmma(ci0, ci1, ineg(vr + vi), ws);
       if (two) {
-        const double ur = Vre[(4 * h + q) * S + m0 + 8 + g], ui = Vim[(4 * h + q) * S + m0 + 8 + g];
+        const double ur = Are[vo + 8], ui = Aim[vo + 8];  // rows m0 + 8.. are all below the panel's diagonal
         dmma(u10, u11, ur, wr);
         dmma(u20, u21, ui, wi);
         dmma(di0, di1, ineg(ur + ui), ws);
@@ -554,26 +601,34 @@ __device__ void qrd_update(const QrdLayout& L, int k, int c0, int m0, double* Ar
   }
 }
 
-
-// Factorises one [H | y] with the calling CTA (4 or 8 warps; warps 0..3 factor
-// the panels, all of them update the trailing columns).
+// Factorises one [H | y] with the calling CTA.
+//
+// Four warps (two CTAs per SM, one matrix's panel overlapping the other's
+// update): panel k, then W and A -= V W for every tile right of it, with
+// barriers between.
+//
+// Eight warps (one matrix per SM): the schedule looks one panel ahead.
+// While warps 4..7 apply panel k to the columns k+16.. (W for their tiles, a
+// barrier of their own, then A -= V W in units of (tile, 16 rows)), warps
+// 0..3 apply it to the next panel's columns k+8..k+15 alone (W split over the
+// four warps by 8-row blocks and summed, then A -= V W) and factor panel k+8
+// into the other Y buffer.  The FP64 units are shared by a panel warp and an
+// update warp on each scheduler, so the panel's latency gaps fill with MMAs.
 __device__ void qr_dmma_one(int N, int M, const double2* __restrict__ Hb, const double2* __restrict__ yb,
                             const QrDst& out) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   QrdLayout L;
-  L.init(N, M, (int)(blockDim.x >> 5));
+  L.init(N, M);
   double* Are = reinterpret_cast<double*>(smem_raw + L.off_are);
   double* Aim = reinterpret_cast<double*>(smem_raw + L.off_aim);
-  double* Vre = reinterpret_cast<double*>(smem_raw + L.off_vre);
-  double* Vim = reinterpret_cast<double*>(smem_raw + L.off_vim);
-  double* Yre = reinterpret_cast<double*>(smem_raw + L.off_yre);
-  double* Yim = reinterpret_cast<double*>(smem_raw + L.off_yim);
+  double* const Y0 = reinterpret_cast<double*>(smem_raw + L.off_y[0]);
+  double* const Y1 = reinterpret_cast<double*>(smem_raw + L.off_y[1]);
   double* red = reinterpret_cast<double*>(smem_raw + L.off_red);
   double2* alpha = reinterpret_cast<double2*>(smem_raw + L.off_alpha);
   double* tau = reinterpret_cast<double*>(smem_raw + L.off_tau);
   int* sing = reinterpret_cast<int*>(smem_raw + L.off_sing);
-  const int tid = threadIdx.x, nthr = blockDim.x, lane = tid & 31, warp = tid >> 5;
   double* tiles = reinterpret_cast<double*>(smem_raw + L.off_tile);
+  const int tid = threadIdx.x, nthr = blockDim.x, lane = tid & 31, warp = tid >> 5, nw = nthr >> 5;
 
   const int plane = L.C8 * L.S;
   for (int t = tid; t < plane; t += nthr) {
@@ -594,25 +649,59 @@ __device__ void qr_dmma_one(int N, int M, const double2* __restrict__ Hb, const 
     Aim[(size_t)M * L.S + r] = v.y;
   }
   __syncthreads();
-  for (int k = 0; k < M; k += 8) {
-    const int bw = min(8, M - k);
-    if (warp < kPanelWarps) qrd_panel(L, k, bw, Are, Aim, Vre, Vim, Yre, Yim, red, alpha, tau, sing, warp, lane);
-    __syncthreads();
-    // W_t = Y^H A_t for every tile of 8 columns (k+8 .. M), then A_t -= V W_t
-    // in units of (tile, 16 rows) spread over all warps (a panel's tile count
-    // is rarely a multiple of the four schedulers)
-    const int ntiles = (M + 1 - (k + 8) + 7) / 8;
-    const int nw = nthr / 32, nrb = (L.N8 - k + 15) / 16;
-    for (int t = warp; t < ntiles; t += nw)
-      qrd_w(L, k, k + 8 + 8 * t, Are, Aim, Yre, Yim, tiles + (size_t)t * 2 * 8 * kTileStride,
-            tiles + (size_t)t * 2 * 8 * kTileStride + 8 * kTileStride, lane);
-    __syncthreads();
-    for (int u = warp; u < ntiles * nrb; u += nw) {
-      const int t = u / nrb, rb = u - t * nrb;
-      const double* tw = tiles + (size_t)t * 2 * 8 * kTileStride;
-      qrd_update(L, k, k + 8 + 8 * t, 16 * rb, Are, Aim, Vre, Vim, tw, tw + 8 * kTileStride, lane);
+  if (nw == kPanelWarps) {
+    for (int k = 0; k < M; k += 8) {
+      qrd_panel(L, k, min(8, M - k), Are, Aim, Y0, red, alpha, tau, sing, warp, lane);
+      __syncthreads();
+      // W_t = Y^H A_t for every tile of 8 columns (k+8 .. M), then A_t -= V W_t
+      // in units of (tile, 16 rows)
+      const int ntiles = (M + 1 - (k + 8) + 7) / 8;
+      const int nrb = (L.N8 - k + 15) / 16;
+      for (int t = warp; t < ntiles; t += nw)
+        qrd_w(L, k, k + 8 + 8 * t, Are, Aim, Y0, tiles + (size_t)t * kTileDoubles, 0, 1, lane);
+      __syncthreads();
+      for (int u = warp; u < ntiles * nrb; u += nw) {
+        const int t = u / nrb, rb = u - t * nrb;
+        qrd_update(L, k, k + 8 + 8 * t, 16 * rb, Are, Aim, tiles + (size_t)t * kTileDoubles, lane);
+      }
+      __syncthreads();
     }
+  } else {
+    if (warp < kPanelWarps) qrd_panel(L, 0, min(8, M), Are, Aim, Y0, red, alpha, tau, sing, warp, lane);
     __syncthreads();
+    // tiles right of panel k exist while k + 8 <= M (column M is y); panel k is then full
+    for (int k = 0, b = 0; k + 8 <= M; k += 8, b ^= 1) {
+      const int kn = k + 8;
+      const int ntiles = (M + 1 - kn + 7) / 8;  // tile 0 holds the next panel's columns
+      const int nrb = (L.N8 - k + 15) / 16;
+      const double* Yc = b ? Y1 : Y0;
+      double* const Yn = b ? Y0 : Y1;
+      if (warp < kPanelWarps) {
+        // the next panel's Y buffer holds the four partial W until that panel writes it
+        double* part = Yn;
+        qrd_w(L, k, kn, Are, Aim, Yc, part + warp * kTileDoubles, warp, kPanelWarps, lane);
+        panel_sync();
+        {
+          const int e = tid;  // 0..127: entry (plane, column, row) of the 2 x 8 x 8 tile
+          const int at = (e >> 6) * 8 * kTileStride + ((e >> 3) & 7) * kTileStride + (e & 7);
+          tiles[at] = (part[at] + part[kTileDoubles + at]) + (part[2 * kTileDoubles + at] + part[3 * kTileDoubles + at]);
+        }
+        panel_sync();
+        for (int rb = warp; rb < nrb; rb += kPanelWarps) qrd_update(L, k, kn, 16 * rb, Are, Aim, tiles, lane);
+        panel_sync();
+        if (kn < M) qrd_panel(L, kn, min(8, M - kn), Are, Aim, Yn, red, alpha, tau, sing, warp, lane);
+      } else {
+        const int uw = warp - kPanelWarps, un = nw - kPanelWarps;
+        for (int t = 1 + uw; t < ntiles; t += un)
+          qrd_w(L, k, kn + 8 * t, Are, Aim, Yc, tiles + (size_t)t * kTileDoubles, 0, 1, lane);
+        update_sync(un * 32);
+        for (int u = uw; u < (ntiles - 1) * nrb; u += un) {
+          const int t = 1 + u / nrb, rb = u - (t - 1) * nrb;
+          qrd_update(L, k, kn + 8 * t, 16 * rb, Are, Aim, tiles + (size_t)t * kTileDoubles, lane);
+        }
+      }
+      __syncthreads();
+    }
   }
   qr_writeout(M, [&](int c, int r) { return make_double2(Are[(size_t)c * L.S + r], Aim[(size_t)c * L.S + r]); },
               alpha, tau, out);
@@ -770,20 +859,20 @@ __device__ void qr_small_pair(int N, int M, bool act, const double2* __restrict_
       double sigma = 0.0, tj = 0.0;
       double2 phr = make_double2(1.0, 0.0), al = make_double2(0.0, 0.0);
       if (s > 0.0) {
-        const double rs = rsqrt_nr(s);
+        const double rs = rsqrt64(s);
         sigma = s * rs;
         const double qq = fma(x0.x, x0.x, x0.y * x0.y);
         double ax0 = 0.0;
         double2 p0 = make_double2(1.0, 0.0);
         if (qq > 0.0) {
-          const double rq = rsqrt_nr(qq);
+          const double rq = rsqrt64(qq);
           ax0 = qq * rq;
           p0 = make_double2(x0.x * rq, x0.y * rq);
         }
         // alpha = -e^{i arg x0} sigma keeps v_j = x0 - alpha free of cancellation
         al = make_double2(-p0.x * sigma, -p0.y * sigma);
         phr = make_double2(-p0.x, -p0.y);
-        tj = rcp_nr(sigma * (sigma + ax0));
+        tj = rcp64(sigma * (sigma + ax0));
       } else {
         sing = 1;
       }
@@ -879,18 +968,21 @@ __global__ void __launch_bounds__(32) qr_small_gather_kernel(int count, const in
 #define MDX_QRD_MIN_TX 48
 #endif
 constexpr int kQrdMinTx = MDX_QRD_MIN_TX;
-size_t qrd_smem(int n_rx, int n_tx, int warps) {
+size_t qrd_smem(int n_rx, int n_tx) {
   QrdLayout L;
-  L.init(n_rx, n_tx, warps);
+  L.init(n_rx, n_tx);
   return L.bytes;
 }
+// The look-ahead keeps four partial W tiles in a free Y buffer of 16 S
+// doubles, S = round_up(n_rx, 8) + 4 >= n_tx + 4.
+static_assert(16 * (kQrdMinTx + 4) >= 4 * kTileDoubles, "Y buffer too small for the partial W tiles");
 bool use_qrd(int n_rx, int n_tx) {
-  return n_tx >= kQrdMinTx && n_rx <= 128 && qrd_smem(n_rx, n_tx, kQrdWarps) <= 227 * 1024;
+  return n_tx >= kQrdMinTx && n_rx <= 128 && qrd_smem(n_rx, n_tx) <= 227 * 1024;
 }
 // Four warps per CTA when two such CTAs fit in one SM's shared memory: one
 // matrix's panel then overlaps the other's trailing update.
 int qrd_warps(int n_rx, int n_tx) {
-  return 2 * qrd_smem(n_rx, n_tx, kPanelWarps) <= 227 * 1024 ? kPanelWarps : kQrdWarps;
+  return 2 * qrd_smem(n_rx, n_tx) <= 227 * 1024 ? kPanelWarps : kQrdWarps;
 }
 
 template <int LPC>
@@ -936,7 +1028,7 @@ cudaError_t launch_qr_gather(int count, int n_rx, int n_tx, const int* ids, cons
   if (count <= 0) return cudaSuccess;
   if (use_qrd(n_rx, n_tx)) {
     const int wq = qrd_warps(n_rx, n_tx);
-    const size_t sm = qrd_smem(n_rx, n_tx, wq);
+    const size_t sm = qrd_smem(n_rx, n_tx);
     if (wq == kPanelWarps) {
       cudaFuncSetAttribute(qr_dmma_gather_kernel<kPanelWarps>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
       qr_dmma_gather_kernel<kPanelWarps><<<count, wq * 32, sm, s>>>(count, ids, reqs, H, y, out);
@@ -971,7 +1063,7 @@ cudaError_t launch_qr(int batch, int n_rx, int n_tx, const double* H, const doub
   if (batch <= 0) return cudaSuccess;
   if (use_qrd(n_rx, n_tx)) {
     const int wq = qrd_warps(n_rx, n_tx);
-    const size_t sm = qrd_smem(n_rx, n_tx, wq);
+    const size_t sm = qrd_smem(n_rx, n_tx);
     if (wq == kPanelWarps) {
       cudaFuncSetAttribute(qr_dmma_kernel<kPanelWarps>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
       qr_dmma_kernel<kPanelWarps><<<batch, wq * 32, sm, s>>>(batch, n_rx, n_tx, H, y, out);
