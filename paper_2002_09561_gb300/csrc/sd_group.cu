@@ -78,15 +78,23 @@ __host__ __device__ constexpr int group_warps() {
 }
 constexpr int kTri = 528;       // column-packed triangle of n = 32
 
+// R and the residual stack in shared memory: column c (rows 0..c) starts at
+// zoff(c) = kTri - (c + 1)(c + 2) / 2, the columns in descending order.  A
+// lane may then write a whole column, rows past its end included: those land
+// in deeper columns (or the padding after column 0), which are rewritten
+// before they are read, so the node step stores every row without a test.
+__host__ __device__ constexpr int zoff(int c) { return kTri - (((c + 1) * (c + 2)) >> 1); }
+
 // Shared memory of one warp, in 4-byte words.  The NG = 32 / G groups of the
 // warp are interleaved element by element (element e of group g at e NG + g),
 // so that the G lanes of every group read consecutive elements at a stride of
 // NG words: the groups of a warp always touch disjoint banks, whichever level
 // each of their trees is at.
-//   R       kTri x NG floats   FP32 R, column-packed
-//   Z       kTri x NG floats   residual stack (level i: rows 0..i at col_off(i))
-//   ST      32 x NG float4     level state {parent partial distance, c_i, u_i, R_ii}
-//   CUR     32 x NG float2     zig-zag cursors {lo, hi}
+//   R       kTri x NG floats          FP32 R, columns at zoff(c)
+//   Z       (kTri + 32) x NG floats   residual stack (level i: rows 0..i at zoff(i)), padded
+//                                     for the rows written past column 0
+//   ST      32 x NG float4     level state {parent partial distance, c_i, cursor lo, cursor hi}
+//                              (u_i = c_i / (2 alpha R_ii) + (P - 1) / 2 and R_ii come from LR)
 //   LR      32 x NG float2     {R_ii, 1 / (2 alpha R_ii)}
 //   XS      32 x NG bytes      current path
 //   per group: kCand candidate partial distances and kCand x 32 path bytes
@@ -95,14 +103,13 @@ struct WarpLayout {
   static constexpr int NG = 32 / G;
   static constexpr int R = 0;
   static constexpr int Z = R + kTri * NG;
-  static constexpr int ST = Z + kTri * NG;
-  static constexpr int CUR = ST + 4 * kGroupN * NG;
-  static constexpr int LR = CUR + 2 * kGroupN * NG;
+  static constexpr int ST = Z + (kTri + kGroupN) * NG;
+  static constexpr int LR = ST + 4 * kGroupN * NG;
   static constexpr int XS = LR + 2 * kGroupN * NG;
   static constexpr int CAND = XS + kGroupN * NG / 4;
   static constexpr int CAND_WORDS = kCand + kCand * kGroupN / 4;  // per group
   static constexpr int WORDS = CAND + NG * CAND_WORDS;
-  static_assert(ST % 4 == 0 && CUR % 2 == 0 && LR % 2 == 0, "16- and 8-byte alignment of the level arrays");
+  static_assert(ST % 4 == 0 && LR % 2 == 0, "16- and 8-byte alignment of the level arrays");
 };
 
 template <int G>
@@ -145,7 +152,9 @@ __device__ __forceinline__ double rescore_fp64_group(int n, const double* lev64,
 #define MDX_SDG_MIN_BLOCKS 5
 #endif
 
-template <int G>
+// kBudget: the launch has a node budget (tested on every descent; without one
+// the node step carries no budget test)
+template <int G, bool kBudget>
 __global__ void __launch_bounds__(group_warps<G>() * 32, MDX_SDG_MIN_BLOCKS) sd_group_kernel(SdArgs g) {
   constexpr int NG = 32 / G;        // groups per warp
   constexpr int RPL = kGroupN / G;  // rows per lane
@@ -170,7 +179,6 @@ __global__ void __launch_bounds__(group_warps<G>() * 32, MDX_SDG_MIN_BLOCKS) sd_
   float* Rw = wbase + L::R;
   float* Zw = wbase + L::Z;
   float4* STw = reinterpret_cast<float4*>(wbase + L::ST);
-  float2* CURw = reinterpret_cast<float2*>(wbase + L::CUR);
   float2* LRw = reinterpret_cast<float2*>(wbase + L::LR);
   uint8_t* XSw = reinterpret_cast<uint8_t*>(wbase + L::XS);
   float* cped = wbase + L::CAND + gid * L::CAND_WORDS;
@@ -178,7 +186,6 @@ __global__ void __launch_bounds__(group_warps<G>() * 32, MDX_SDG_MIN_BLOCKS) sd_
 #define RW(e) Rw[(e) * NG + gid]
 #define ZW(e) Zw[(e) * NG + gid]
 #define ST(l) STw[(l) * NG + gid]
-#define CUR(l) CURw[(l) * NG + gid]
 #define LR(l) LRw[(l) * NG + gid]
 #define XS(j) XSw[(j) * NG + gid]
 
@@ -195,7 +202,8 @@ __global__ void __launch_bounds__(group_warps<G>() * 32, MDX_SDG_MIN_BLOCKS) sd_
   bool solo = false;
   int ncl = 0;  // leaf candidates of the running task
   long long nodes = 0, peds = 0, flops = 0, committed = 0;
-  int n32 = 0, p32 = 0, lsum = 0, task_nodes = 0, left32 = 0x7fffffff;
+  int n32 = 0, p32 = 0, lsum = 0, left32 = 0x7fffffff;
+  int task_nodes = 0;  // nodes of the running task up to the last periodic check
   int restarts = 0;           // radius doublings so far (solo)
   float r2_start = INFINITY;  // radius of the current pass (solo)
   bool budget_hit = false;
@@ -204,13 +212,13 @@ __global__ void __launch_bounds__(group_warps<G>() * 32, MDX_SDG_MIN_BLOCKS) sd_
   bool recheck = true;  // idle groups try the queue again
   bool ev_leaf = false, ev_done = false;
   float leaf_ped = 0.0f;
-  int leaf_k = 0;
+  float leaf_kf = 0.0f;
 
   // the level a group enters (task node, root restart): cursors from u
   auto enter_level = [&](int lvl, float pp) {
     i = lvl;
     ped_par = pp;
-    c = ZW(col_off(lvl) + lvl);
+    c = ZW(zoff(lvl) + lvl);
     const float2 rl = LR(lvl);
     rii = rl.x;
     u = fmaf(c, rl.y, uoff);
@@ -225,7 +233,7 @@ __global__ void __launch_bounds__(group_warps<G>() * 32, MDX_SDG_MIN_BLOCKS) sd_
       // --------------------------------------------------------- a leaf
       if (__any_sync(full, ev_leaf)) {
         if (ev_leaf) {
-          XS(0) = (uint8_t)leaf_k;
+          XS(0) = (uint8_t)(int)leaf_kf;
           int slot = -1;
           if (ncl < kCand) {
             slot = ncl++;
@@ -367,7 +375,7 @@ __global__ void __launch_bounds__(group_warps<G>() * 32, MDX_SDG_MIN_BLOCKS) sd_
         if (restart) {
           // the root's residuals (no rows fixed) are ybar itself
           const float* yb = a.yb32 + (size_t)v * vec_stride32(n);
-          for (int r = gl; r < n; r += G) ZW(col_off(n - 1) + r) = yb[r];
+          for (int r = gl; r < n; r += G) ZW(zoff(n - 1) + r) = yb[r];
         }
         __syncwarp();
         if (restart) {
@@ -532,12 +540,13 @@ __global__ void __launch_bounds__(group_warps<G>() * 32, MDX_SDG_MIN_BLOCKS) sd_
         const bool stage = got != 0 && staged != tv;
         if (stage) {
           const float* src = a.R32 + (size_t)tv * ts;
-          for (int e = gl; e < tri(n); e += G) RW(e) = src[e];
+          for (int cc = 0; cc < n; ++cc)
+            for (int r = gl; r <= cc; r += G) RW(zoff(cc) + r) = src[col_off(cc) + r];
         }
         __syncwarp();
         if (stage) {
           for (int r = gl; r < n; r += G) {
-            const float rr = RW(col_off(r) + r);
+            const float rr = RW(zoff(r) + r);
             LR(r) = make_float2(rr, 0.5f / (alpha * rr));
           }
           staged = tv;
@@ -553,7 +562,7 @@ __global__ void __launch_bounds__(group_warps<G>() * 32, MDX_SDG_MIN_BLOCKS) sd_
             float e2 = 0.0f;
             for (int r = gl; r < n; r += G) {
               float T = fabsf(yb[r]);
-              for (int j = r; j < n; ++j) T += amax * fabsf(RW(col_off(j) + r));
+              for (int j = r; j < n; ++j) T += amax * fabsf(RW(zoff(j) + r));
               const float w = (float)(n - r + 1) * T;
               e2 += w * w;
             }
@@ -611,8 +620,8 @@ __global__ void __launch_bounds__(group_warps<G>() * 32, MDX_SDG_MIN_BLOCKS) sd_
             if (r <= top) {
               float z = yb[r];
               for (int j = n - 1; j > top; --j)
-                z = fmaf(-RW(col_off(j) + r), (float)(2 * (int)XS(j) - (P - 1)) * alpha, z);
-              ZW(col_off(top) + r) = z;
+                z = fmaf(-RW(zoff(j) + r), (float)(2 * (int)XS(j) - (P - 1)) * alpha, z);
+              ZW(zoff(top) + r) = z;
             }
           }
         }
@@ -698,8 +707,11 @@ __global__ void __launch_bounds__(group_warps<G>() * 32, MDX_SDG_MIN_BLOCKS) sd_
     // outcomes and stall on its resolution every pass).
     {
       const bool busy = mode == 1;
-      const int ip = min(i + 1, n - 1), im = max(i - 1, 0);
-      const int ci = col_off(i);
+      // ip = n (the root) and im = -1 (a leaf) index past the level arrays
+      // into their neighbours in shared memory; those values are never used
+      // (no pop at the task's top level, no descent from level 0)
+      const int ip = i + 1, im = i - 1;
+      const int ci = zoff(i), cm = ci + i + 1;  // zoff(i - 1)
       float rcv[RPL], zinv[RPL];
 #pragma unroll
       for (int t = 0; t < RPL; ++t) {
@@ -707,7 +719,7 @@ __global__ void __launch_bounds__(group_warps<G>() * 32, MDX_SDG_MIN_BLOCKS) sd_
         zinv[t] = ZW(ci + gl + G * t);
       }
       const float4 stp = ST(ip);
-      const float2 curp = CUR(ip);
+      const float2 lrp = LR(ip);
       const float2 lrn = LR(im);
       const bool has_lo = flo >= 0.0f, has_hi = fhi < Pf;
       const bool has = busy && (has_lo || has_hi);
@@ -718,29 +730,35 @@ __global__ void __launch_bounds__(group_warps<G>() * 32, MDX_SDG_MIN_BLOCKS) sd_
       const float av = fmaf(kf, 2.0f, -(Pf - 1.0f)) * alpha;  // (2k - (P - 1)) alpha
       const float d = fmaf(-rii, av, c);
       const float ped = fmaf(d, d, ped_par);
-      p32 += has ? 1 : 0;
+      if (has) ++p32;
       const bool ok = has && ped < bnd;
       const bool deep = ok && i > 0;
-      const bool desc = deep && n32 < left32;
-      const bool bstop = deep && n32 >= left32;
-      budget_hit = budget_hit || bstop;
+      bool desc = deep, bstop = false;
+      if (kBudget) {
+        desc = deep && n32 < left32;
+        bstop = deep && n32 >= left32;
+        budget_hit = budget_hit || bstop;
+      }
       ev_done = busy && ((!ok && i == top) || bstop);
       ev_leaf = ok && i == 0;
       leaf_ped = ped;
-      leaf_k = (int)kf;
+      leaf_kf = kf;
       const bool pop = busy && !ok && i != top;
-      float cn = 0.0f;
-      const int cm = col_off(im);
+      // the new level's residuals (rows 0..i-1 matter; the rest spill into
+      // deeper columns), and row i - 1's, held by lane (i - 1) mod G at
+      // t = (i - 1) / G, for the next level's interference
+      float zn[RPL];
 #pragma unroll
       for (int t = 0; t < RPL; ++t) {
-        const int r = gl + G * t;
-        const float z = fmaf(-rcv[t], av, zinv[t]);
-        if (desc && r < i) ZW(cm + r) = z;
-        cn = (r == i - 1) ? z : cn;
+        zn[t] = fmaf(-rcv[t], av, zinv[t]);
+        if (desc) ZW(cm + gl + G * t) = zn[t];
       }
+      const int tsel = (i - 1) / G;
+      float cn = zn[0];
+#pragma unroll
+      for (int t = 1; t < RPL; ++t) cn = (tsel == t) ? zn[t] : cn;
       if (desc) {
-        ST(i) = make_float4(ped_par, c, u, rii);
-        CUR(i) = make_float2(flo, fhi);
+        ST(i) = make_float4(ped_par, c, flo, fhi);
         XS(i) = (uint8_t)(int)kf;
       }
       const float cnew = __shfl_sync(full, cn, lead + ((i - 1) & (G - 1)));
@@ -749,13 +767,15 @@ __global__ void __launch_bounds__(group_warps<G>() * 32, MDX_SDG_MIN_BLOCKS) sd_
       i = desc ? im : (pop ? ip : i);
       ped_par = desc ? ped : (pop ? stp.x : ped_par);
       c = desc ? cnew : (pop ? stp.y : c);
-      u = desc ? unew : (pop ? stp.z : u);
-      rii = desc ? lrn.x : (pop ? stp.w : rii);
-      flo = desc ? flonew : (pop ? curp.x : flo);
-      fhi = desc ? flonew + 1.0f : (pop ? curp.y : fhi);
-      n32 += desc ? 1 : 0;
-      lsum += desc ? im : 0;
-      task_nodes += desc ? 1 : 0;
+      // the parent's u is recomputed exactly as it was formed on the way down
+      u = desc ? unew : (pop ? fmaf(stp.y, lrp.y, uoff) : u);
+      rii = desc ? lrn.x : (pop ? lrp.x : rii);
+      flo = desc ? flonew : (pop ? stp.z : flo);
+      fhi = desc ? flonew + 1.0f : (pop ? stp.w : fhi);
+      if (desc) {
+        ++n32;
+        lsum += im;
+      }
     }
 
     // ===================================================== periodic check
@@ -765,6 +785,7 @@ __global__ void __launch_bounds__(group_warps<G>() * 32, MDX_SDG_MIN_BLOCKS) sd_
       const bool busy = mode == 1 && !ev_done;
       SdVec* vs = busy ? vec_of(g, v) : nullptr;
       if (busy) {
+        task_nodes += n32;
         nodes += n32;
         peds += p32;
         flops += (long long)n32 * node_flops0 - 2ll * lsum;
@@ -778,7 +799,7 @@ __global__ void __launch_bounds__(group_warps<G>() * 32, MDX_SDG_MIN_BLOCKS) sd_
             bnd = prune_bound(r2, E, n);
           }
         }
-        if (a.budget > 0) {
+        if (kBudget) {
           unsigned long long tot = 0;
           int bh = 0;
           if (gl == 0) {
@@ -834,13 +855,13 @@ __global__ void __launch_bounds__(group_warps<G>() * 32, MDX_SDG_MIN_BLOCKS) sd_
               lrii = rii;
             } else {
               const float4 st = ST(l);
-              const float2 cu = CUR(l);
-              llo = cu.x;
-              lhi = cu.y;
+              const float2 lr = LR(l);
+              llo = st.z;
+              lhi = st.w;
               lped = st.x;
               lc = st.y;
-              lu = st.z;
-              lrii = st.w;
+              lu = fmaf(lc, lr.y, uoff);
+              lrii = lr.x;
             }
             if (llo < 0.0f && lhi >= Pf) continue;
             // children inside the sphere, in Schnorr-Euchner order: counted first, then written
@@ -915,7 +936,8 @@ __global__ void __launch_bounds__(group_warps<G>() * 32, MDX_SDG_MIN_BLOCKS) sd_
               flo = -1.0f;
               fhi = Pf;
             } else {
-              CUR(l) = make_float2(-1.0f, Pf);
+              ST(l).z = -1.0f;
+              ST(l).w = Pf;
             }
           }
           if (gl == 0) {
@@ -932,20 +954,20 @@ __global__ void __launch_bounds__(group_warps<G>() * 32, MDX_SDG_MIN_BLOCKS) sd_
 #undef RW
 #undef ZW
 #undef ST
-#undef CUR
 #undef LR
 #undef XS
 
-template <int G>
+template <int G, bool kBudget>
 cudaError_t launch_group(const SdArgs& g, int num_sms, cudaStream_t s) {
   const size_t smem = group_cta_bytes<G>();
-  cudaError_t e = cudaFuncSetAttribute(sd_group_kernel<G>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaError_t e =
+      cudaFuncSetAttribute(sd_group_kernel<G, kBudget>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   int per_sm = 0;
-  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, sd_group_kernel<G>, group_warps<G>() * 32, smem);
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, sd_group_kernel<G, kBudget>, group_warps<G>() * 32, smem);
   if (e != cudaSuccess) return e;
   if (per_sm < 1) return cudaErrorInvalidConfiguration;
-  sd_group_kernel<G><<<per_sm * num_sms, group_warps<G>() * 32, smem, s>>>(g);
+  sd_group_kernel<G, kBudget><<<per_sm * num_sms, group_warps<G>() * 32, smem, s>>>(g);
   return cudaGetLastError();
 }
 
@@ -953,7 +975,8 @@ cudaError_t launch_group(const SdArgs& g, int num_sms, cudaStream_t s) {
 
 cudaError_t launch_sd_group(const SdArgs& g, int num_sms, cudaStream_t s) {
   if (g.a.n > kGroupN) return cudaErrorInvalidConfiguration;
-  return launch_group<kGroupLanes>(g, num_sms, s);
+  return g.a.budget > 0 ? launch_group<kGroupLanes, true>(g, num_sms, s)
+                        : launch_group<kGroupLanes, false>(g, num_sms, s);
 }
 
 }  // namespace mdx
