@@ -733,9 +733,9 @@ __global__ void __launch_bounds__(group_warps<G>() * 32, MDX_SDG_MIN_BLOCKS) sd_
       if (has) ++p32;
       const bool ok = has && ped < bnd;
       const bool deep = ok && i > 0;
-      bool desc = deep, bstop = false;
+      bool visit = deep, bstop = false;  // the child is a visited (branched) node
       if (kBudget) {
-        desc = deep && n32 < left32;
+        visit = deep && n32 < left32;
         bstop = deep && n32 >= left32;
         budget_hit = budget_hit || bstop;
       }
@@ -751,19 +751,31 @@ __global__ void __launch_bounds__(group_warps<G>() * 32, MDX_SDG_MIN_BLOCKS) sd_
 #pragma unroll
       for (int t = 0; t < RPL; ++t) {
         zn[t] = fmaf(-rcv[t], av, zinv[t]);
-        if (desc) ZW(cm + gl + G * t) = zn[t];
+        if (visit) ZW(cm + gl + G * t) = zn[t];
       }
       const int tsel = (i - 1) / G;
       float cn = zn[0];
 #pragma unroll
       for (int t = 1; t < RPL; ++t) cn = (tsel == t) ? zn[t] : cn;
-      if (desc) {
+      if (visit) {
         ST(i) = make_float4(ped_par, c, flo, fhi);
         XS(i) = (uint8_t)(int)kf;
       }
       const float cnew = __shfl_sync(full, cn, lead + ((i - 1) & (G - 1)));
       const float unew = fmaf(cnew, lrn.y, uoff);
       const float flonew = fminf(fmaxf(ceilf(unew - 0.5f), 0.0f), Pf - 1.0f);
+      // The visited node's first child in Schnorr-Euchner order (the PAM
+      // index nearest u, the lower one on a tie), evaluated as the next pass
+      // would.  Outside the sphere it rules out every child of the node, so
+      // the group does not descend: the node and that one evaluation are
+      // counted, and the next pass goes on with the next child of level i.
+      // (The stores above, made for a descent, touch only state that a
+      // group at level i never reads.)
+      const float hi1 = flonew + 1.0f;
+      const float k1 = (hi1 < Pf && fabsf(unew - flonew) > fabsf(hi1 - unew)) ? hi1 : flonew;
+      const float d1 = fmaf(-lrn.x, fmaf(k1, 2.0f, -(Pf - 1.0f)) * alpha, cnew);
+      const bool enter = fmaf(d1, d1, ped) < bnd;
+      const bool desc = visit && enter;
       i = desc ? im : (pop ? ip : i);
       ped_par = desc ? ped : (pop ? stp.x : ped_par);
       c = desc ? cnew : (pop ? stp.y : c);
@@ -772,9 +784,10 @@ __global__ void __launch_bounds__(group_warps<G>() * 32, MDX_SDG_MIN_BLOCKS) sd_
       rii = desc ? lrn.x : (pop ? lrp.x : rii);
       flo = desc ? flonew : (pop ? stp.z : flo);
       fhi = desc ? flonew + 1.0f : (pop ? stp.w : fhi);
-      if (desc) {
+      if (visit) {
         ++n32;
         lsum += im;
+        if (!enter) ++p32;
       }
     }
 
