@@ -719,6 +719,9 @@ __global__ void __launch_bounds__(group_warps<G>() * 32, MDX_SDG_MIN_BLOCKS) sd_
         rcv[t] = RW(ci + gl + G * t);
         zinv[t] = ZW(ci + gl + G * t);
       }
+      // row i - 1 of this level's R column and residuals, read by every lane
+      // (the next level's interference without a shuffle from its owner)
+      const float rim = RW(ci + im), zim = ZW(ci + im);
       const float4 stp = ST(ip);
       const float2 lrp = LR(ip);
       const float4 stq = ST(ip + 1);
@@ -768,23 +771,17 @@ __global__ void __launch_bounds__(group_warps<G>() * 32, MDX_SDG_MIN_BLOCKS) sd_
       const float4 sb = pop2 ? stq : stp;
       const float2 lb = pop2 ? lrq : lrp;
       // the new level's residuals (rows 0..i-1 matter; the rest spill into
-      // deeper columns), and row i - 1's, held by lane (i - 1) mod G at
-      // t = (i - 1) / G, for the next level's interference
-      float zn[RPL];
+      // deeper columns)
 #pragma unroll
       for (int t = 0; t < RPL; ++t) {
-        zn[t] = fmaf(-rcv[t], av, zinv[t]);
-        if (visit) ZW(cm + gl + G * t) = zn[t];
+        const float zn = fmaf(-rcv[t], av, zinv[t]);
+        if (visit) ZW(cm + gl + G * t) = zn;
       }
-      const int tsel = (i - 1) / G;
-      float cn = zn[0];
-#pragma unroll
-      for (int t = 1; t < RPL; ++t) cn = (tsel == t) ? zn[t] : cn;
       if (visit) {
         ST(i) = make_float4(ped_par, c, flo, fhi);
         XS(i) = (uint8_t)(int)kf;
       }
-      const float cnew = __shfl_sync(full, cn, lead + ((i - 1) & (G - 1)));
+      const float cnew = fmaf(-rim, av, zim);  // the same FMA as row i - 1's residual
       const float unew = fmaf(cnew, lrn.y, uoff);
       const float flonew = fminf(fmaxf(ceilf(unew - 0.5f), 0.0f), Pf - 1.0f);
       // The visited node's first child in Schnorr-Euchner order (the PAM
