@@ -194,6 +194,7 @@ __global__ void __launch_bounds__(group_warps<G>() * 32, MDX_SDG_MIN_BLOCKS) sd_
   long long ticket = -1;  // the group leader's unanswered ticket of the task queue
   int staged = -1;  // vector whose R is in this group's shared memory
   int v = -1, top = n - 1, i = n - 1;
+  int ci = zoff(n - 1);  // zoff(i), kept with i
   // the level's state: parent partial distance, interference c_i, u_i (the
   // real-valued PAM index of c_i / R_ii), R_ii, and the zig-zag cursors (the
   // next lower / higher PAM index, as floats; lo < 0 or hi >= P: exhausted)
@@ -217,6 +218,7 @@ __global__ void __launch_bounds__(group_warps<G>() * 32, MDX_SDG_MIN_BLOCKS) sd_
   // the level a group enters (task node, root restart): cursors from u
   auto enter_level = [&](int lvl, float pp) {
     i = lvl;
+    ci = zoff(lvl);
     ped_par = pp;
     c = ZW(zoff(lvl) + lvl);
     const float2 rl = LR(lvl);
@@ -229,7 +231,180 @@ __global__ void __launch_bounds__(group_warps<G>() * 32, MDX_SDG_MIN_BLOCKS) sd_
   for (;;) {
     // ==================================================== events and work
     const bool want = (mode == 0) || (mode == 2 && (recheck || (since & 15) == 15));
-    if (__any_sync(full, ev_leaf || ev_done || want)) {
+    // one vote per pass decides whether anything but the node step runs:
+    // events of the last pass, groups that want work, the periodic check
+    if (__any_sync(full, ev_leaf || ev_done || want || since >= kSplitEvery)) {
+      // ---------------------------------------------------- periodic check
+      if (since >= kSplitEvery) {
+        since = 0;
+        recheck = true;
+        const bool busy = mode == 1 && !ev_done;
+        SdVec* vs = busy ? vec_of(g, v) : nullptr;
+        if (busy) {
+          task_nodes += n32;
+          nodes += n32;
+          peds += p32;
+          flops += (long long)n32 * node_flops0 - 2ll * lsum;
+          n32 = p32 = lsum = 0;
+          if (!solo) {
+            unsigned int rb = 0;
+            if (gl == 0) rb = *(volatile unsigned int*)&vs->r2bits;
+            const float gr2 = __uint_as_float(__shfl_sync(gmask, rb, lead));
+            if (gr2 < r2) {
+              r2 = gr2;
+              bnd = prune_bound(r2, E, n);
+            }
+          }
+          if (kBudget) {
+            unsigned long long tot = 0;
+            int bh = 0;
+            if (gl == 0) {
+              tot = atomicAdd(&vs->nodes, (unsigned long long)nodes) + (unsigned long long)nodes;
+              atomicAdd(&vs->peds, (unsigned long long)peds);
+              atomicAdd(&vs->flops, (unsigned long long)flops);
+              if (tot >= (unsigned long long)a.budget) atomicExch(&vs->budget_hit, 1);
+              bh = *(volatile int*)&vs->budget_hit;
+            }
+            tot = __shfl_sync(gmask, tot, lead);
+            bh = __shfl_sync(gmask, bh, lead);
+            nodes = peds = flops = 0;  // committed to vs
+            committed = (long long)tot;
+            if (tot >= (unsigned long long)a.budget || bh) {
+              budget_hit = true;
+              left32 = 0;
+            } else {
+              const long long left = a.budget - committed;
+              left32 = left > 0x7fffffffll ? 0x7fffffff : (int)left;
+            }
+          }
+        }
+        // donation while more groups wait than tasks are queued for them
+        int wantd = 0;
+        if (busy && !(a.flags & MDX_SEQUENTIAL_SEARCH) && task_nodes >= kSplitMinNodes && gl == 0) {
+          // tickets taken beyond the tasks reserved so far: groups waiting for work
+          const int waiting = (int)(*(volatile unsigned int*)&g.sh->q_head - *(volatile unsigned int*)&g.sh->q_tail);
+          wantd = waiting > 0 ? 1 : 0;
+        }
+        wantd = __shfl_sync(full, wantd, lead);
+        if (__any_sync(full, wantd)) {
+          if (wantd) {
+            if (gl == 0) atomicAdd(&g.sh->split_checks, 1u);
+            if (solo) {
+              // the vector's state becomes shared: publish the radius first
+              if (gl == 0) {
+                atomicMin(&vs->r2bits, __float_as_uint(r2));
+                __threadfence();
+              }
+              solo = false;
+            }
+            int given = 0;
+            // the top-most open level (the current node's own level only at the task's root)
+            const int lmin = (i == top) ? i : i + 1;
+            for (int l = top; l >= lmin && l >= kMinSplitLevel && given == 0; --l) {
+              float llo, lhi, lc, lu, lped, lrii;
+              if (l == i) {
+                llo = flo;
+                lhi = fhi;
+                lc = c;
+                lu = u;
+                lped = ped_par;
+                lrii = rii;
+              } else {
+                const float4 st = ST(l);
+                const float2 lr = LR(l);
+                llo = st.z;
+                lhi = st.w;
+                lped = st.x;
+                lc = st.y;
+                lu = fmaf(lc, lr.y, uoff);
+                lrii = lr.x;
+              }
+              if (llo < 0.0f && lhi >= Pf) continue;
+              // children inside the sphere, in Schnorr-Euchner order: counted first, then written
+              int cnt = 0;
+              {
+                float a_lo = llo, a_hi = lhi;
+                while (a_lo >= 0.0f || a_hi < Pf) {
+                  float kk;
+                  if (a_hi >= Pf || (a_lo >= 0.0f && fabsf(lu - a_lo) <= fabsf(a_hi - lu))) {
+                    kk = a_lo;
+                    a_lo -= 1.0f;
+                  } else {
+                    kk = a_hi;
+                    a_hi += 1.0f;
+                  }
+                  const float d = fmaf(-lrii, fmaf(kk, 2.0f, -(Pf - 1.0f)) * alpha, lc);
+                  if (!(fmaf(d, d, lped) < bnd)) break;
+                  ++cnt;
+                }
+              }
+              long long base_slot = -1;
+              if (cnt > 0 && gl == 0) {
+                atomicAdd(&vs->pending, cnt);
+                atomicAdd(&g.sh->outstanding, cnt);
+                // tickets may run ahead of the tail, so slots are reserved by
+                // atomicAdd; a slot is rewritten only after its previous task was
+                // copied out (slot_writable)
+                base_slot = (long long)atomicAdd(&g.sh->q_tail, (unsigned)cnt);
+                atomicAdd(&g.sh->donated, (unsigned)cnt);
+                atomicAdd(&g.sh->progress, 1u);
+              }
+              base_slot = __shfl_sync(gmask, base_slot, lead);
+              if (cnt > 0 && base_slot < 0) break;  // queue full: keep the rest
+              for (int q = 0; q < cnt; ++q) {
+                float kk;
+                if (lhi >= Pf || (llo >= 0.0f && fabsf(lu - llo) <= fabsf(lhi - lu))) {
+                  kk = llo;
+                  llo -= 1.0f;
+                } else {
+                  kk = lhi;
+                  lhi += 1.0f;
+                }
+                const float d = fmaf(-lrii, fmaf(kk, 2.0f, -(Pf - 1.0f)) * alpha, lc);
+                const float pd = fmaf(d, d, lped);
+                const unsigned long long sl = (unsigned long long)base_slot + q;
+                SdTask* t = g.queue + ((unsigned)sl & (g.qcap - 1));
+                int wok = 1;
+                if (gl == 0) {
+                  wok = slot_writable(g, t, sl);
+                  if (!wok) {
+                    atomicExch(&g.sh->error, 3);
+                    atomicSub(&vs->pending, 1);
+                    atomicSub(&g.sh->outstanding, 1);
+                  }
+                }
+                wok = __shfl_sync(gmask, wok, lead);
+                if (!wok) continue;
+                for (int j = l + 1 + gl; j < n; j += G) t->x[j] = XS(j);
+                if (gl == 0) {
+                  t->x[l] = (uint8_t)(int)kk;
+                  t->v = v;
+                  t->level = l - 1;
+                  t->ped = pd;
+                }
+                __threadfence();
+                __syncwarp(gmask);
+                if (gl == 0) atomicExch(&t->seq, (g.epoch << 32) | (sl + 1ull));
+              }
+              given += cnt;
+              // the donated (or out-of-sphere) children are gone from this group's search
+              if (l == i) {
+                flo = -1.0f;
+                fhi = Pf;
+              } else {
+                ST(l).z = -1.0f;
+                ST(l).w = Pf;
+              }
+            }
+            if (gl == 0) {
+              if (given > 0) atomicAdd(&g.sh->splits, 1u);
+              else atomicAdd(&g.sh->no_level, 1u);
+            }
+          }
+          __syncwarp();
+        }
+      }
+
       // --------------------------------------------------------- a leaf
       if (__any_sync(full, ev_leaf)) {
         if (ev_leaf) {
@@ -712,7 +887,7 @@ __global__ void __launch_bounds__(group_warps<G>() * 32, MDX_SDG_MIN_BLOCKS) sd_
       // those values are never used (no pop at or above the task's top
       // level, no descent from level 0)
       const int ip = i + 1, im = i - 1;
-      const int ci = zoff(i), cm = ci + i + 1;  // zoff(i - 1)
+      const int cm = ci + i + 1;  // zoff(i - 1)
       float rcv[RPL], zinv[RPL];
 #pragma unroll
       for (int t = 0; t < RPL; ++t) {
@@ -784,18 +959,19 @@ __global__ void __launch_bounds__(group_warps<G>() * 32, MDX_SDG_MIN_BLOCKS) sd_
       const float cnew = fmaf(-rim, av, zim);  // the same FMA as row i - 1's residual
       const float unew = fmaf(cnew, lrn.y, uoff);
       const float flonew = fminf(fmaxf(ceilf(unew - 0.5f), 0.0f), Pf - 1.0f);
-      // The visited node's first child in Schnorr-Euchner order (the PAM
-      // index nearest u, the lower one on a tie), evaluated as the next pass
-      // would.  Outside the sphere it rules out every child of the node, so
-      // the group does not descend: the node and that one evaluation are
-      // counted, and the next pass goes on with the next child of level i.
-      // (The stores above, made for a descent, touch only state that a
-      // group at level i never reads.)
-      const float hi1 = flonew + 1.0f;
-      const float k1 = (hi1 < Pf && fabsf(unew - flonew) > fabsf(hi1 - unew)) ? hi1 : flonew;
-      const float d1 = fmaf(-lrn.x, fmaf(k1, 2.0f, -(Pf - 1.0f)) * alpha, cnew);
+      // The visited node's first child in Schnorr-Euchner order, evaluated
+      // as the next pass would: flonew = ceil(u - 1/2) clamped to the
+      // constellation is the PAM index nearest u (the lower one on a tie),
+      // and the zig-zag takes it first.  Outside the sphere it rules out
+      // every child of the node, so the group does not descend: the node and
+      // that one evaluation are counted, and the next pass goes on with the
+      // next child of level i.  (The stores above, made for a descent, touch
+      // only state that a group at level i never reads.)
+      const float d1 = fmaf(-lrn.x, fmaf(flonew, 2.0f, -(Pf - 1.0f)) * alpha, cnew);
       const bool enter = fmaf(d1, d1, ped) < bnd;
       const bool desc = visit && enter;
+      const int cp = ci - (i + 2);  // zoff(i + 1)
+      ci = desc ? cm : (back ? (pop2 ? cp - (i + 3) : cp) : ci);
       i = desc ? im : (back ? ip + (pop2 ? 1 : 0) : i);
       ped_par = desc ? ped : (back ? sb.x : ped_par);
       c = desc ? cnew : (back ? sb.y : c);
@@ -811,176 +987,7 @@ __global__ void __launch_bounds__(group_warps<G>() * 32, MDX_SDG_MIN_BLOCKS) sd_
       }
     }
 
-    // ===================================================== periodic check
-    if (++since >= kSplitEvery) {
-      since = 0;
-      recheck = true;
-      const bool busy = mode == 1 && !ev_done;
-      SdVec* vs = busy ? vec_of(g, v) : nullptr;
-      if (busy) {
-        task_nodes += n32;
-        nodes += n32;
-        peds += p32;
-        flops += (long long)n32 * node_flops0 - 2ll * lsum;
-        n32 = p32 = lsum = 0;
-        if (!solo) {
-          unsigned int rb = 0;
-          if (gl == 0) rb = *(volatile unsigned int*)&vs->r2bits;
-          const float gr2 = __uint_as_float(__shfl_sync(gmask, rb, lead));
-          if (gr2 < r2) {
-            r2 = gr2;
-            bnd = prune_bound(r2, E, n);
-          }
-        }
-        if (kBudget) {
-          unsigned long long tot = 0;
-          int bh = 0;
-          if (gl == 0) {
-            tot = atomicAdd(&vs->nodes, (unsigned long long)nodes) + (unsigned long long)nodes;
-            atomicAdd(&vs->peds, (unsigned long long)peds);
-            atomicAdd(&vs->flops, (unsigned long long)flops);
-            if (tot >= (unsigned long long)a.budget) atomicExch(&vs->budget_hit, 1);
-            bh = *(volatile int*)&vs->budget_hit;
-          }
-          tot = __shfl_sync(gmask, tot, lead);
-          bh = __shfl_sync(gmask, bh, lead);
-          nodes = peds = flops = 0;  // committed to vs
-          committed = (long long)tot;
-          if (tot >= (unsigned long long)a.budget || bh) {
-            budget_hit = true;
-            left32 = 0;
-          } else {
-            const long long left = a.budget - committed;
-            left32 = left > 0x7fffffffll ? 0x7fffffff : (int)left;
-          }
-        }
-      }
-      // donation while more groups wait than tasks are queued for them
-      int wantd = 0;
-      if (busy && !(a.flags & MDX_SEQUENTIAL_SEARCH) && task_nodes >= kSplitMinNodes && gl == 0) {
-        // tickets taken beyond the tasks reserved so far: groups waiting for work
-        const int waiting = (int)(*(volatile unsigned int*)&g.sh->q_head - *(volatile unsigned int*)&g.sh->q_tail);
-        wantd = waiting > 0 ? 1 : 0;
-      }
-      wantd = __shfl_sync(full, wantd, lead);
-      if (__any_sync(full, wantd)) {
-        if (wantd) {
-          if (gl == 0) atomicAdd(&g.sh->split_checks, 1u);
-          if (solo) {
-            // the vector's state becomes shared: publish the radius first
-            if (gl == 0) {
-              atomicMin(&vs->r2bits, __float_as_uint(r2));
-              __threadfence();
-            }
-            solo = false;
-          }
-          int given = 0;
-          // the top-most open level (the current node's own level only at the task's root)
-          const int lmin = (i == top) ? i : i + 1;
-          for (int l = top; l >= lmin && l >= kMinSplitLevel && given == 0; --l) {
-            float llo, lhi, lc, lu, lped, lrii;
-            if (l == i) {
-              llo = flo;
-              lhi = fhi;
-              lc = c;
-              lu = u;
-              lped = ped_par;
-              lrii = rii;
-            } else {
-              const float4 st = ST(l);
-              const float2 lr = LR(l);
-              llo = st.z;
-              lhi = st.w;
-              lped = st.x;
-              lc = st.y;
-              lu = fmaf(lc, lr.y, uoff);
-              lrii = lr.x;
-            }
-            if (llo < 0.0f && lhi >= Pf) continue;
-            // children inside the sphere, in Schnorr-Euchner order: counted first, then written
-            int cnt = 0;
-            {
-              float a_lo = llo, a_hi = lhi;
-              while (a_lo >= 0.0f || a_hi < Pf) {
-                float kk;
-                if (a_hi >= Pf || (a_lo >= 0.0f && fabsf(lu - a_lo) <= fabsf(a_hi - lu))) {
-                  kk = a_lo;
-                  a_lo -= 1.0f;
-                } else {
-                  kk = a_hi;
-                  a_hi += 1.0f;
-                }
-                const float d = fmaf(-lrii, fmaf(kk, 2.0f, -(Pf - 1.0f)) * alpha, lc);
-                if (!(fmaf(d, d, lped) < bnd)) break;
-                ++cnt;
-              }
-            }
-            long long base_slot = -1;
-            if (cnt > 0 && gl == 0) {
-              atomicAdd(&vs->pending, cnt);
-              atomicAdd(&g.sh->outstanding, cnt);
-              // tickets may run ahead of the tail, so slots are reserved by
-              // atomicAdd; a slot is rewritten only after its previous task was
-              // copied out (slot_writable)
-              base_slot = (long long)atomicAdd(&g.sh->q_tail, (unsigned)cnt);
-              atomicAdd(&g.sh->donated, (unsigned)cnt);
-              atomicAdd(&g.sh->progress, 1u);
-            }
-            base_slot = __shfl_sync(gmask, base_slot, lead);
-            if (cnt > 0 && base_slot < 0) break;  // queue full: keep the rest
-            for (int q = 0; q < cnt; ++q) {
-              float kk;
-              if (lhi >= Pf || (llo >= 0.0f && fabsf(lu - llo) <= fabsf(lhi - lu))) {
-                kk = llo;
-                llo -= 1.0f;
-              } else {
-                kk = lhi;
-                lhi += 1.0f;
-              }
-              const float d = fmaf(-lrii, fmaf(kk, 2.0f, -(Pf - 1.0f)) * alpha, lc);
-              const float pd = fmaf(d, d, lped);
-              const unsigned long long sl = (unsigned long long)base_slot + q;
-              SdTask* t = g.queue + ((unsigned)sl & (g.qcap - 1));
-              int wok = 1;
-              if (gl == 0) {
-                wok = slot_writable(g, t, sl);
-                if (!wok) {
-                  atomicExch(&g.sh->error, 3);
-                  atomicSub(&vs->pending, 1);
-                  atomicSub(&g.sh->outstanding, 1);
-                }
-              }
-              wok = __shfl_sync(gmask, wok, lead);
-              if (!wok) continue;
-              for (int j = l + 1 + gl; j < n; j += G) t->x[j] = XS(j);
-              if (gl == 0) {
-                t->x[l] = (uint8_t)(int)kk;
-                t->v = v;
-                t->level = l - 1;
-                t->ped = pd;
-              }
-              __threadfence();
-              __syncwarp(gmask);
-              if (gl == 0) atomicExch(&t->seq, (g.epoch << 32) | (sl + 1ull));
-            }
-            given += cnt;
-            // the donated (or out-of-sphere) children are gone from this group's search
-            if (l == i) {
-              flo = -1.0f;
-              fhi = Pf;
-            } else {
-              ST(l).z = -1.0f;
-              ST(l).w = Pf;
-            }
-          }
-          if (gl == 0) {
-            if (given > 0) atomicAdd(&g.sh->splits, 1u);
-            else atomicAdd(&g.sh->no_level, 1u);
-          }
-        }
-        __syncwarp();
-      }
-    }
+    ++since;
   }
 }
 
