@@ -881,6 +881,10 @@ __global__ void __launch_bounds__(group_warps<G>() * 32, MDX_SDG_MIN_BLOCKS) sd_
     // instructions under their own predicates (a branch would serialise the
     // outcomes and stall on its resolution every pass).
     {
+      // rows i - 1 of the R and residual columns are read below by every lane
+      // of the group, while only the row's owner wrote the residual (in an
+      // earlier pass): the warp barrier orders those writes before the reads
+      __syncwarp();
       const bool busy = mode == 1;
       // ip, ip + 1 up to n + 1 (above the root) and im = -1 (below a leaf)
       // index past the level arrays into their neighbours in shared memory;
