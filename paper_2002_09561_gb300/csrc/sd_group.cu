@@ -230,7 +230,7 @@ __global__ void __launch_bounds__(group_warps<G>() * 32, MDX_SDG_MIN_BLOCKS) sd_
 
   for (;;) {
     // ==================================================== events and work
-    const bool want = (mode == 0) || (mode == 2 && (recheck || (since & 15) == 15));
+    const bool want = (mode == 0) || (mode == 2 && (recheck || (since & 15) == 14));
     // one vote per pass decides whether anything but the node step runs:
     // events of the last pass, groups that want work, the periodic check
     if (__any_sync(full, ev_leaf || ev_done || want || since >= kSplitEvery)) {
@@ -643,7 +643,7 @@ __global__ void __launch_bounds__(group_warps<G>() * 32, MDX_SDG_MIN_BLOCKS) sd_
       }
 
       // ------------------------------------------------- acquire work
-      const bool wants = (mode == 0) || (mode == 2 && (recheck || (since & 15) == 15));
+      const bool wants = (mode == 0) || (mode == 2 && (recheck || (since & 15) == 14));
       if (__any_sync(full, wants)) {
         // 0: nothing, 1: queued task, 2: fresh vector.  Fresh vectors come
         // first; once they are gone a group takes a ticket of the task queue
@@ -879,13 +879,17 @@ __global__ void __launch_bounds__(group_warps<G>() * 32, MDX_SDG_MIN_BLOCKS) sd_
     // first, independently of the child chosen.  The step has no branch: the
     // groups of a warp that pop, descend, or have no task run the same
     // instructions under their own predicates (a branch would serialise the
-    // outcomes and stall on its resolution every pass).
-    {
+    // outcomes and stall on its resolution every pass).  Two passes run per
+    // vote of the slow paths; a group whose first pass raised an event (a
+    // leaf, the end of its task) sits the second one out.
+#pragma unroll
+    for (int sub = 0; sub < 2; ++sub) {
       // rows i - 1 of the R and residual columns are read below by every lane
       // of the group, while only the row's owner wrote the residual (in an
       // earlier pass): the warp barrier orders those writes before the reads
       __syncwarp();
-      const bool busy = mode == 1;
+      const bool held = sub == 1 && (ev_leaf || ev_done);
+      const bool busy = mode == 1 && !held;
       // ip, ip + 1 up to n + 1 (above the root) and im = -1 (below a leaf)
       // index past the level arrays into their neighbours in shared memory;
       // those values are never used (no pop at or above the task's top
@@ -924,10 +928,12 @@ __global__ void __launch_bounds__(group_warps<G>() * 32, MDX_SDG_MIN_BLOCKS) sd_
         bstop = deep && n32 >= left32;
         budget_hit = budget_hit || bstop;
       }
-      ev_done = busy && ((!ok && i == top) || bstop);
-      ev_leaf = ok && i == 0;
-      leaf_ped = ped;
-      leaf_kf = kf;
+      if (!held) {
+        ev_done = busy && ((!ok && i == top) || bstop);
+        ev_leaf = ok && i == 0;
+        leaf_ped = ped;
+        leaf_kf = kf;
+      }
       const bool pop = busy && !ok && i != top;
       // A pop: the parent's next child (its state is the one a pop restores)
       // is evaluated here as the next pass would.  Outside the sphere, or with
@@ -991,7 +997,7 @@ __global__ void __launch_bounds__(group_warps<G>() * 32, MDX_SDG_MIN_BLOCKS) sd_
       }
     }
 
-    ++since;
+    since += 2;
   }
 }
 
