@@ -77,6 +77,8 @@ __host__ __device__ constexpr int group_warps() {
   return G >= 8 ? 2 : 1;
 }
 constexpr int kTri = 528;       // column-packed triangle of n = 32
+// node-step passes per vote of the slow paths (divides 16 and kSplitEvery)
+constexpr int kPassesPerVote = 4;
 
 // R and the residual stack in shared memory: column c (rows 0..c) starts at
 // zoff(c) = kTri - (c + 1)(c + 2) / 2, the columns in descending order.  A
@@ -230,7 +232,7 @@ __global__ void __launch_bounds__(group_warps<G>() * 32, MDX_SDG_MIN_BLOCKS) sd_
 
   for (;;) {
     // ==================================================== events and work
-    const bool want = (mode == 0) || (mode == 2 && (recheck || (since & 15) == 14));
+    const bool want = (mode == 0) || (mode == 2 && (recheck || (since & 15) == 16 - kPassesPerVote));
     // one vote per pass decides whether anything but the node step runs:
     // events of the last pass, groups that want work, the periodic check
     if (__any_sync(full, ev_leaf || ev_done || want || since >= kSplitEvery)) {
@@ -643,7 +645,7 @@ __global__ void __launch_bounds__(group_warps<G>() * 32, MDX_SDG_MIN_BLOCKS) sd_
       }
 
       // ------------------------------------------------- acquire work
-      const bool wants = (mode == 0) || (mode == 2 && (recheck || (since & 15) == 14));
+      const bool wants = (mode == 0) || (mode == 2 && (recheck || (since & 15) == 16 - kPassesPerVote));
       if (__any_sync(full, wants)) {
         // 0: nothing, 1: queued task, 2: fresh vector.  Fresh vectors come
         // first; once they are gone a group takes a ticket of the task queue
@@ -879,16 +881,16 @@ __global__ void __launch_bounds__(group_warps<G>() * 32, MDX_SDG_MIN_BLOCKS) sd_
     // first, independently of the child chosen.  The step has no branch: the
     // groups of a warp that pop, descend, or have no task run the same
     // instructions under their own predicates (a branch would serialise the
-    // outcomes and stall on its resolution every pass).  Two passes run per
-    // vote of the slow paths; a group whose first pass raised an event (a
-    // leaf, the end of its task) sits the second one out.
+    // outcomes and stall on its resolution every pass).  kPassesPerVote
+    // passes run per vote of the slow paths; a group whose pass raised an
+    // event (a leaf, the end of its task) sits the rest of them out.
 #pragma unroll
-    for (int sub = 0; sub < 2; ++sub) {
+    for (int sub = 0; sub < kPassesPerVote; ++sub) {
       // rows i - 1 of the R and residual columns are read below by every lane
       // of the group, while only the row's owner wrote the residual (in an
       // earlier pass): the warp barrier orders those writes before the reads
       __syncwarp();
-      const bool held = sub == 1 && (ev_leaf || ev_done);
+      const bool held = sub > 0 && (ev_leaf || ev_done);
       const bool busy = mode == 1 && !held;
       // ip, ip + 1 up to n + 1 (above the root) and im = -1 (below a leaf)
       // index past the level arrays into their neighbours in shared memory;
@@ -997,7 +999,7 @@ __global__ void __launch_bounds__(group_warps<G>() * 32, MDX_SDG_MIN_BLOCKS) sd_
       }
     }
 
-    since += 2;
+    since += kPassesPerVote;
   }
 }
 
