@@ -892,10 +892,9 @@ __global__ void __launch_bounds__(group_warps<G>() * 32, MDX_SDG_MIN_BLOCKS) sd_
       __syncwarp();
       const bool held = sub > 0 && (ev_leaf || ev_done);
       const bool busy = mode == 1 && !held;
-      // ip, ip + 1 up to n + 1 (above the root) and im = -1 (below a leaf)
-      // index past the level arrays into their neighbours in shared memory;
-      // those values are never used (no pop at or above the task's top
-      // level, no descent from level 0)
+      // ip = n (the root) and im = -1 (a leaf) index past the level arrays
+      // into their neighbours in shared memory; those values are never used
+      // (no pop at the task's top level, no descent from level 0)
       const int ip = i + 1, im = i - 1;
       const int cm = ci + i + 1;  // zoff(i - 1)
       float rcv[RPL], zinv[RPL];
@@ -909,8 +908,6 @@ __global__ void __launch_bounds__(group_warps<G>() * 32, MDX_SDG_MIN_BLOCKS) sd_
       const float rim = RW(ci + im), zim = ZW(ci + im);
       const float4 stp = ST(ip);
       const float2 lrp = LR(ip);
-      const float4 stq = ST(ip + 1);
-      const float2 lrq = LR(ip + 1);
       const float2 lrn = LR(im);
       const bool has_lo = flo >= 0.0f, has_hi = fhi < Pf;
       const bool has = busy && (has_lo || has_hi);
@@ -937,26 +934,6 @@ __global__ void __launch_bounds__(group_warps<G>() * 32, MDX_SDG_MIN_BLOCKS) sd_
         leaf_kf = kf;
       }
       const bool pop = busy && !ok && i != top;
-      // A pop: the parent's next child (its state is the one a pop restores)
-      // is evaluated here as the next pass would.  Outside the sphere, or with
-      // none left, the parent level is exhausted as well, and the group pops a
-      // second level at once (at the task's top level the task ends), saving
-      // that pass; the evaluation is counted.  Inside, the group pops one
-      // level and the next pass evaluates that child again and descends.
-      const float up = fmaf(stp.y, lrp.y, uoff);
-      const bool plo = stp.z >= 0.0f, phi = stp.w < Pf;
-      const bool ptake_lo = plo && (!phi || fabsf(up - stp.z) <= fabsf(stp.w - up));
-      const float kp = ptake_lo ? stp.z : stp.w;
-      const float dp = fmaf(-lrp.x, fmaf(kp, 2.0f, -(Pf - 1.0f)) * alpha, stp.y);
-      const bool pfail = !(plo || phi) || !(fmaf(dp, dp, stp.x) < bnd);
-      const bool pop2 = pop && pfail && ip != top;
-      if (pop && pfail) {
-        if (plo || phi) ++p32;
-        if (ip == top) ev_done = true;
-      }
-      const bool back = pop && !(pfail && ip == top);  // one or two levels up
-      const float4 sb = pop2 ? stq : stp;
-      const float2 lb = pop2 ? lrq : lrp;
       // the new level's residuals (rows 0..i-1 matter; the rest spill into
       // deeper columns)
 #pragma unroll
@@ -982,16 +959,15 @@ __global__ void __launch_bounds__(group_warps<G>() * 32, MDX_SDG_MIN_BLOCKS) sd_
       const float d1 = fmaf(-lrn.x, fmaf(flonew, 2.0f, -(Pf - 1.0f)) * alpha, cnew);
       const bool enter = fmaf(d1, d1, ped) < bnd;
       const bool desc = visit && enter;
-      const int cp = ci - (i + 2);  // zoff(i + 1)
-      ci = desc ? cm : (back ? (pop2 ? cp - (i + 3) : cp) : ci);
-      i = desc ? im : (back ? ip + (pop2 ? 1 : 0) : i);
-      ped_par = desc ? ped : (back ? sb.x : ped_par);
-      c = desc ? cnew : (back ? sb.y : c);
-      // a popped level's u is recomputed exactly as it was formed on the way down
-      u = desc ? unew : (back ? fmaf(sb.y, lb.y, uoff) : u);
-      rii = desc ? lrn.x : (back ? lb.x : rii);
-      flo = desc ? flonew : (back ? sb.z : flo);
-      fhi = desc ? flonew + 1.0f : (back ? sb.w : fhi);
+      ci = desc ? cm : (pop ? ci - (i + 2) : ci);  // zoff(i - 1), zoff(i + 1)
+      i = desc ? im : (pop ? ip : i);
+      ped_par = desc ? ped : (pop ? stp.x : ped_par);
+      c = desc ? cnew : (pop ? stp.y : c);
+      // the parent's u is recomputed exactly as it was formed on the way down
+      u = desc ? unew : (pop ? fmaf(stp.y, lrp.y, uoff) : u);
+      rii = desc ? lrn.x : (pop ? lrp.x : rii);
+      flo = desc ? flonew : (pop ? stp.z : flo);
+      fhi = desc ? flonew + 1.0f : (pop ? stp.w : fhi);
       if (visit) {
         ++n32;
         lsum += im;
