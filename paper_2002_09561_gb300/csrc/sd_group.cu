@@ -78,7 +78,7 @@ __host__ __device__ constexpr int group_warps() {
 }
 constexpr int kTri = 528;       // column-packed triangle of n = 32
 // node-step passes per vote of the slow paths (divides 16 and kSplitEvery)
-constexpr int kPassesPerVote = 4;
+constexpr int kPassesPerVote = 8;
 
 // R and the residual stack in shared memory: column c (rows 0..c) starts at
 // zoff(c) = kTri - (c + 1)(c + 2) / 2, the columns in descending order.  A
