@@ -98,7 +98,7 @@ __host__ __device__ constexpr int zoff(int c) { return kTri - (((c + 1) * (c + 2
 //   ST      32 x NG float4     level state {parent partial distance, c_i, cursor lo, cursor hi}
 //                              (u_i = c_i / (2 alpha R_ii) + (P - 1) / 2 and R_ii come from LR)
 //   LR      32 x NG float2     {R_ii, 1 / (2 alpha R_ii)}
-//   XS      32 x NG bytes      current path
+//   XS      32 x NG floats     current path (PAM indices as floats: no conversion on a descent)
 //   per group: kCand candidate partial distances and kCand x 32 path bytes
 template <int G>
 struct WarpLayout {
@@ -108,7 +108,7 @@ struct WarpLayout {
   static constexpr int ST = Z + (kTri + kGroupN) * NG;
   static constexpr int LR = ST + 4 * kGroupN * NG;
   static constexpr int XS = LR + 2 * kGroupN * NG;
-  static constexpr int CAND = XS + kGroupN * NG / 4;
+  static constexpr int CAND = XS + kGroupN * NG;
   static constexpr int CAND_WORDS = kCand + kCand * kGroupN / 4;  // per group
   static constexpr int WORDS = CAND + NG * CAND_WORDS;
   static_assert(ST % 4 == 0 && LR % 2 == 0, "16- and 8-byte alignment of the level arrays");
@@ -182,7 +182,7 @@ __global__ void __launch_bounds__(group_warps<G>() * 32, MDX_SDG_MIN_BLOCKS) sd_
   float* Zw = wbase + L::Z;
   float4* STw = reinterpret_cast<float4*>(wbase + L::ST);
   float2* LRw = reinterpret_cast<float2*>(wbase + L::LR);
-  uint8_t* XSw = reinterpret_cast<uint8_t*>(wbase + L::XS);
+  float* XSw = wbase + L::XS;
   float* cped = wbase + L::CAND + gid * L::CAND_WORDS;
   uint8_t* cx = reinterpret_cast<uint8_t*>(cped + kCand);
 #define RW(e) Rw[(e) * NG + gid]
@@ -377,7 +377,7 @@ __global__ void __launch_bounds__(group_warps<G>() * 32, MDX_SDG_MIN_BLOCKS) sd_
                 }
                 wok = __shfl_sync(gmask, wok, lead);
                 if (!wok) continue;
-                for (int j = l + 1 + gl; j < n; j += G) t->x[j] = XS(j);
+                for (int j = l + 1 + gl; j < n; j += G) t->x[j] = (uint8_t)(int)XS(j);
                 if (gl == 0) {
                   t->x[l] = (uint8_t)(int)kk;
                   t->v = v;
@@ -410,7 +410,7 @@ __global__ void __launch_bounds__(group_warps<G>() * 32, MDX_SDG_MIN_BLOCKS) sd_
       // --------------------------------------------------------- a leaf
       if (__any_sync(full, ev_leaf)) {
         if (ev_leaf) {
-          XS(0) = (uint8_t)(int)leaf_kf;
+          XS(0) = leaf_kf;
           int slot = -1;
           if (ncl < kCand) {
             slot = ncl++;
@@ -426,7 +426,7 @@ __global__ void __launch_bounds__(group_warps<G>() * 32, MDX_SDG_MIN_BLOCKS) sd_
           }
           if (slot >= 0) {
             uint8_t* dst = cx + slot * kGroupN;
-            for (int j = gl; j < n; j += G) dst[j] = XS(j);
+            for (int j = gl; j < n; j += G) dst[j] = (uint8_t)(int)XS(j);
             cped[slot] = leaf_ped;
           }
           if (!solo && gl == 0) atomicMin(&vec_of(g, v)->r2bits, __float_as_uint(leaf_ped));
@@ -687,7 +687,7 @@ __global__ void __launch_bounds__(group_warps<G>() * 32, MDX_SDG_MIN_BLOCKS) sd_
         // copy the task's path, then free the slot
         if (got == 1)
           for (int j = tlevel + 1 + gl; j < n; j += G)
-            XS(j) = ((volatile uint8_t*)g.queue[(unsigned)slot & (g.qcap - 1)].x)[j];
+            XS(j) = (float)((volatile uint8_t*)g.queue[(unsigned)slot & (g.qcap - 1)].x)[j];
         __syncwarp();
         if ((got == 1 || got == -2) && gl == 0) {
           __threadfence();
@@ -797,7 +797,7 @@ __global__ void __launch_bounds__(group_warps<G>() * 32, MDX_SDG_MIN_BLOCKS) sd_
             if (r <= top) {
               float z = yb[r];
               for (int j = n - 1; j > top; --j)
-                z = fmaf(-RW(zoff(j) + r), (float)(2 * (int)XS(j) - (P - 1)) * alpha, z);
+                z = fmaf(-RW(zoff(j) + r), fmaf(XS(j), 2.0f, -(Pf - 1.0f)) * alpha, z);
               ZW(zoff(top) + r) = z;
             }
           }
@@ -943,7 +943,7 @@ __global__ void __launch_bounds__(group_warps<G>() * 32, MDX_SDG_MIN_BLOCKS) sd_
       }
       if (visit) {
         ST(i) = make_float4(ped_par, c, flo, fhi);
-        XS(i) = (uint8_t)(int)kf;
+        XS(i) = kf;
       }
       const float cnew = fmaf(-rim, av, zim);  // the same FMA as row i - 1's residual
       const float unew = fmaf(cnew, lrn.y, uoff);
