@@ -18,8 +18,10 @@
  * caller; the library never frees caller memory and never keeps a caller
  * pointer beyond the call.  With MDX_HOST_BUFFERS, the same arguments are
  * host pointers (pinned memory gives asynchronous copies); the library
- * stages them through buffers it allocated in mdx_create and returns after
- * the results are back in host memory.
+ * stages them through buffers it allocated in mdx_create (the inputs are
+ * copied in chunks on a stream of the context's own, after the work already
+ * queued on `stream`, and the QR of each chunk starts as soon as that chunk
+ * is in) and returns after the results are back in host memory.
  *
  * Layouts (all row-major, C order):
  *   H          double [batch][n_rx][n_tx][2]   (re, im) pairs
@@ -340,7 +342,8 @@ mdx_status detect_kbest_noalloc(const mdx_params* p, int batch, const double* H,
 
 /* Kernel timing for benchmarks.  While enabled, every call records CUDA
  * events on its stream around the QR kernel and the search kernel (up to
- * 1024 calls are kept).  mdx_profile_read waits for those events, writes
+ * 1024 calls are kept; with MDX_HOST_BUFFERS the QR interval includes the
+ * wait for the staged inputs).  mdx_profile_read waits for those events, writes
  * ms_out[0] = summed QR time, ms_out[1] = summed search time (milliseconds),
  * ms_out[2] = number of calls recorded, ms_out[3] = the error word of the
  * last detect_sd launch (non-zero if a bounded wait inside it expired),

@@ -42,6 +42,12 @@ struct mdx_ctx {
   double* smet = nullptr;
   int32_t* svst = nullptr;
   int64_t* sstats = nullptr;
+  // host inputs are copied on this stream in up to kHostChunks chunks, each
+  // followed by an event the QR of that chunk waits for (see run_detect)
+  static constexpr int kHostChunks = 8;
+  cudaStream_t copy_stream = nullptr;
+  cudaEvent_t ev_free = nullptr;
+  cudaEvent_t ev_chunk[kHostChunks] = {};
   // uneven batches (detect_mixed): the uploaded request table and its device
   // descriptors [MixedReq x n | order x n | QR ids x n], the QR class runs
   // (n_rx, n_tx, first id, count), per-warp global state slots, the tuning
@@ -147,6 +153,10 @@ void free_all(mdx_ctx* c) {
   if (c->mx_dev) cudaFree(c->mx_dev);
   if (c->mx_scratch) cudaFree(c->mx_scratch);
   if (c->mx_pinned) cudaFreeHost(c->mx_pinned);
+  for (cudaEvent_t ev : c->ev_chunk)
+    if (ev) cudaEventDestroy(ev);
+  if (c->ev_free) cudaEventDestroy(c->ev_free);
+  if (c->copy_stream) cudaStreamDestroy(c->copy_stream);
 }
 
 enum Algo { ALGO_SD = 0, ALGO_KBEST = 1, ALGO_HYBRID = 2, ALGO_LINEAR = 3 };
@@ -239,12 +249,31 @@ mdx_status run_detect(int algo, mdx_ctx* c, const mdx_params* p, int batch, cons
   double* dmet = met;
   int32_t* dvst = vst;
   int64_t* dstats = stats;
+  // Host inputs: copied on the context's copy stream in chunks of at least
+  // 32 MB, each chunk's QR waiting on the caller's stream for that chunk
+  // only, so that the copy of chunk j + 1 overlaps the QR of chunk j.  The
+  // copy stream first waits for everything already queued on the caller's
+  // stream (an earlier call may still read the staging buffers).
+  const size_t h_bytes = sizeof(double) * 2 * (size_t)batch * N * M;
+  const int chunks = host ? (int)std::min<size_t>(mdx_ctx::kHostChunks,
+                                                  std::max<size_t>(1, h_bytes / ((size_t)32 << 20)))
+                          : 1;
+  auto chunk_begin = [&](int j) { return (int)((long long)batch * j / chunks); };
   if (host) {
-    e = cudaMemcpyAsync(c->sH, H, sizeof(double) * 2 * (size_t)batch * N * M, cudaMemcpyHostToDevice, s);
-    if (e == cudaSuccess)
-      e = cudaMemcpyAsync(c->sy, y, sizeof(double) * 2 * (size_t)batch * N, cudaMemcpyHostToDevice, s);
+    cudaStream_t cs = c->copy_stream;
+    e = cudaEventRecord(c->ev_free, s);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(cs, c->ev_free, 0);
     if (e == cudaSuccess && nv)
-      e = cudaMemcpyAsync(c->snv, nv, sizeof(double) * batch, cudaMemcpyHostToDevice, s);
+      e = cudaMemcpyAsync(c->snv, nv, sizeof(double) * batch, cudaMemcpyHostToDevice, cs);
+    for (int j = 0; j < chunks && e == cudaSuccess; ++j) {
+      const size_t b0 = (size_t)chunk_begin(j), nb = (size_t)chunk_begin(j + 1) - b0;
+      e = cudaMemcpyAsync(c->sH + b0 * 2 * N * M, H + b0 * 2 * N * M, sizeof(double) * 2 * nb * N * M,
+                          cudaMemcpyHostToDevice, cs);
+      if (e == cudaSuccess)
+        e = cudaMemcpyAsync(c->sy + b0 * 2 * N, y + b0 * 2 * N, sizeof(double) * 2 * nb * N, cudaMemcpyHostToDevice,
+                            cs);
+      if (e == cudaSuccess) e = cudaEventRecord(c->ev_chunk[j], cs);
+    }
     if (e != cudaSuccess) return cuda_fail(c, e, "host-to-device staging");
     dH = c->sH;
     dy = c->sy;
@@ -260,9 +289,18 @@ mdx_status run_detect(int algo, mdx_ctx* c, const mdx_params* p, int batch, cons
     ev = c->prof_ev[c->prof_n++];
     cudaEventRecord(ev[0], s);
   }
-  QrOut q{c->R64, c->yb64, c->R32, c->yb32, nullptr, nullptr, c->singular};
-  e = launch_qr(batch, N, M, dH, dy, q, s);
-  if (e != cudaSuccess) return cuda_fail(c, e, "QR launch");
+  for (int j = 0; j < chunks; ++j) {
+    const int b0 = chunk_begin(j), nb = chunk_begin(j + 1) - b0;
+    if (host) {
+      e = cudaStreamWaitEvent(s, c->ev_chunk[j], 0);
+      if (e != cudaSuccess) return cuda_fail(c, e, "host-to-device staging");
+    }
+    QrOut q{c->R64 + (size_t)b0 * tri_stride64(n), c->yb64 + (size_t)b0 * vec_stride64(n),
+            c->R32 + (size_t)b0 * tri_stride32(n), c->yb32 + (size_t)b0 * vec_stride32(n),
+            nullptr, nullptr, c->singular + b0};
+    e = launch_qr(nb, N, M, dH + (size_t)b0 * 2 * N * M, dy + (size_t)b0 * 2 * N, q, s);
+    if (e != cudaSuccess) return cuda_fail(c, e, "QR launch");
+  }
 
   if (learned || order) {
     // radius proposed by the network (r^2 = sigma^2 exp(o_0)) and/or capped by
@@ -915,6 +953,9 @@ mdx_status mdx_create(mdx_ctx** out, int device, int max_batch, int max_n_rx, in
   chk(alloc(c, reinterpret_cast<unsigned char**>(&c->sd_queue), sd_task_bytes() * kSdQueueSlots));
   chk(alloc(c, &c->sd_vstate, B * sd_vec_state_bytes(n)));
   chk(alloc(c, &c->sd_order, sd_order_ints(max_batch)));
+  chk(cudaStreamCreateWithFlags(&c->copy_stream, cudaStreamNonBlocking));
+  chk(cudaEventCreateWithFlags(&c->ev_free, cudaEventDisableTiming));
+  for (cudaEvent_t& ev : c->ev_chunk) chk(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
   if (e != cudaSuccess) {
     cudaGetLastError();
     free_all(c);

@@ -152,3 +152,31 @@ def test_sequential_counts_match_the_oracle_exactly_at_high_snr(env):
     print(f"node counts equal to the oracle's on {eq.mean():.4f} of vectors, totals {g.sum()} vs {o.sum()}")
     assert eq.mean() > 0.9
     assert abs(g.sum() / o.sum() - 1.0) < 0.02
+
+
+def test_host_buffers_in_chunks_equal_the_device_path():
+    """40,000 vectors (164 MB of H): the host inputs are copied in chunks on
+    the context's copy stream, each chunk's QR waiting for its own copy; the
+    answers are those of the device path, bit for bit."""
+    import torch
+
+    from paper_2002_09561_gb300 import mdx
+
+    B = 40000
+    ctx = mdx.Context(0, max_batch=B, max_n_rx=16, max_n_tx=16)
+    try:
+        w = wl.generate(3123, B, 16, 16, 16, 18.0)
+        p = mdx.make_params(16, 16, 16, radius="paper")
+        H, y, nv = (torch.from_numpy(w[k]).cuda() for k in ("H", "y", "noise_var"))
+        sym_d, met_d, vst_d, _ = mdx.detect("sd", ctx, p, H, y, nv)
+        torch.cuda.synchronize()
+        pin = lambda a: torch.from_numpy(a).pin_memory().numpy()  # noqa: E731
+        sym = torch.empty((B, 16), dtype=torch.uint8).pin_memory().numpy()
+        met = torch.empty(B, dtype=torch.float64).pin_memory().numpy()
+        vst = torch.empty(B, dtype=torch.int32).pin_memory().numpy()
+        mdx.detect_host("sd", ctx, p, pin(w["H"]), pin(w["y"]), pin(w["noise_var"]), sym, met, vst)
+        np.testing.assert_array_equal(sym, sym_d.cpu().numpy())
+        np.testing.assert_array_equal(met, met_d.cpu().numpy())
+        np.testing.assert_array_equal(vst, vst_d.cpu().numpy())
+    finally:
+        ctx.close()
