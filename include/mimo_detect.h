@@ -131,7 +131,9 @@ typedef struct {
   int hybrid_depth;      /* real rows explored by the hybrid's SD master (Sec. VI),
                             0..min(2 n_tx, 12) with sqrt(qam)^depth <= 4096 */
   long long node_budget; /* per-vector cap on branched nodes (detect_sd, detect_hybrid);
-                            0 = none */
+                            0 = none.  detect_sd with a budget searches each
+                            vector's tree in one worker (no subtree splitting),
+                            so that the cap is exact */
   int flags;             /* MDX_* flags above */
 } mdx_params;
 

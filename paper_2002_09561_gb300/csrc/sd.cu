@@ -62,6 +62,10 @@ __global__ void __launch_bounds__(kWarpsMax * 32, ROWS == 1 ? MDX_SD_MIN_BLOCKS_
   const SearchArgs& a = g.a;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int n = a.n, P = a.P;
+  // a vector's tree is split between warps unless the search is sequential or
+  // has a node budget (a cap per vector, which tasks running at once could
+  // only check between periodic checks)
+  const bool may_split = !(a.flags & MDX_SEQUENTIAL_SEARCH) && a.budget <= 0;
   const int ts = tri_stride32(n);
   unsigned char* base = smem + warp * sd_warp_bytes(n);
   float* Rc = reinterpret_cast<float*>(base);  // column-packed R (FP32)
@@ -131,9 +135,10 @@ __global__ void __launch_bounds__(kWarpsMax * 32, ROWS == 1 ? MDX_SD_MIN_BLOCKS_
         if (v < a.batch) {
           fresh = true;
         } else {
-          // idle: wait until a task is queued or everything is finished
-          int leave = 0;
-          if (lane == 0) {
+          // idle: wait until a task is queued or everything is finished (a
+          // search that does not split queues no task)
+          int leave = may_split ? 0 : 1;
+          if (lane == 0 && may_split) {
             atomicAdd(&g.sh->idle, 1);
             for (int it = 0; it < (1 << 22); ++it) {
               if (*(volatile unsigned int*)&g.sh->q_head < *(volatile unsigned int*)&g.sh->q_tail) break;
@@ -398,7 +403,7 @@ __global__ void __launch_bounds__(kWarpsMax * 32, ROWS == 1 ? MDX_SD_MIN_BLOCKS_
         }
         // split only while more warps wait than tasks are queued for them
         int want = 0;
-        if (!(a.flags & MDX_SEQUENTIAL_SEARCH) && task_nodes >= kSplitMinNodes && lane == 0) {
+        if (may_split && task_nodes >= kSplitMinNodes && lane == 0) {
           const int idle_w = *(volatile int*)&g.sh->idle;
           const int queued = (int)(*(volatile unsigned int*)&g.sh->q_tail - *(volatile unsigned int*)&g.sh->q_head);
           want = idle_w > queued ? 1 : 0;

@@ -168,6 +168,11 @@ __global__ void __launch_bounds__(group_warps<G>() * 32, MDX_SDG_MIN_BLOCKS) sd_
   const unsigned full = 0xffffffffu;
   const int n = a.n, P = a.P;
   const float Pf = (float)P;
+  // A vector's tree is split between groups unless the search is sequential
+  // or has a node budget: the budget is a cap per vector, which tasks running
+  // at once could only check between passes (and it bounds the work of a
+  // vector anyway)
+  const bool may_split = !(a.flags & MDX_SEQUENTIAL_SEARCH) && !kBudget;
   const int ts = tri_stride32(n);
   const float alpha = a.alpha;
   const float uoff = 0.5f * (float)(P - 1);
@@ -282,7 +287,7 @@ __global__ void __launch_bounds__(group_warps<G>() * 32, MDX_SDG_MIN_BLOCKS) sd_
         }
         // donation while more groups wait than tasks are queued for them
         int wantd = 0;
-        if (busy && !(a.flags & MDX_SEQUENTIAL_SEARCH) && task_nodes >= kSplitMinNodes && gl == 0) {
+        if (busy && may_split && task_nodes >= kSplitMinNodes && gl == 0) {
           // tickets taken beyond the tasks reserved so far: groups waiting for work
           const int waiting = (int)(*(volatile unsigned int*)&g.sh->q_head - *(volatile unsigned int*)&g.sh->q_tail);
           wantd = waiting > 0 ? 1 : 0;
@@ -664,7 +669,7 @@ __global__ void __launch_bounds__(group_warps<G>() * 32, MDX_SDG_MIN_BLOCKS) sd_
             if (got == 2 && g.order) tv = g.order[tv];
             if (got == 0) atomicSub(&g.sh->outstanding, 1);
           }
-          if (got == 0 && ticket < 0 && !(a.flags & MDX_SEQUENTIAL_SEARCH))
+          if (got == 0 && ticket < 0 && may_split)
             ticket = (long long)atomicAdd(&g.sh->q_head, 1u);
           if (got == 0 && ticket >= 0) {
             SdTask* t = g.queue + ((unsigned)ticket & (g.qcap - 1));
@@ -826,13 +831,13 @@ __global__ void __launch_bounds__(group_warps<G>() * 32, MDX_SDG_MIN_BLOCKS) sd_
       // ------------------------------------------ the whole warp waits
       if (!__any_sync(full, mode == 1)) {
         if (__any_sync(full, mode == 0)) continue;  // a group just ended a vector: look again
-        // every group holds a ticket (or, in a sequential search, has nothing
-        // left to take): wait until a ticket's slot is published, fresh vectors
+        // every group holds a ticket (or, in a search that does not split, has
+        // nothing left to take): wait until a ticket's slot is published, fresh vectors
         // appear, or no task is queued or running any more.  The wait is bounded
         // by progress: it gives up (error word 4) only after about 2^22 polls in
         // which no task ended anywhere.
         int leave = 0;
-        if (a.flags & MDX_SEQUENTIAL_SEARCH) {
+        if (!may_split) {
           leave = 1;
         } else {
           unsigned int seen = 0;

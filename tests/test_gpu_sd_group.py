@@ -180,3 +180,28 @@ def test_host_buffers_in_chunks_equal_the_device_path():
         np.testing.assert_array_equal(vst, vst_d.cpu().numpy())
     finally:
         ctx.close()
+
+
+def test_budget_above_the_split_threshold(env):
+    """A budget above the 512 nodes a task searches before it may donate: a
+    budgeted search does not split trees, so the cap holds exactly (with
+    splitting, tasks running at once overshot it by a third); vectors that
+    finish within it get the oracle's exact answer, the others a leaf no
+    better than the ML one."""
+    torch, mdx, ctx = env
+    budget = 5000
+    w = wl.generate(3124, 200, 16, 16, 16, 5.0)
+    sym, met, vst, st, split = _run(env, w, 16, budget=budget)
+    ref = oracle.detect_batch("sd", w["H"], w["y"], w["noise_var"], 16, radius="paper", want_gap=True)
+    hit = vst == mdx.MDX_V_BUDGET_EXCEEDED
+    print(f"budget {budget}: {hit.sum()} of {len(vst)} vectors hit it, max nodes {st[:, 0].max()}, "
+          f"max nodes / budget {st[:, 0].max() / budget:.3f}, split counters {split}")
+    assert 0 < hit.sum() < len(vst)
+    done = ~hit
+    same = (sym[done] == ref["sym"][done]).all(axis=1)
+    assert (same | (ref["gap"][done] < SD_GAP)).all()
+    rel = np.abs(met[done][same] - ref["metric"][done][same]) / ref["metric"][done][same]
+    assert rel.max() < MET_RTOL
+    assert (met[hit] >= ref["metric"][hit] * (1 - 1e-9)).all()
+    assert (st[:, 0] <= budget).all()
+    assert split["donated"] == 0
