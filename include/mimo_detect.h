@@ -130,10 +130,13 @@ typedef struct {
                             (detect_kbest, detect_hybrid) */
   int hybrid_depth;      /* real rows explored by the hybrid's SD master (Sec. VI),
                             0..min(2 n_tx, 12) with sqrt(qam)^depth <= 4096 */
-  long long node_budget; /* per-vector cap on branched nodes (detect_sd, detect_hybrid);
-                            0 = none.  detect_sd with a budget searches each
-                            vector's tree in one worker (no subtree splitting),
-                            so that the cap is exact */
+  long long node_budget; /* per-vector budget of branched nodes (detect_sd,
+                            detect_hybrid); 0 = none.  detect_sd: an exact cap
+                            (a budgeted search keeps each vector's tree in one
+                            worker, without subtree splitting); detect_hybrid:
+                            the vector stops once a finished prefix run brings
+                            its count to the budget, so the runs in flight may
+                            pass it */
   int flags;             /* MDX_* flags above */
 } mdx_params;
 
