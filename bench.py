@@ -54,8 +54,10 @@ WORKLOADS = {
     # complex tree (one level per complex antenna, Q children): exact SD with the
     # learned radius and K-best on the paper's 16x16 64-QAM configuration
     # (the complex-tree SD runs one warp per vector without subtree splitting, so
-    # its low-SNR tail is one warp's: the sweep starts at 12 dB)
-    "16x16-16qam-sd-complex-learned": dict(n=16, qam=16, snr=[12.0, 14.0, 16.0, 18.0, 20.0], vectors=100_000,
+    # its low-SNR tail is one warp's: the sweep starts at 12 dB, 20,000 vectors
+    # per step, and the Babai control, whose open first sphere leaves that tail
+    # unbounded, is not run)
+    "16x16-16qam-sd-complex-learned": dict(n=16, qam=16, snr=[12.0, 14.0, 16.0, 18.0, 20.0], vectors=20_000,
                                            detector="sd", radius="paper", K=0, depth=0, learned=True,
                                            complex=True),
     "16x16-64qam-kbest32-complex": dict(n=16, qam=64, snr=[16.0, 20.0, 24.0, 28.0], vectors=100_000,
@@ -526,7 +528,7 @@ def main():
                  "identical_decisions": bool(torch.equal(pout[0], out[0])),
                  "ber": int(perrs[0]) / (B * bits_vec), "speedup_learned": pms / ms,
                  "search_ms_per_launch": pprof[1] / max(pprof[2], 1), "per_snr": per_snr(w, ph, data["sym"])}
-        if algo == "sd":
+        if algo == "sd" and not w.get("complex"):
             # the Babai-radius control: no initial radius, so the first leaf the
             # Schnorr-Euchner descent reaches (the Babai / ZF-SIC point) sets r^2
             bsteps = max(1, min(args.steps, 5))
