@@ -82,7 +82,7 @@ METRIC = "decoded vectors/s at matched BER (16x16 16QAM, 100x100 64QAM), learned
 # grows with the number of vectors), with the capture it comes from.  A kernel
 # changed since its capture has no entry here until it is captured again.
 TRAFFIC_PER_VECTOR = {
-    "16x16-16qam-sd-learned": ((226.345216e6 + 6.197504e6) / 30000,
+    "16x16-16qam-sd-learned": ((225.386240e6 + 6.145024e6) / 30000,
                                "ncu capture of sd_group_kernel, 30,000 vectors of the learned 16x16 sweep "
                                "(profiles/sd_group_kernel_16x16_16qam_sweep_30k.md), scaled by vectors"),
     "100x100-64qam-hybrid32-learned": ((517.457664e6 + 4.140800e6) / 2000,
