@@ -16,26 +16,38 @@
 // level and then pops, descends or reports a leaf, without branches: the
 // shared-memory operands of both outcomes (the R column and residuals of a
 // descent, the parent's saved state of a pop) are loaded first, independently
-// of the child chosen, so their latency overlaps the choice; the zig-zag
-// cursors are kept as floats, so choosing the child and forming its PAM level
-// need no conversions.  Rare events (a leaf, the end of a task, work to
-// fetch) raise a flag that one warp vote per pass turns into a slow path.
+// of the child chosen, so their latency overlaps the choice.  A child inside
+// the sphere is a visited node; the pass also evaluates that node's first
+// child (the PAM index nearest u), and when it lies outside the sphere, so do
+// all the others and the group does not descend.  The new level's
+// interference c_{i-1} = z_{i-1} - R_{i-1,i} a_i comes from row i - 1 of the
+// R and residual columns, which every lane of the group loads (after a warp
+// barrier: only the row's owner wrote the residual), not from a shuffle at
+// the end of the residual update.  The zig-zag cursors and the current path
+// are kept as floats, so choosing a child, forming its PAM level and
+// recording it need no conversions.  Passes run kPassesPerVote at a time;
+// between them one warp vote decides the rare events (a leaf, the end of a
+// task, work to fetch, the periodic check), and a group whose pass raised one
+// sits out the rest of the passes until then.
 //
 // Shared memory.  Per group (one vector's task at a time): the vector's FP32
-// R (column-packed), the residual stack z, the per-level state {parent
-// partial distance, c_i, u_i, R_ii}, the zig-zag cursors, {R_ii, 1 / (2 alpha
-// R_ii)}, the current path, and up to kCand leaf candidates of the running
-// task.  The four groups of a warp are interleaved element by element
-// (WarpLayout), so their lanes always touch disjoint banks, whichever levels
-// their trees are at.  Every value a lane reads from its group's state it
-// either wrote itself (all lanes of a group write the same level state and
-// path entries) or reads after a warp barrier; residual rows are lane-owned.
+// R and the residual stack z, both with the columns in descending order
+// (zoff: rows a lane writes past a column's end land in deeper columns), the
+// per-level state {parent partial distance, c_i, zig-zag cursors},
+// {R_ii, 1 / (2 alpha R_ii)}, the current path, and up to kCand leaf
+// candidates of the running task.  The four groups of a warp are
+// interleaved element by element (WarpLayout), so their lanes always touch
+// disjoint banks, whichever levels their trees are at.  Every value a lane
+// reads from its group's state it either wrote itself (all lanes of a group
+// write the same level state and path entries) or reads after a warp
+// barrier; residual rows are lane-owned.
 //
 // Each residual is the same FP32 FMA chain in the same order as in sd.cu
 // (z_r = ybar_r - sum_{j > i} R_rj x_j, j from n-1 down), and each PAM level
 // the same product (2k - (P-1)) alpha, so every partial distance, pruning
 // decision and visited-node count of a sequential search equals the warp
-// kernel's.
+// kernel's (a node not entered because its first child is outside the
+// sphere is counted, as is that child's evaluation).
 //
 // Work.  A task is a tree node of one vector (rows above it fixed), with the
 // queue records and per-vector state of sd.cu.  Fresh vectors come first, in
@@ -52,8 +64,9 @@
 // top-most open level (at least kMinSplitLevel rows above the leaves); from
 // then on the vector's radius is shared through atomicMin on its FP32 bits,
 // its tasks merge their candidates into the vector's list under its lock,
-// and the task that finishes last re-scores that list.  An empty sphere
-// doubles the radius (r^2 <- 2 r^2) and searches the root again.
+// and the task that finishes last re-scores that list.  A search with a
+// node budget does not split (the budget is an exact cap per vector).  An
+// empty sphere doubles the radius (r^2 <- 2 r^2) and searches the root again.
 //
 // Waiting.  A group with a ticket looks at its slot every 16 passes while
 // its warp has busy groups; a warp whose groups all wait polls the slots
