@@ -21,9 +21,11 @@ torch.distributed.run, one rank per GPU, each rank detecting its own shard.
 from __future__ import annotations
 
 import argparse
+import hashlib
 import json
 import math
 import os
+import re
 import statistics
 import subprocess
 import sys
@@ -79,16 +81,50 @@ DEFAULT_WORKLOAD = "16x16-16qam-sd-learned"
 METRIC = "decoded vectors/s at matched BER (16x16 16QAM, 100x100 64QAM), learned vs plain"
 # DRAM bytes (read + write) of the dominant kernel per vector, from one ncu
 # capture of the same kernel on a smaller run of the same workload (traffic
-# grows with the number of vectors), with the capture it comes from.  A kernel
-# changed since its capture has no entry here until it is captured again.
+# grows with the number of vectors), with the capture it comes from and the
+# code hash (code_hash: comments and spacing aside) of the kernel's sources
+# it was taken on.  When the sources no longer hash to that value, the line
+# reports no traffic until the kernel is captured again.
+KERNEL_SOURCES = {
+    "16x16-16qam-sd-learned": ("sd_group.cu", "sd_common.cuh", "mdx_internal.cuh"),
+    "100x100-64qam-hybrid32-learned": ("kbest.cu", "warp_kbest.cuh", "mdx_internal.cuh"),
+}
 TRAFFIC_PER_VECTOR = {
     "16x16-16qam-sd-learned": ((225.386240e6 + 6.145024e6) / 30000,
                                "ncu capture of sd_group_kernel, 30,000 vectors of the learned 16x16 sweep "
-                               "(profiles/sd_group_kernel_16x16_16qam_sweep_30k.md), scaled by vectors"),
+                               "(profiles/sd_group_kernel_16x16_16qam_sweep_30k.md), scaled by vectors",
+                               "c3df0095b257f5bc"),
     "100x100-64qam-hybrid32-learned": ((517.457664e6 + 4.140800e6) / 2000,
                                        "ncu capture of hybrid_kernel, 2,000 vectors of the learned 100x100 "
-                                       "workload (profiles/hybrid_kernel_100x100_64qam_2k.md), scaled by vectors"),
+                                       "workload (profiles/hybrid_kernel_100x100_64qam_2k.md), scaled by vectors",
+                                       "fbe258b0bd5146e6"),
 }
+
+
+def code_hash(files, csrc=None):
+    """sha256 (first 16 hex digits) of the given kernel sources with comments
+    removed and white space collapsed, so that a comment edit keeps a
+    capture's figures and a code change drops them."""
+    csrc = csrc or os.path.join(ROOT, "paper_2002_09561_gb300", "csrc")
+    h = hashlib.sha256()
+    for f in files:
+        with open(os.path.join(csrc, f)) as fh:
+            text = fh.read()
+        text = re.sub(r"/\*.*?\*/", " ", text, flags=re.S)
+        text = re.sub(r"//[^\n]*", " ", text)
+        h.update(" ".join(text.split()).encode())
+    return h.hexdigest()[:16]
+
+
+def traffic_per_vector(workload):
+    """(bytes per vector, source) of the workload's capture if the kernel's
+    sources are still the ones it was taken on, else (None, why)."""
+    tpv = TRAFFIC_PER_VECTOR.get(workload)
+    if not tpv:
+        return None, "no capture of the current kernel"
+    if code_hash(KERNEL_SOURCES[workload]) != tpv[2]:
+        return None, f"the kernel changed since its capture ({tpv[1]})"
+    return tpv[0], tpv[1]
 FP32_LANES_PER_SM = 128  # FP32 FMA lanes per SM (4 sub-partitions x 32)
 
 
@@ -689,13 +725,13 @@ def search_roofline(workload, algo, stats, search_ms, calls, qr_ms, sms, probe, 
     flops = float(stats[:, 4].sum())
     per_launch_s = (search_ms / max(calls, 1)) / 1e3
     achieved = flops / per_launch_s / 1e12 if per_launch_s > 0 else 0.0
-    tpv = TRAFFIC_PER_VECTOR.get(workload)
+    tpv, tsrc = traffic_per_vector(workload)
     nodes = float(stats[:, 0].sum())
     return {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
             "measured_fma_peak": probe["fp32_fma_tflops"], "frac_of_measured": achieved / probe["fp32_fma_tflops"],
-            "traffic": tpv[0] * B if tpv else None,
+            "traffic": tpv * B if tpv else None,
             "traffic_unit": "bytes per launch (dram read + write)" if tpv else None,
-            "traffic_source": tpv[1] if tpv else "no capture of the current kernel",
+            "traffic_source": tsrc,
             "kernel": f"{algo} search", "search_ms_per_launch": 1e3 * per_launch_s,
             "qr_ms_per_launch": qr_ms / max(calls, 1),
             "nodes_per_s": nodes / per_launch_s if per_launch_s > 0 else None,
