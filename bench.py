@@ -94,10 +94,10 @@ TRAFFIC_PER_VECTOR = {
                                "ncu capture of sd_group_kernel, 30,000 vectors of the learned 16x16 sweep "
                                "(profiles/sd_group_kernel_16x16_16qam_sweep_30k.md), scaled by vectors",
                                "c3df0095b257f5bc"),
-    "100x100-64qam-hybrid32-learned": ((517.457664e6 + 4.140800e6) / 2000,
+    "100x100-64qam-hybrid32-learned": ((516.954880e6 + 4.081664e6) / 2000,
                                        "ncu capture of hybrid_kernel, 2,000 vectors of the learned 100x100 "
                                        "workload (profiles/hybrid_kernel_100x100_64qam_2k.md), scaled by vectors",
-                                       "fbe258b0bd5146e6"),
+                                       "e4500e2afb5bc28e"),
 }
 
 
