@@ -8,9 +8,9 @@
 //              incremental partial distances (Eq. inc), one warp walking the
 //              whole tree: lanes own rows, the residual of every row below the
 //              current level sits in a stack zs[level][row], so a descent
-//              costs one FMA per lower row and the next interference is the
-//              owner lane's value broadcast by a shuffle (the same node step as
-//              the split-task decoder, without the task queue);
+//              costs one FMA per lower row, every lane forms the next
+//              interference from row i - 1 itself, and a node whose nearest
+//              child is outside the sphere is counted but not entered;
 //   K-best     Sec. VI, selection of the K best children per level by a
 //              warp tournament over the survivors' Schnorr-Euchner child
 //              streams (warp_kbest.cuh).
@@ -238,6 +238,26 @@ __device__ void sd_request(const MixedArgs& g, const MixedReq& q, int r, const f
       }
       // descend into child k: push level i, update the residuals of the rows below
       const float av = (float)(2 * k - (P - 1)) * alpha;
+      const float* zin = zs + col_off(i);
+      const float* rc = Rc + col_off(i);
+      // the next level's interference, computed by every lane from row i - 1
+      // (the same FMA as that row's residual below; the column was written
+      // before the last warp barrier), and the new level's first child, the
+      // PAM index nearest u (sorted order only): outside the sphere it rules
+      // out every child, so the node is counted with that one evaluation and
+      // the search goes on at level i
+      const float cnext = fmaf(-rc[i - 1], av, zin[i - 1]);
+      const float unext = fmaf(cnext, lv_rinv[i - 1], uoff);
+      const int lonext = NAT ? 0 : min(max((int)ceilf(unext - 0.5f), 0), P - 1);
+      if (!NAT) {
+        const float d1 = fmaf(-lv_rii[i - 1], (float)(2 * lonext - (P - 1)) * alpha, cnext);
+        if (!(fmaf(d1, d1, ped) < bnd)) {
+          ++nodes;
+          ++peds;
+          flops += 2 * (n - i) + 4 * P;
+          continue;
+        }
+      }
       if (lane == 0) {
         lv_ped[i] = ped_par;
         lv_c[i] = c;
@@ -245,26 +265,19 @@ __device__ void sd_request(const MixedArgs& g, const MixedReq& q, int r, const f
         lv_lohi[i] = (lo + 1) | (hi << 16);
         xs[i] = (uint8_t)k;
       }
-      const float* zin = zs + col_off(i);
       float* zout = zs + col_off(i - 1);
-      const float* rc = Rc + col_off(i);
-      float cnext = 0.0f;
 #pragma unroll
       for (int t = 0; t < ROWS; ++t) {
         const int rr = lane + 32 * t;
-        if (rr < i) {
-          const float z = fmaf(-rc[rr], av, zin[rr]);
-          zout[rr] = z;
-          if (rr == i - 1) cnext = z;
-        }
+        if (rr < i) zout[rr] = fmaf(-rc[rr], av, zin[rr]);
       }
       --i;
-      c = __shfl_sync(0xffffffffu, cnext, i & 31);
       __syncwarp();
+      c = cnext;
       ped_par = ped;
       rii = lv_rii[i];
-      u = fmaf(c, lv_rinv[i], uoff);
-      lo = NAT ? 0 : min(max((int)ceilf(u - 0.5f), 0), P - 1);
+      u = unext;
+      lo = lonext;
       hi = NAT ? P : lo + 1;
       ++nodes;
       flops += 2 * (n - 1 - i) + 4 * P;

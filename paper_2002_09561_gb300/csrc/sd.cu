@@ -25,8 +25,10 @@
 // node at level i (rows n-1..i+1 fixed) the residual of every lower row,
 //   z_r = ybar_r - sum_{j > i} R_rj x_j   (r <= i),
 // is kept in a shared-memory stack zs[level i][r]; descending into child
-// x_i = a costs one FMA per row below (z_r -= R_ri a), and the interference
-// of the next row is the owner lane's updated z, broadcast by one shuffle.
+// x_i = a costs one FMA per row below (z_r -= R_ri a), and every lane forms
+// the interference of the next row itself from row i - 1 (read after the
+// warp barrier that ends each descent); a node whose nearest child is
+// outside the sphere is counted but not entered.
 // Each partial distance is one FMA chain in a fixed order (j = n-1 down to
 // i+1), identical whether a node is reached by descent or rebuilt from a
 // task's path.  The control state of the current level is warp-uniform and
@@ -342,31 +344,45 @@ __global__ void __launch_bounds__(kWarpsMax * 32, ROWS == 1 ? MDX_SD_MIN_BLOCKS_
       }
       // descend into child k: push level i, update the residuals of the rows below
       const float av = (float)(2 * k - (P - 1)) * alpha;
+      const float* zin = zs + col_off(i);
+      const float* rc = Rc + col_off(i);
+      // the next level's interference, computed by every lane from row i - 1
+      // (the same FMA as that row's residual below; the column was written
+      // before the last warp barrier), and the new level's first child, the
+      // PAM index nearest u: outside the sphere it rules out every child, so
+      // the node is counted with that one evaluation and the search goes on
+      // at level i
+      const float cnext = fmaf(-rc[i - 1], av, zin[i - 1]);
+      const float2 rl = lv_r[i - 1];
+      const float unext = fmaf(cnext, rl.y, uoff);
+      const int lonext = min(max((int)ceilf(unext - 0.5f), 0), P - 1);
+      {
+        const float d1 = fmaf(-rl.x, (float)(2 * lonext - (P - 1)) * alpha, cnext);
+        if (!(fmaf(d1, d1, ped) < bnd)) {
+          ++n32;
+          ++p32;
+          lsum += i - 1;
+          ++task_nodes;
+          continue;
+        }
+      }
       if (lane == 0) {
         lv_st[i] = make_float4(ped_par, c, u, __int_as_float((lo + 1) | (hi << 16)));
         xs[i] = (uint8_t)k;
       }
-      const float* zin = zs + col_off(i);
       float* zout = zs + col_off(i - 1);
-      const float* rc = Rc + col_off(i);
-      float cnext = 0.0f;
 #pragma unroll
       for (int t = 0; t < ROWS; ++t) {
         const int r = lane + 32 * t;
-        if (r < i) {
-          const float z = fmaf(-rc[r], av, zin[r]);
-          zout[r] = z;
-          if (r == i - 1) cnext = z;
-        }
+        if (r < i) zout[r] = fmaf(-rc[r], av, zin[r]);
       }
       --i;
-      c = __shfl_sync(0xffffffffu, cnext, i & 31);
       __syncwarp();
+      c = cnext;
       ped_par = ped;
-      const float2 rl = lv_r[i];
       rii = rl.x;
-      u = fmaf(c, rl.y, uoff);
-      lo = min(max((int)ceilf(u - 0.5f), 0), P - 1);
+      u = unext;
+      lo = lonext;
       hi = lo + 1;
       ++n32;
       lsum += i;
