@@ -108,6 +108,30 @@ def test_hybrid_100x100_64qam_plain_and_learned_against_oracle(env, hybrid_ctx, 
         assert (vst != mdx.MDX_V_SINGULAR).all()
 
 
+def test_hybrid_100x100_host_buffers_in_chunks_equal_the_device_path(env):
+    """400 vectors of 100x100 (64 MB of H): with host buffers the inputs are
+    copied in two chunks and each chunk's blocked QR runs on its own slice
+    of the workspace; the hybrid's answers are those of the device path, bit
+    for bit."""
+    torch, mdx = env
+    B = 400
+    ctx = mdx.Context(0, max_batch=B, max_n_rx=100, max_n_tx=100)
+    try:
+        w = wl.generate(7200, B, 100, 100, 64, 28.0)
+        p = mdx.make_params(100, 100, 64, radius="paper", K=32, depth=4)
+        sym_d, met_d, vst_d, _ = _detect(torch, mdx, "hybrid", ctx, p, _device(torch, w))
+        pin = lambda a: torch.from_numpy(a).pin_memory().numpy()  # noqa: E731
+        sym = torch.empty((B, 100), dtype=torch.uint8).pin_memory().numpy()
+        met = torch.empty(B, dtype=torch.float64).pin_memory().numpy()
+        vst = torch.empty(B, dtype=torch.int32).pin_memory().numpy()
+        mdx.detect_host("hybrid", ctx, p, pin(w["H"]), pin(w["y"]), pin(w["noise_var"]), sym, met, vst)
+        np.testing.assert_array_equal(sym, sym_d)
+        np.testing.assert_array_equal(met, met_d)
+        np.testing.assert_array_equal(vst, vst_d)
+    finally:
+        ctx.close()
+
+
 # ------------------------------------------------------------- 16x16 16-QAM exact SD
 
 
