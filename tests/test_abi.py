@@ -70,6 +70,14 @@ def test_null_context_is_rejected(libmdx):
         assert f(None, ctypes.byref(p), 1, *([None] * 8)) == -1
 
 
+def test_measure_peaks_rejects_bad_arguments(libmdx):
+    f = libmdx.mdx_measure_peaks
+    f.argtypes = [ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p]
+    out = (ctypes.c_double * 4)()
+    assert f(0, None, None) == -1  # no output array
+    assert f(-1, ctypes.cast(out, ctypes.c_void_p), None) == -1  # no such device
+
+
 def test_no_cpu_fallback_without_library(tmp_path, monkeypatch):
     from paper_2002_09561_gb300 import mdx
 

@@ -205,3 +205,18 @@ def test_budget_above_the_split_threshold(env):
     assert (met[hit] >= ref["metric"][hit] * (1 - 1e-9)).all()
     assert (st[:, 0] <= budget).all()
     assert split["donated"] == 0
+
+
+def test_measure_peaks_are_plausible(env):
+    """The probes behind the bench's roofline denominators: FP32 FMA, FP64
+    FMA and FP64 MMA rates within a factor of two of what this GPU's units
+    give at their clocks (about 80, 1.26 and 1.26 TFLOP/s), the FP32 rate far
+    above the FP64 ones."""
+    from paper_2002_09561_gb300 import mdx
+
+    pk = mdx.measure_peaks(0)
+    print("measured peaks", pk)
+    assert 40.0 < pk["fp32_fma_tflops"] < 160.0
+    assert 0.6 < pk["fp64_fma_tflops"] < 2.6
+    assert 0.6 < pk["fp64_mma_tflops"] < 2.6
+    assert pk["fp32_fma_tflops"] > 20 * pk["fp64_fma_tflops"]
