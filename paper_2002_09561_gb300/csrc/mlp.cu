@@ -538,19 +538,34 @@ struct RadiusArgs {
 // takes the PAM index of largest logit o[1 + r P + k] (ties to the lower k),
 // scaled by 1 + 2^-16 so that x^ stays inside the sphere under the search's
 // own FP32 evaluation.
-__global__ void radius_kernel(RadiusArgs a) {
-  const int v = blockIdx.x * blockDim.x + threadIdx.x;
-  if (v >= a.batch) return;
-  const float* o = a.O + (size_t)v * a.DO;
+// Eight lanes per vector (four vectors per warp): the group's lanes take
+// the rows' argmaxes and residuals r = g, g + 8, ... (consecutive lanes read
+// consecutive entries of each R column), and the distance is summed over the
+// rows in order on every lane of the group, so that each residual is the same
+// FMA chain (columns r..n-1) and the distance the same sum (rows 0..n-1) as
+// one thread computing the whole vector.
+constexpr int kRadiusLanes = 8;
+constexpr int kRadiusMaxN = 2 * kFullFeaturesMaxTx;  // the ordering head's rows at most
+constexpr int kRadiusThreads = 128;
+
+__global__ void __launch_bounds__(kRadiusThreads) radius_kernel(RadiusArgs a) {
+  constexpr int G = kRadiusLanes, RPL = kRadiusMaxN / G;
+  __shared__ uint8_t xh_all[kRadiusThreads / G][kRadiusMaxN];
+  const int lane = threadIdx.x & 31, gl = lane & (G - 1), lead = lane & ~(G - 1);
+  const int grp = threadIdx.x / G;
+  const int v = (blockIdx.x * kRadiusThreads + threadIdx.x) / G;
+  const bool act = v < a.batch;
+  const int vv = act ? v : 0;  // lanes past the batch follow along for the shuffles
   double r2;
-  if (a.learned) r2 = a.nv[v] * exp((double)o[0]);
-  else if (a.base_mode == RADIUS_PAPER) r2 = (double)a.n_rx * a.n_tx * a.nv[v];
+  if (a.learned) r2 = a.nv[vv] * exp((double)a.O[(size_t)vv * a.DO]);
+  else if (a.base_mode == RADIUS_PAPER) r2 = (double)a.n_rx * a.n_tx * a.nv[vv];
   else if (a.base_mode == RADIUS_VALUE) r2 = a.base_value;
   else r2 = INFINITY;
   if (a.order) {
     const int n = a.n, P = a.P;
-    uint8_t xh[64];
-    for (int r = 0; r < n; ++r) {
+    const float* o = a.O + (size_t)vv * a.DO;
+    uint8_t* xh = xh_all[grp];
+    for (int r = gl; r < n; r += G) {
       int best = 0;
       float bl = o[1 + r * P];
       for (int k = 1; k < P; ++k)
@@ -560,18 +575,30 @@ __global__ void radius_kernel(RadiusArgs a) {
         }
       xh[r] = (uint8_t)best;
     }
-    const float* R = a.R32 + (size_t)v * tri_stride32(n);
-    const float* yb = a.yb32 + (size_t)v * vec_stride32(n);
+    __syncwarp();
+    const float* R = a.R32 + (size_t)vv * tri_stride32(n);
+    const float* yb = a.yb32 + (size_t)vv * vec_stride32(n);
+    float e[RPL];
+#pragma unroll
+    for (int t = 0; t < RPL; ++t) {
+      const int r = gl + G * t;
+      e[t] = 0.0f;
+      if (r < n) {
+        float et = yb[r];
+        for (int c = r; c < n; ++c) et = fmaf(-R[col_off(c) + r], (float)(2 * (int)xh[c] - (P - 1)) * a.alpha, et);
+        e[t] = et;
+      }
+    }
     float d = 0.0f;
-    for (int r = 0; r < n; ++r) {
-      float e = yb[r];
-      for (int c = r; c < n; ++c) e = fmaf(-R[col_off(c) + r], (float)(2 * (int)xh[c] - (P - 1)) * a.alpha, e);
-      d = fmaf(e, e, d);
+#pragma unroll
+    for (int r = 0; r < kRadiusMaxN; ++r) {
+      const float er = __shfl_sync(0xffffffffu, e[r / G], lead + (r % G));
+      if (r < n) d = fmaf(er, er, d);
     }
     const double cap = (double)d * (1.0 + 1.0 / 65536.0);
     if (cap > 0.0 && cap < r2) r2 = cap;
   }
-  a.r2[v] = (float)r2;
+  if (act && gl == 0) a.r2[v] = (float)r2;
 }
 
 int grid_for(long long total, int threads) {
@@ -811,7 +838,8 @@ cudaError_t mlp_radius(MlpState* s, int batch, const double* nv, bool learned, b
   a.R32 = R32;
   a.yb32 = yb32;
   a.r2 = s->r2;
-  radius_kernel<<<(batch + 127) / 128, 128, 0, st>>>(a);
+  radius_kernel<<<(int)(((long long)batch * kRadiusLanes + kRadiusThreads - 1) / kRadiusThreads), kRadiusThreads, 0,
+                  st>>>(a);
   return cudaGetLastError();
 }
 
