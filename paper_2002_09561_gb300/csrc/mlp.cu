@@ -353,22 +353,25 @@ constexpr int kH = 256;
 __global__ void mlp_features_kernel(int batch, int rows, int n, int D0, const float* __restrict__ R32,
                                     const float* __restrict__ yb32, const double* __restrict__ nv,
                                     __nv_bfloat16* X, __nv_bfloat16* Xt, float* F) {
-  const long long total = (long long)rows * D0;
+  // a warp per vector row, its lanes over the features (no index division)
   const int T = n * (n + 1) / 2;
   const int ts = tri_stride32(n), vs = vec_stride32(n);
-  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
-       e += (long long)gridDim.x * blockDim.x) {
-    const int v = (int)(e / D0), f = (int)(e % D0);
-    float x = 0.0f;
-    if (v < batch) {
-      if (f < T) x = R32[(size_t)v * ts + f];
-      else if (f < T + n) x = yb32[(size_t)v * vs + (f - T)];
-      else if (f == T + n) x = (float)(-10.0 * log10(nv[v]) / 30.0);
+  const int lane = threadIdx.x & 31;
+  const int w0 = (int)((blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5);
+  const int nw = (int)(((long long)gridDim.x * blockDim.x) >> 5);
+  for (int v = w0; v < rows; v += nw) {
+    for (int f = lane; f < D0; f += 32) {
+      float x = 0.0f;
+      if (v < batch) {
+        if (f < T) x = R32[(size_t)v * ts + f];
+        else if (f < T + n) x = yb32[(size_t)v * vs + (f - T)];
+        else if (f == T + n) x = (float)(-10.0 * log10(nv[v]) / 30.0);
+      }
+      const __nv_bfloat16 b = __float2bfloat16(x);
+      X[(size_t)v * D0 + f] = b;
+      if (Xt) Xt[(size_t)f * rows + v] = b;
+      if (F && v < batch) F[(size_t)v * D0 + f] = x;
     }
-    const __nv_bfloat16 b = __float2bfloat16(x);
-    X[(size_t)v * D0 + f] = b;
-    if (Xt) Xt[(size_t)f * rows + v] = b;
-    if (F && v < batch) F[(size_t)v * D0 + f] = x;
   }
 }
 
@@ -733,7 +736,7 @@ cudaError_t mlp_features(MlpState* s, int batch, int rows, const float* R32, con
         batch, rows, s->n, s->P, alpha, s->D0, R32, yb32, nv, s->X, train ? s->Xt : nullptr, F);
     return cudaGetLastError();
   }
-  mlp_features_kernel<<<grid_for((long long)rows * s->D0, 256), 256, 0, st>>>(
+  mlp_features_kernel<<<grid_for((long long)rows * 32, 256), 256, 0, st>>>(
       batch, rows, s->n, s->D0, R32, yb32, nv, s->X, train ? s->Xt : nullptr, F);
   return cudaGetLastError();
 }
