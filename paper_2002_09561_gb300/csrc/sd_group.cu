@@ -82,8 +82,13 @@ namespace {
 
 constexpr int kGroupN = 32;     // largest n of this kernel
 // Lanes per vector.  Eight (four vectors per warp, rows g, g + 8, g + 16,
-// g + 24 of lane g) measured faster than four on the 16x16 16-QAM batches.
-constexpr int kGroupLanes = 8;
+// g + 24 of lane g) measured faster than four on the 16x16 16-QAM batches
+// (four lanes: fewer instructions per node, but half the warps per SM for
+// the same trees, which exposes each pass's dependent chain).
+#ifndef MDX_SDG_LANES
+#define MDX_SDG_LANES 8
+#endif
+constexpr int kGroupLanes = MDX_SDG_LANES;
 // warps per CTA: as many as let five CTAs share an SM's 228 KB
 template <int G>
 __host__ __device__ constexpr int group_warps() {
@@ -91,7 +96,12 @@ __host__ __device__ constexpr int group_warps() {
 }
 constexpr int kTri = 528;       // column-packed triangle of n = 32
 // node-step passes per vote of the slow paths (divides 16 and kSplitEvery)
-constexpr int kPassesPerVote = 8;
+#ifndef MDX_SDG_PASSES
+#define MDX_SDG_PASSES 8
+#endif
+constexpr int kPassesPerVote = MDX_SDG_PASSES;
+static_assert(kPassesPerVote <= 16 && 16 % kPassesPerVote == 0, "the ticket check cadence");
+static_assert(kSplitEvery % kPassesPerVote == 0, "the split check cadence");
 
 // R and the residual stack in shared memory: column c (rows 0..c) starts at
 // zoff(c) = kTri - (c + 1)(c + 2) / 2, the columns in descending order.  A
