@@ -240,30 +240,52 @@ __global__ void __launch_bounds__(128, 1) tc_gemm_kernel(const __grid_constant__
       TMEM_LD32(taddr, r);
       asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
       const int col0 = n0 + c;
+      // the thread's row, 32 columns: 16-byte loads and stores (the launcher
+      // checks the alignment of every epilogue pointer and leading dimension)
       if (epi.mode == TC_F32) {
-        float* o = epi.outf + (size_t)row * epi.ldf + col0;
+        float4* o = reinterpret_cast<float4*>(epi.outf + (size_t)row * epi.ldf + col0);
+        const float4* b = epi.bias ? reinterpret_cast<const float4*>(epi.bias + col0) : nullptr;
 #pragma unroll
-        for (int j = 0; j < 32; ++j) {
-          float v = __uint_as_float(r[j]);
-          if (epi.bias) v += epi.bias[col0 + j];
-          o[j] = v;
+        for (int q = 0; q < 8; ++q) {
+          float4 v = make_float4(__uint_as_float(r[4 * q]), __uint_as_float(r[4 * q + 1]),
+                                 __uint_as_float(r[4 * q + 2]), __uint_as_float(r[4 * q + 3]));
+          if (b) {
+            const float4 bb = b[q];
+            v.x += bb.x;
+            v.y += bb.y;
+            v.z += bb.z;
+            v.w += bb.w;
+          }
+          o[q] = v;
         }
       } else {
-        __nv_bfloat16 vb[32];
+        __align__(16) __nv_bfloat16 vb[32];
+        if (epi.mode == TC_BIAS_RELU) {
+          const float4* b = reinterpret_cast<const float4*>(epi.bias + col0);
 #pragma unroll
-        for (int j = 0; j < 32; ++j) {
-          float v = __uint_as_float(r[j]);
-          if (epi.mode == TC_BIAS_RELU) {
-            v = fmaxf(v + epi.bias[col0 + j], 0.0f);
-          } else {
-            const float mk = __bfloat162float(epi.mask[(size_t)row * epi.ldm + col0 + j]);
-            v = mk > 0.0f ? v : 0.0f;
+          for (int q = 0; q < 8; ++q) {
+            const float4 bb = b[q];
+            vb[4 * q] = __float2bfloat16(fmaxf(__uint_as_float(r[4 * q]) + bb.x, 0.0f));
+            vb[4 * q + 1] = __float2bfloat16(fmaxf(__uint_as_float(r[4 * q + 1]) + bb.y, 0.0f));
+            vb[4 * q + 2] = __float2bfloat16(fmaxf(__uint_as_float(r[4 * q + 2]) + bb.z, 0.0f));
+            vb[4 * q + 3] = __float2bfloat16(fmaxf(__uint_as_float(r[4 * q + 3]) + bb.w, 0.0f));
           }
-          vb[j] = __float2bfloat16(v);
-        }
-        __nv_bfloat16* o = epi.outb + (size_t)row * epi.ldb + col0;
+        } else {
+          const uint4* m = reinterpret_cast<const uint4*>(epi.mask + (size_t)row * epi.ldm + col0);
 #pragma unroll
-        for (int j = 0; j < 32; ++j) o[j] = vb[j];
+          for (int q = 0; q < 4; ++q) {
+            __align__(16) __nv_bfloat16 mk[8];
+            *reinterpret_cast<uint4*>(mk) = m[q];
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+              const float v = __uint_as_float(r[8 * q + j]);
+              vb[8 * q + j] = __float2bfloat16(__bfloat162float(mk[j]) > 0.0f ? v : 0.0f);
+            }
+          }
+        }
+        uint4* o = reinterpret_cast<uint4*>(epi.outb + (size_t)row * epi.ldb + col0);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) o[q] = reinterpret_cast<const uint4*>(vb)[q];
         if (epi.outt) {
 #pragma unroll
           for (int j = 0; j < 32; ++j) epi.outt[(size_t)(col0 + j) * epi.ldt + row] = vb[j];
@@ -333,6 +355,13 @@ cudaError_t tc_gemm(const void* A, int lda, const void* B, int ldb, int M, int N
   if (M % kTM || K % kTK || M <= 0 || N <= 0 || K <= 0) return cudaErrorInvalidValue;
   if ((lda % 8) || (ldb % 8)) return cudaErrorInvalidValue;
   if ((reinterpret_cast<uintptr_t>(A) & 15) || (reinterpret_cast<uintptr_t>(B) & 15)) return cudaErrorInvalidValue;
+  // the epilogue moves 16 bytes at a time along each output row
+  auto misaligned = [](const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15) != 0; };
+  if (epi.mode == TC_F32 && (!epi.outf || misaligned(epi.outf) || epi.ldf % 4)) return cudaErrorInvalidValue;
+  if (epi.mode != TC_F32 && (!epi.outb || misaligned(epi.outb) || epi.ldb % 8)) return cudaErrorInvalidValue;
+  if (epi.mode == TC_BIAS_RELU && (!epi.bias || misaligned(epi.bias))) return cudaErrorInvalidValue;
+  if (epi.mode == TC_F32 && epi.bias && misaligned(epi.bias)) return cudaErrorInvalidValue;
+  if (epi.mode == TC_MASK && (!epi.mask || misaligned(epi.mask) || epi.ldm % 8)) return cudaErrorInvalidValue;
   if (N % 256 == 0) return launch_tc<256>(A, lda, B, ldb, M, N, K, epi, s);
   if (N % 192 == 0) return launch_tc<192>(A, lda, B, ldb, M, N, K, epi, s);
   if (N % 128 == 0) return launch_tc<128>(A, lda, B, ldb, M, N, K, epi, s);
