@@ -90,10 +90,10 @@ KERNEL_SOURCES = {
     "100x100-64qam-hybrid32-learned": ("kbest.cu", "warp_kbest.cuh", "mdx_internal.cuh"),
 }
 TRAFFIC_PER_VECTOR = {
-    "16x16-16qam-sd-learned": ((225.386240e6 + 6.145024e6) / 30000,
+    "16x16-16qam-sd-learned": ((225.208576e6 + 6.209024e6) / 30000,
                                "ncu capture of sd_group_kernel, 30,000 vectors of the learned 16x16 sweep "
                                "(profiles/sd_group_kernel_16x16_16qam_sweep_30k.md), scaled by vectors",
-                               "1209af741397d327"),
+                               "41cf9bf6e4c91aa7"),
     "100x100-64qam-hybrid32-learned": ((516.954880e6 + 4.081664e6) / 2000,
                                        "ncu capture of hybrid_kernel, 2,000 vectors of the learned 100x100 "
                                        "workload (profiles/hybrid_kernel_100x100_64qam_2k.md), scaled by vectors",

@@ -15,20 +15,28 @@
 // The node step.  Each pass evaluates one child of every busy group's current
 // level and then pops, descends or reports a leaf, without branches: the
 // shared-memory operands of both outcomes (the R column and residuals of a
-// descent, the parent's saved state of a pop) are loaded first, independently
-// of the child chosen, so their latency overlaps the choice.  A child inside
-// the sphere is a visited node; the pass also evaluates that node's first
-// child (the PAM index nearest u), and when it lies outside the sphere, so do
-// all the others and the group does not descend.  The new level's
+// descent, the saved state of the level a pop returns to) are loaded first,
+// independently of the child chosen, so their latency overlaps the choice.  A
+// child inside the sphere is a visited node; the pass also evaluates that
+// node's first child (the PAM index nearest u), and when it lies outside the
+// sphere, so do all the others and the group does not descend.  It evaluates
+// the child's next sibling as well: outside the sphere (the bound only
+// shrinks, so it stays outside), no pass returns to the level, and a pop
+// jumps over every such level to the nearest one with a sibling left inside
+// (each level keeps that return level).  Almost every pass then visits a
+// node: a failing evaluation no longer costs a pass of its own, nor does the
+// climb back through levels with nothing left.  The new level's
 // interference c_{i-1} = z_{i-1} - R_{i-1,i} a_i comes from row i - 1 of the
 // R and residual columns, which every lane of the group loads (after a warp
 // barrier: only the row's owner wrote the residual), not from a shuffle at
 // the end of the residual update.  The zig-zag cursors and the current path
 // are kept as floats, so choosing a child, forming its PAM level and
-// recording it need no conversions.  Passes run kPassesPerVote at a time;
-// between them one warp vote decides the rare events (a leaf, the end of a
-// task, work to fetch, the periodic check), and a group whose pass raised one
-// sits out the rest of the passes until then.
+// recording it need no conversions.  Passes run kPassesPerVote at a time,
+// from one copy of the node step in a loop (an unrolled copy per pass
+// overflows the instruction cache); between them one warp vote decides the
+// rare events (a leaf, the end of a task, work to fetch, the periodic check),
+// and a group whose pass raised one sits out the rest of the passes until
+// then.
 //
 // Shared memory.  Per group (one vector's task at a time): the vector's FP32
 // R and the residual stack z, both with the columns in descending order
@@ -47,7 +55,8 @@
 // the same product (2k - (P-1)) alpha, so every partial distance, pruning
 // decision and visited-node count of a sequential search equals the warp
 // kernel's (a node not entered because its first child is outside the
-// sphere is counted, as is that child's evaluation).
+// sphere is counted, as is that child's evaluation, and so is the failing
+// evaluation of a sibling that ends its level).
 //
 // Work.  A task is a tree node of one vector (rows above it fixed), with the
 // queue records and per-vector state of sd.cu.  Fresh vectors come first, in
@@ -95,11 +104,19 @@ __host__ __device__ constexpr int group_warps() {
   return G >= 8 ? 2 : 1;
 }
 constexpr int kTri = 528;       // column-packed triangle of n = 32
-// node-step passes per vote of the slow paths (divides 16 and kSplitEvery)
+// node-step passes per vote of the slow paths (divides 16 and kSplitEvery);
+// a group that raised an event sits out the rest of them
 #ifndef MDX_SDG_PASSES
-#define MDX_SDG_PASSES 8
+#define MDX_SDG_PASSES 16
 #endif
 constexpr int kPassesPerVote = MDX_SDG_PASSES;
+// copies of the node step in the pass loop: one.  The loop body must stay
+// small enough for the instruction cache; on the 16x16 16-QAM sweep one copy
+// searched in 40.5 ms, two in 43.4 ms, four in 52.7 ms (four passes per vote)
+#ifndef MDX_SDG_UNROLL
+#define MDX_SDG_UNROLL 1
+#endif
+constexpr int kPassUnroll = MDX_SDG_UNROLL;
 static_assert(kPassesPerVote <= 16 && 16 % kPassesPerVote == 0, "the ticket check cadence");
 static_assert(kSplitEvery % kPassesPerVote == 0, "the split check cadence");
 
@@ -122,6 +139,7 @@ __host__ __device__ constexpr int zoff(int c) { return kTri - (((c + 1) * (c + 2
 //                              (u_i = c_i / (2 alpha R_ii) + (P - 1) / 2 and R_ii come from LR)
 //   LR      32 x NG float2     {R_ii, 1 / (2 alpha R_ii)}
 //   XS      32 x NG floats     current path (PAM indices as floats: no conversion on a descent)
+//   RT      32 x NG bytes      return level of each level on the path (where a pop from it goes)
 //   per group: kCand candidate partial distances and kCand x 32 path bytes
 template <int G>
 struct WarpLayout {
@@ -131,7 +149,8 @@ struct WarpLayout {
   static constexpr int ST = Z + (kTri + kGroupN) * NG;
   static constexpr int LR = ST + 4 * kGroupN * NG;
   static constexpr int XS = LR + 2 * kGroupN * NG;
-  static constexpr int CAND = XS + kGroupN * NG;
+  static constexpr int RT = XS + kGroupN * NG;
+  static constexpr int CAND = RT + kGroupN * NG / 4;
   static constexpr int CAND_WORDS = kCand + kCand * kGroupN / 4;  // per group
   static constexpr int WORDS = CAND + NG * CAND_WORDS;
   static_assert(ST % 4 == 0 && LR % 2 == 0, "16- and 8-byte alignment of the level arrays");
@@ -211,6 +230,7 @@ __global__ void __launch_bounds__(group_warps<G>() * 32, MDX_SDG_MIN_BLOCKS) sd_
   float4* STw = reinterpret_cast<float4*>(wbase + L::ST);
   float2* LRw = reinterpret_cast<float2*>(wbase + L::LR);
   float* XSw = wbase + L::XS;
+  uint8_t* RTw = reinterpret_cast<uint8_t*>(wbase + L::RT);
   float* cped = wbase + L::CAND + gid * L::CAND_WORDS;
   uint8_t* cx = reinterpret_cast<uint8_t*>(cped + kCand);
 #define RW(e) Rw[(e) * NG + gid]
@@ -218,6 +238,7 @@ __global__ void __launch_bounds__(group_warps<G>() * 32, MDX_SDG_MIN_BLOCKS) sd_
 #define ST(l) STw[(l) * NG + gid]
 #define LR(l) LRw[(l) * NG + gid]
 #define XS(j) XSw[(j) * NG + gid]
+#define RT(l) RTw[(l) * NG + gid]
 
   // ---- per-group state (identical in the group's lanes)
   int mode = 0;     // 0: needs work, 1: busy, 2: idle (holding a queue ticket, or done)
@@ -225,6 +246,10 @@ __global__ void __launch_bounds__(group_warps<G>() * 32, MDX_SDG_MIN_BLOCKS) sd_
   int staged = -1;  // vector whose R is in this group's shared memory
   int v = -1, top = n - 1, i = n - 1;
   int ci = zoff(n - 1);  // zoff(i), kept with i
+  // the level a pop from level i goes to: the nearest level above i whose
+  // next child was inside the sphere when the path left it (top + 1: none,
+  // the task ends); levels in between have no child left to try
+  int rt = n;
   // the level's state: parent partial distance, interference c_i, u_i (the
   // real-valued PAM index of c_i / R_ii), R_ii, and the zig-zag cursors (the
   // next lower / higher PAM index, as floats; lo < 0 or hi >= P: exhausted)
@@ -249,6 +274,7 @@ __global__ void __launch_bounds__(group_warps<G>() * 32, MDX_SDG_MIN_BLOCKS) sd_
   auto enter_level = [&](int lvl, float pp) {
     i = lvl;
     ci = zoff(lvl);
+    rt = lvl + 1;
     ped_par = pp;
     c = ZW(zoff(lvl) + lvl);
     const float2 rl = LR(lvl);
@@ -912,7 +938,7 @@ __global__ void __launch_bounds__(group_warps<G>() * 32, MDX_SDG_MIN_BLOCKS) sd_
     // outcomes and stall on its resolution every pass).  kPassesPerVote
     // passes run per vote of the slow paths; a group whose pass raised an
     // event (a leaf, the end of its task) sits the rest of them out.
-#pragma unroll
+#pragma unroll kPassUnroll
     for (int sub = 0; sub < kPassesPerVote; ++sub) {
       // rows i - 1 of the R and residual columns are read below by every lane
       // of the group, while only the row's owner wrote the residual (in an
@@ -920,10 +946,10 @@ __global__ void __launch_bounds__(group_warps<G>() * 32, MDX_SDG_MIN_BLOCKS) sd_
       __syncwarp();
       const bool held = sub > 0 && (ev_leaf || ev_done);
       const bool busy = mode == 1 && !held;
-      // ip = n (the root) and im = -1 (a leaf) index past the level arrays
-      // into their neighbours in shared memory; those values are never used
-      // (no pop at the task's top level, no descent from level 0)
-      const int ip = i + 1, im = i - 1;
+      // rt = n (a task at the root) and im = -1 (a leaf) index past the level
+      // arrays into their neighbours in shared memory; those values are never
+      // used (no pop past the task's top level, no descent from level 0)
+      const int im = i - 1;
       const int cm = ci + i + 1;  // zoff(i - 1)
       float rcv[RPL], zinv[RPL];
 #pragma unroll
@@ -934,8 +960,9 @@ __global__ void __launch_bounds__(group_warps<G>() * 32, MDX_SDG_MIN_BLOCKS) sd_
       // row i - 1 of this level's R column and residuals, read by every lane
       // (the next level's interference without a shuffle from its owner)
       const float rim = RW(ci + im), zim = ZW(ci + im);
-      const float4 stp = ST(ip);
-      const float2 lrp = LR(ip);
+      const float4 stp = ST(rt);
+      const float2 lrp = LR(rt);
+      const int rtp = RT(rt);
       const float2 lrn = LR(im);
       const bool has_lo = flo >= 0.0f, has_hi = fhi < Pf;
       const bool has = busy && (has_lo || has_hi);
@@ -948,20 +975,24 @@ __global__ void __launch_bounds__(group_warps<G>() * 32, MDX_SDG_MIN_BLOCKS) sd_
       const float ped = fmaf(d, d, ped_par);
       if (has) ++p32;
       const bool ok = has && ped < bnd;
+      // The child's next sibling in Schnorr-Euchner order, evaluated now with
+      // the same operations as the pass that would take it.  The pruning
+      // bound only shrinks, so a sibling outside the sphere now is outside
+      // then: the level ends with this child, and no pass comes back to it.
+      const bool has_lo2 = flo >= 0.0f, has_hi2 = fhi < Pf;
+      const bool take_lo2 = has_lo2 && (!has_hi2 || fabsf(u - flo) <= fabsf(fhi - u));
+      const float kf2 = take_lo2 ? flo : fhi;
+      const float d2 = fmaf(-rii, fmaf(kf2, 2.0f, -(Pf - 1.0f)) * alpha, c);
+      const bool has2 = has_lo2 || has_hi2;
+      const bool exh = !(has2 && fmaf(d2, d2, ped_par) < bnd);
       const bool deep = ok && i > 0;
+      const bool leaf = ok && i == 0;
       bool visit = deep, bstop = false;  // the child is a visited (branched) node
       if (kBudget) {
         visit = deep && n32 < left32;
         bstop = deep && n32 >= left32;
         budget_hit = budget_hit || bstop;
       }
-      if (!held) {
-        ev_done = busy && ((!ok && i == top) || bstop);
-        ev_leaf = ok && i == 0;
-        leaf_ped = ped;
-        leaf_kf = kf;
-      }
-      const bool pop = busy && !ok && i != top;
       // the new level's residuals (rows 0..i-1 matter; the rest spill into
       // deeper columns)
 #pragma unroll
@@ -972,6 +1003,7 @@ __global__ void __launch_bounds__(group_warps<G>() * 32, MDX_SDG_MIN_BLOCKS) sd_
       if (visit) {
         ST(i) = make_float4(ped_par, c, flo, fhi);
         XS(i) = kf;
+        RT(i) = (uint8_t)rt;
       }
       const float cnew = fmaf(-rim, av, zim);  // the same FMA as row i - 1's residual
       const float unew = fmaf(cnew, lrn.y, uoff);
@@ -981,26 +1013,44 @@ __global__ void __launch_bounds__(group_warps<G>() * 32, MDX_SDG_MIN_BLOCKS) sd_
       // constellation is the PAM index nearest u (the lower one on a tie),
       // and the zig-zag takes it first.  Outside the sphere it rules out
       // every child of the node, so the group does not descend: the node and
-      // that one evaluation are counted, and the next pass goes on with the
-      // next child of level i.  (The stores above, made for a descent, touch
-      // only state that a group at level i never reads.)
+      // that one evaluation are counted, and the group goes on with the next
+      // child of level i, or leaves the level when none is inside.  (The
+      // stores above, made for a descent, touch only state that a group at
+      // level i never reads.)
       const float d1 = fmaf(-lrn.x, fmaf(flonew, 2.0f, -(Pf - 1.0f)) * alpha, cnew);
       const bool enter = fmaf(d1, d1, ped) < bnd;
       const bool desc = visit && enter;
-      ci = desc ? cm : (pop ? ci - (i + 2) : ci);  // zoff(i - 1), zoff(i + 1)
-      i = desc ? im : (pop ? ip : i);
+      // the level is left: its child was outside the sphere (or none was
+      // left), or the child (a leaf, or a node not entered) was the last one
+      // inside
+      const bool leave = busy && (!ok || (exh && (leaf || (visit && !enter))));
+      const bool pop = leave && rt <= top;
+      if (!held) {
+        ev_done = (leave && rt > top) || bstop;
+        ev_leaf = leaf;
+        leaf_ped = ped;
+        leaf_kf = kf;
+      }
+      const int zrt = kTri - (((rt + 1) * (rt + 2)) >> 1);  // zoff(rt)
+      ci = desc ? cm : (pop ? zrt : ci);
+      const int iold = i;
+      i = desc ? im : (pop ? rt : i);
       ped_par = desc ? ped : (pop ? stp.x : ped_par);
       c = desc ? cnew : (pop ? stp.y : c);
-      // the parent's u is recomputed exactly as it was formed on the way down
+      // the level's u is recomputed exactly as it was formed on the way down
       u = desc ? unew : (pop ? fmaf(stp.y, lrp.y, uoff) : u);
       rii = desc ? lrn.x : (pop ? lrp.x : rii);
       flo = desc ? flonew : (pop ? stp.z : flo);
       fhi = desc ? flonew + 1.0f : (pop ? stp.w : fhi);
+      rt = desc ? (exh ? rt : iold) : (pop ? rtp : rt);
       if (visit) {
         ++n32;
         lsum += im;
         if (!enter) ++p32;
       }
+      // the sibling's evaluation, when it ends the level, is one the
+      // sequential search makes too
+      if ((visit || leaf) && has2 && exh) ++p32;
     }
 
     since += kPassesPerVote;
@@ -1012,6 +1062,7 @@ __global__ void __launch_bounds__(group_warps<G>() * 32, MDX_SDG_MIN_BLOCKS) sd_
 #undef ST
 #undef LR
 #undef XS
+#undef RT
 
 template <int G, bool kBudget>
 cudaError_t launch_group(const SdArgs& g, int num_sms, cudaStream_t s) {
