@@ -116,6 +116,30 @@ def code_hash(files, csrc=None):
     return h.hexdigest()[:16]
 
 
+# Warp instructions the search kernel executes per branched node (all of the
+# launch's instructions over its nodes), from the same kind of capture and
+# tied to the sources in the same way: with the live node rate this gives the
+# kernel's instruction-issue rate, the resource that bounds it.
+INSTRUCTIONS_PER_NODE = {
+    "16x16-16qam-sd-learned": (1.2128964723e10 / 297008606,
+                               "ncu capture of sd_group_kernel, 30,000 vectors of the learned 16x16 sweep: "
+                               "smsp__inst_executed.sum over the launch's branched nodes "
+                               "(profiles/sd_group_kernel_16x16_16qam_sweep_30k.md)",
+                               "41cf9bf6e4c91aa7"),
+}
+
+
+def instructions_per_node(workload):
+    """(warp instructions per node, source) of the workload's capture if the
+    kernel's sources are still the ones it was taken on, else (None, why)."""
+    ipn = INSTRUCTIONS_PER_NODE.get(workload)
+    if not ipn:
+        return None, "no capture of the current kernel"
+    if code_hash(KERNEL_SOURCES[workload]) != ipn[2]:
+        return None, f"the kernel changed since its capture ({ipn[1]})"
+    return ipn[0], ipn[1]
+
+
 def traffic_per_vector(workload):
     """(bytes per vector, source) of the workload's capture if the kernel's
     sources are still the ones it was taken on, else (None, why)."""
@@ -727,6 +751,16 @@ def search_roofline(workload, algo, stats, search_ms, calls, qr_ms, sms, probe, 
     achieved = flops / per_launch_s / 1e12 if per_launch_s > 0 else 0.0
     tpv, tsrc = traffic_per_vector(workload)
     nodes = float(stats[:, 0].sum())
+    # the bound in practice: instruction issue (4 schedulers per SM, one warp
+    # instruction per cycle each), at the captured instructions per node
+    ipn, isrc = instructions_per_node(workload)
+    issue_peak = sms * 4 * sm_max * 1e6
+    issue = {"warp_instructions_per_node": ipn, "source": isrc}
+    if ipn and per_launch_s > 0:
+        rate = ipn * nodes / per_launch_s
+        issue.update({"achieved": rate / 1e12, "peak": issue_peak / 1e12, "unit": "T warp instructions/s",
+                      "frac": rate / issue_peak,
+                      "peak_source": f"derived: {sms} SMs x 4 schedulers x 1 instruction per cycle x {sm_max:.0f} MHz"})
     return {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
             "measured_fma_peak": probe["fp32_fma_tflops"], "frac_of_measured": achieved / probe["fp32_fma_tflops"],
             "traffic": tpv * B if tpv else None,
@@ -736,7 +770,8 @@ def search_roofline(workload, algo, stats, search_ms, calls, qr_ms, sms, probe, 
             "qr_ms_per_launch": qr_ms / max(calls, 1),
             "nodes_per_s": nodes / per_launch_s if per_launch_s > 0 else None,
             "nodes_per_s_per_sm": nodes / per_launch_s / sms if per_launch_s > 0 else None,
-            "peak_source": f"derived: {sms} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 x {sm_max:.0f} MHz"}
+            "peak_source": f"derived: {sms} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 x {sm_max:.0f} MHz",
+            "issue": issue}
 
 
 def qr_roofline(n_rx, n_tx, B, prof, sms, probe):
