@@ -273,13 +273,15 @@ def detect_mixed(reqs, H, y, noise_var, want_gap=True, nthreads=0):
     the paper's N M sigma^2), node_budget and the offsets of each request's H,
     y and symbols in the flat arrays) detected request by request with
     detect_batch, grouping requests of equal parameters.  Returns flat symbols
-    and per-request metric, status and gap."""
+    and per-request metric, status, gap and stats (nodes, evaluations,
+    restarts, leaves, as detect_batch)."""
     H, y, nv = _f64(H).ravel(), _f64(y).ravel(), _f64(noise_var).ravel()
     nreq = len(reqs)
     nsym = int(max((int(r["sym_offset"]) + int(r["n_tx"]) for r in reqs), default=0))
     sym = np.zeros(nsym, dtype=np.uint8)
     met, gap = np.zeros(nreq), np.ones(nreq)
     status = np.zeros(nreq, dtype=np.int32)
+    stats = np.zeros((nreq, 4), dtype=np.int64)
     groups = {}
     for i, r in enumerate(reqs):
         key = (int(r["n_rx"]), int(r["n_tx"]), int(r["qam"]), int(r["algo"]),
@@ -301,7 +303,8 @@ def detect_mixed(reqs, H, y, noise_var, want_gap=True, nthreads=0):
         met[idx] = out["metric"]
         status[idx] = out["status"]
         gap[idx] = out["gap"]
-    return {"sym": sym, "metric": met, "status": status, "gap": gap}
+        stats[idx] = out["stats"]
+    return {"sym": sym, "metric": met, "status": status, "gap": gap, "stats": stats}
 
 
 def _slice(x, qam):

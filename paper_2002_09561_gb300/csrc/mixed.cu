@@ -126,9 +126,14 @@ __device__ void finish_request(const MixedArgs& g, const MixedReq& q, int r, con
 }
 
 // Exact SD of one request by one warp (ROWS = rows per lane, n <= 32 ROWS).
-// NAT: children in natural index order (the unsorted depth-first search the
-// paper compares against, Sec. IV-A) instead of Schnorr-Euchner order; a
-// child outside the sphere then does not end its level.
+// In Schnorr-Euchner order a visited node's next sibling is evaluated with
+// it; outside the sphere it finishes the level (the bound only shrinks), and
+// a pop goes straight to the nearest level above with a sibling left inside
+// (each level keeps that return level), so no iteration is spent climbing
+// through finished levels.  NAT: children in natural index order (the
+// unsorted depth-first search the paper compares against, Sec. IV-A)
+// instead; a child outside the sphere then does not end its level, and pops
+// go up one level at a time.
 template <int ROWS, bool NAT>
 __device__ void sd_request(const MixedArgs& g, const MixedReq& q, int r, const float* Rc, const float* yb,
                            unsigned char* st, float E, int lane) {
@@ -166,6 +171,10 @@ __device__ void sd_request(const MixedArgs& g, const MixedReq& q, int r, const f
     __syncwarp();
     float bnd = prune_bound(r2, E, n);
     int i = n - 1;
+    // sorted order: the level a pop from level i goes to, the nearest level
+    // above whose next child was inside the sphere when the path left it
+    // (n: none); the levels in between have no child left to try
+    int ret = n;
     float ped_par = 0.0f;
     float c = zs[col_off(i) + i];
     float rii = lv_rii[i];
@@ -189,19 +198,20 @@ __device__ void sd_request(const MixedArgs& g, const MixedReq& q, int r, const f
         ++peds;
       }
       if (NAT && k >= 0 && !(ped < bnd)) continue;  // unsorted: try the next child
-      if (k < 0 || !(ped < bnd)) {
-        if (i == n - 1) break;  // the root is exhausted
-        ++i;                    // backtrack
-        ped_par = lv_ped[i];
-        c = lv_c[i];
-        u = lv_u[i];
-        rii = lv_rii[i];
-        const int lh = lv_lohi[i];
-        lo = (lh & 0xffff) - 1;
-        hi = lh >> 16;
-        continue;
-      }
-      if (i == 0) {
+      // sorted order: whether the level's next child (the one a later
+      // iteration would take) is outside the sphere now, evaluated with the
+      // same operations; the bound only shrinks, so then it is outside then
+      // and nothing at this level is left to try
+      auto level_done = [&]() {
+        if (lo < 0 && hi >= P) return true;
+        const int k2 = (hi >= P || (lo >= 0 && fabsf(u - (float)lo) <= fabsf((float)hi - u))) ? lo : hi;
+        const float d2 = fmaf(-rii, (float)(2 * k2 - (P - 1)) * alpha, c);
+        if (fmaf(d2, d2, ped_par) < bnd) return false;
+        ++peds;  // the evaluation that ends the level, made here
+        return true;
+      };
+      bool up = k < 0 || !(ped < bnd);
+      if (i == 0 && !up) {
         // leaf inside the sphere: keep it among the kMixCand best, shrink the radius
         int slot = -1;
         if (lane == 0) {
@@ -230,6 +240,25 @@ __device__ void sd_request(const MixedArgs& g, const MixedReq& q, int r, const f
           r2 = ped;
           bnd = prune_bound(r2, E, n);
         }
+        if (NAT || !level_done()) continue;
+        up = true;
+      }
+      if (up) {
+        if (NAT) {
+          if (i == n - 1) break;  // the root is exhausted
+          ++i;                    // backtrack
+        } else {
+          if (ret >= n) break;  // no level above has a child left
+          i = ret;              // back to the nearest level with one
+        }
+        ped_par = lv_ped[i];
+        c = lv_c[i];
+        u = lv_u[i];
+        rii = lv_rii[i];
+        const int lh = lv_lohi[i];
+        lo = (lh & 0xff) - 1;
+        if (!NAT) ret = (lh >> 8) & 0xff;
+        hi = lh >> 16;
         continue;
       }
       if (q.budget > 0 && nodes >= q.budget) {
@@ -249,12 +278,26 @@ __device__ void sd_request(const MixedArgs& g, const MixedReq& q, int r, const f
       const float cnext = fmaf(-rc[i - 1], av, zin[i - 1]);
       const float unext = fmaf(cnext, lv_rinv[i - 1], uoff);
       const int lonext = NAT ? 0 : min(max((int)ceilf(unext - 0.5f), 0), P - 1);
+      bool done_here = false;
       if (!NAT) {
         const float d1 = fmaf(-lv_rii[i - 1], (float)(2 * lonext - (P - 1)) * alpha, cnext);
+        done_here = level_done();
         if (!(fmaf(d1, d1, ped) < bnd)) {
           ++nodes;
           ++peds;
           flops += 2 * (n - i) + 4 * P;
+          if (!done_here) continue;
+          // nothing else at this level: back to the return level
+          if (ret >= n) break;
+          i = ret;
+          ped_par = lv_ped[i];
+          c = lv_c[i];
+          u = lv_u[i];
+          rii = lv_rii[i];
+          const int lh = lv_lohi[i];
+          lo = (lh & 0xff) - 1;
+          ret = (lh >> 8) & 0xff;
+          hi = lh >> 16;
           continue;
         }
       }
@@ -262,9 +305,10 @@ __device__ void sd_request(const MixedArgs& g, const MixedReq& q, int r, const f
         lv_ped[i] = ped_par;
         lv_c[i] = c;
         lv_u[i] = u;
-        lv_lohi[i] = (lo + 1) | (hi << 16);
+        lv_lohi[i] = (lo + 1) | (NAT ? 0 : ret << 8) | (hi << 16);
         xs[i] = (uint8_t)k;
       }
+      if (!NAT && !done_here) ret = i;
       float* zout = zs + col_off(i - 1);
 #pragma unroll
       for (int t = 0; t < ROWS; ++t) {

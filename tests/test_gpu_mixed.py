@@ -100,6 +100,29 @@ def test_mixed_small_sizes(env):
     assert set(np.unique(vst)) <= {0, 1, 2}
 
 
+def test_mixed_sd_node_counts_match_the_oracle_at_high_snr(env):
+    """An exact-SD request runs on one warp without splitting, so its visited
+    nodes are those of the sequential Schnorr-Euchner search, whatever way the
+    warp moves between levels (it evaluates a visited node's next sibling and
+    pops straight past levels with nothing left inside the sphere).  They
+    differ from the oracle's only where a partial distance lies within the
+    FP32 pruning slack of the radius, so at 20..30 dB they are equal on most
+    requests and the totals agree closely."""
+    torch, mdx, ctx = env
+    d = wl.generate_mixed_inputs(41, 600, antennas=(4, 8, 16), snr_range=(20.0, 30.0), sd_fraction=1.0)
+    reqs = _table(mdx, d, budget=0)
+    H, y, nv = _dev(torch, d)
+    gpu = mdx.detect_mixed(ctx, reqs, H, y, nv)
+    torch.cuda.synchronize()
+    ref = oracle.detect_mixed(reqs, d["H"], d["y"], d["noise_var"])
+    _compare(reqs, gpu, ref, "exact SD, 20..30 dB")
+    g, o = gpu[3].cpu().numpy()[:, 0], ref["stats"][:, 0]
+    eq = g == o
+    print(f"node counts equal to the oracle's on {eq.mean():.4f} of requests, totals {g.sum()} vs {o.sum()}")
+    assert eq.mean() > 0.9
+    assert abs(g.sum() / o.sum() - 1.0) < 0.02
+
+
 def test_mixed_large_sizes(env):
     """32, 64 and 100 antennas: K-best K=64 over the whole SNR range, exact SD
     at 24..30 dB with the node budget."""
