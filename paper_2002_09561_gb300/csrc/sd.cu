@@ -36,6 +36,10 @@
 // backtrack.  Children are visited in increasing (c_i - R_ii a_k)^2 by a
 // zig-zag around u_i = c_i / (2 alpha R_ii) + (P-1)/2 in PAM-index space,
 // ties to the lower index; a child reaching the pruning bound ends the level.
+// A visited node's next sibling is evaluated with it: outside the sphere (the
+// bound only shrinks) it ends its level at once, and a pop goes straight to
+// the nearest level above with a sibling left inside, which each level keeps
+// packed with its cursors.
 //
 // The task queue is a ring: a consumer claims an index, waits for the
 // producer's sequence number, copies the record and marks the slot free; a
@@ -260,8 +264,39 @@ __global__ void __launch_bounds__(kWarpsMax * 32, ROWS == 1 ? MDX_SD_MIN_BLOCKS_
     float u = fmaf(c, rtop.y, uoff);
     int lo = min(max((int)ceilf(u - 0.5f), 0), P - 1);
     int hi = lo + 1;
+    // the level a pop from level i goes to: the nearest level above whose
+    // next child was inside the sphere when the path left it (top + 1: none,
+    // the task is done); the levels in between have no child left to try
+    int ret = top + 1;
     n32 = 1;
     lsum = top;
+    // Whether the level's next child in Schnorr-Euchner order (the one a
+    // later iteration would take) is outside the sphere now, evaluated with
+    // the same operations; the bound only shrinks, so it is outside then and
+    // the level has nothing left.  The evaluation is counted here.
+    auto level_done = [&]() {
+      if (lo < 0 && hi >= P) return true;
+      const int k2 = (hi >= P || (lo >= 0 && fabsf(u - (float)lo) <= fabsf((float)hi - u))) ? lo : hi;
+      const float d2 = fmaf(-rii, (float)(2 * k2 - (P - 1)) * alpha, c);
+      if (fmaf(d2, d2, ped_par) < bnd) return false;
+      ++p32;
+      return true;
+    };
+    // back to the return level (false: the task's node is exhausted)
+    auto pop = [&]() {
+      if (ret > top) return false;
+      i = ret;
+      const float4 st = lv_st[i];
+      ped_par = st.x;
+      c = st.y;
+      u = st.z;
+      rii = lv_r[i].x;
+      const int lh = __float_as_int(st.w);
+      lo = (lh & 0xff) - 1;
+      ret = (lh >> 8) & 0xff;
+      hi = lh >> 16;
+      return true;
+    };
     // budget left for this task's uncommitted nodes (n32 counts them)
     int left32 = 0x7fffffff;
     if (a.budget > 0) {
@@ -282,16 +317,7 @@ __global__ void __launch_bounds__(kWarpsMax * 32, ROWS == 1 ? MDX_SD_MIN_BLOCKS_
         ++p32;
       }
       if (k < 0 || !(ped < bnd)) {
-        if (i == top) break;  // the task's node is exhausted
-        ++i;                  // backtrack: pop level i
-        const float4 st = lv_st[i];
-        ped_par = st.x;
-        c = st.y;
-        u = st.z;
-        rii = lv_r[i].x;
-        const int lh = __float_as_int(st.w);
-        lo = (lh & 0xffff) - 1;
-        hi = lh >> 16;
+        if (!pop()) break;  // the task's node is exhausted
         continue;
       }
       if (i == 0) {
@@ -336,6 +362,7 @@ __global__ void __launch_bounds__(kWarpsMax * 32, ROWS == 1 ? MDX_SD_MIN_BLOCKS_
           r2 = ped;
           bnd = prune_bound(r2, E, n);
         }
+        if (level_done() && !pop()) break;
         continue;
       }
       if (n32 >= left32) {
@@ -356,6 +383,7 @@ __global__ void __launch_bounds__(kWarpsMax * 32, ROWS == 1 ? MDX_SD_MIN_BLOCKS_
       const float2 rl = lv_r[i - 1];
       const float unext = fmaf(cnext, rl.y, uoff);
       const int lonext = min(max((int)ceilf(unext - 0.5f), 0), P - 1);
+      const bool done_here = level_done();
       {
         const float d1 = fmaf(-rl.x, (float)(2 * lonext - (P - 1)) * alpha, cnext);
         if (!(fmaf(d1, d1, ped) < bnd)) {
@@ -363,13 +391,15 @@ __global__ void __launch_bounds__(kWarpsMax * 32, ROWS == 1 ? MDX_SD_MIN_BLOCKS_
           ++p32;
           lsum += i - 1;
           ++task_nodes;
+          if (done_here && !pop()) break;
           continue;
         }
       }
       if (lane == 0) {
-        lv_st[i] = make_float4(ped_par, c, u, __int_as_float((lo + 1) | (hi << 16)));
+        lv_st[i] = make_float4(ped_par, c, u, __int_as_float((lo + 1) | (ret << 8) | (hi << 16)));
         xs[i] = (uint8_t)k;
       }
+      if (!done_here) ret = i;
       float* zout = zs + col_off(i - 1);
 #pragma unroll
       for (int t = 0; t < ROWS; ++t) {
@@ -447,7 +477,7 @@ __global__ void __launch_bounds__(kWarpsMax * 32, ROWS == 1 ? MDX_SD_MIN_BLOCKS_
             } else {
               const float4 st = lv_st[l];
               const int lh = __float_as_int(st.w);
-              llo = (lh & 0xffff) - 1;
+              llo = (lh & 0xff) - 1;
               lhi = lh >> 16;
               lc = st.y;
               lu = st.z;
@@ -520,7 +550,8 @@ __global__ void __launch_bounds__(kWarpsMax * 32, ROWS == 1 ? MDX_SD_MIN_BLOCKS_
               lo = -1;
               hi = P;
             } else if (lane == 0) {
-              reinterpret_cast<int*>(&lv_st[l])[3] = P << 16;
+              int* w = reinterpret_cast<int*>(&lv_st[l]) + 3;
+              *w = (*w & 0xff00) | (P << 16);  // no child left; the return level stays
             }
             __syncwarp();
           }

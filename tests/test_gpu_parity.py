@@ -124,6 +124,27 @@ def test_sd_ragged_sizes(env, N, M, qam, snr, B):
     _compare(gpu, ref, SD_GAP)
 
 
+def test_sd_above_32_rows_counts_and_answers(env):
+    """n = 48 real rows (24 x 24 16-QAM) take the warp kernel, which
+    evaluates a visited node's next sibling with it and pops straight to the
+    nearest level with a sibling left inside.  Without splitting its visited
+    nodes are those of the sequential Schnorr-Euchner search: equal to the
+    oracle's except where a partial distance lies within the FP32 pruning
+    slack of the radius.  With splitting the answers are the oracle's."""
+    torch, mdx, ctx = env
+    w = wl.generate(3123, 300, 24, 24, 16, 18.0)
+    ref = oracle.detect_batch("sd", w["H"], w["y"], w["noise_var"], 16, radius="paper", want_gap=True)
+    seq = _run(env, "sd", w, 16, radius="paper", flags=mdx.MDX_SEQUENTIAL_SEARCH)
+    _compare(seq, ref, SD_GAP, label="sd sequential 24x24 16-QAM 18 dB")
+    g, o = seq[3][:, 0], ref["stats"][:, 0]
+    eq = g == o
+    print(f"node counts equal to the oracle's on {eq.mean():.4f} of vectors, totals {g.sum()} vs {o.sum()}")
+    assert eq.mean() > 0.8
+    assert abs(g.sum() / o.sum() - 1.0) < 0.03
+    gpu = _run(env, "sd", w, 16, radius="paper")
+    _compare(gpu, ref, SD_GAP, label="sd 24x24 16-QAM 18 dB")
+
+
 def test_sd_radius_doubling(env):
     """A radius far below the ML metric leaves the sphere empty; the detector
     doubles it until a leaf appears and still returns the ML point."""
