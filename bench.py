@@ -129,26 +129,30 @@ INSTRUCTIONS_PER_NODE = {
 }
 
 
-def instructions_per_node(workload):
-    """(warp instructions per node, source) of the workload's capture if the
-    kernel's sources are still the ones it was taken on, else (None, why)."""
-    ipn = INSTRUCTIONS_PER_NODE.get(workload)
-    if not ipn:
+def _captured(table, workload):
+    """(value, source) of the workload's entry in a table of ncu-captured
+    figures if the kernel's sources are still the ones the capture was taken
+    on, else (None, why)."""
+    entry = table.get(workload)
+    if not entry:
         return None, "no capture of the current kernel"
-    if code_hash(KERNEL_SOURCES[workload]) != ipn[2]:
-        return None, f"the kernel changed since its capture ({ipn[1]})"
-    return ipn[0], ipn[1]
+    if code_hash(KERNEL_SOURCES[workload]) != entry[2]:
+        return None, f"the kernel changed since its capture ({entry[1]})"
+    return entry[0], entry[1]
+
+
+def instructions_per_node(workload):
+    """(warp instructions per node, source) of the workload's capture, or
+    (None, why)."""
+    return _captured(INSTRUCTIONS_PER_NODE, workload)
 
 
 def traffic_per_vector(workload):
-    """(bytes per vector, source) of the workload's capture if the kernel's
-    sources are still the ones it was taken on, else (None, why)."""
-    tpv = TRAFFIC_PER_VECTOR.get(workload)
-    if not tpv:
-        return None, "no capture of the current kernel"
-    if code_hash(KERNEL_SOURCES[workload]) != tpv[2]:
-        return None, f"the kernel changed since its capture ({tpv[1]})"
-    return tpv[0], tpv[1]
+    """(DRAM bytes per vector, source) of the workload's capture, or
+    (None, why)."""
+    return _captured(TRAFFIC_PER_VECTOR, workload)
+
+
 FP32_LANES_PER_SM = 128  # FP32 FMA lanes per SM (4 sub-partitions x 32)
 
 
